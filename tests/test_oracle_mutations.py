@@ -1,0 +1,73 @@
+"""The oracle's pins must catch plausible mistakes: each case plants one mistake in a
+temporary copy of the oracle source (CPU only), rebuilds it, and checks that at least one
+pin of ``test_oracle_pins`` fails against the mutant."""
+import importlib
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import tests.test_oracle_pins as pins
+
+MUTANTS = {
+    # attached segment weight without the triangle-area ratio
+    "drop_area_ratio": ("T g = fabs(dot(nprev, din)) * fabs(dot(n, din)) * area / r2;",
+                        "T g = fabs(dot(nprev, din)) * fabs(dot(n, din)) / r2;",
+                        ["test_attached_gradient_unbiased_for_derivative_of_expected_image"]),
+    # sensor importance with cos^2 instead of cos^3 of the camera angle
+    "importance_cos2": ("T geo = cosc * T(K) / (dist2 * cc * cc * cc);",
+                        "T geo = cosc * T(K) / (dist2 * cc * cc);",
+                        ["test_primal_closed_form_area_light_over_plane"]),
+    # emitted flux without the pi of the cosine-weighted direction pdf
+    "emitter_no_pi": ("beta[c] = Le[c] * T(A_L * PI);", "beta[c] = Le[c] * T(A_L);",
+                      ["test_primal_closed_form_area_light_over_plane"]),
+    # p-polarised Fresnel amplitude with a flipped sign inside
+    "fresnel_rp": ("T rp = (ci - eta * ct) / (ci + eta * ct);", "T rp = (ci + eta * ct) / (ci + eta * ct);",
+                   ["test_dielectric_fresnel_and_snell"]),
+    # tent filter taps swapped (splat lands on the wrong side of the pixel centre)
+    "tent_swap": ("T wx[2] = {T(1.0) - fx, fx}, wy[2] = {T(1.0) - fy, fy};",
+                  "T wx[2] = {fx, T(1.0) - fx}, wy[2] = {fy, T(1.0) - fy};",
+                  ["test_primal_reciprocity_with_path_tracer", "test_primal_closed_form_area_light_over_plane"]),
+    # LRB-3 restatement: subtract the vertex's own contribution before its splat gradient
+    "lrb3_order": ("for (int c = 0; c < 3; ++c) { wsplat[c] = Pw[3 * ci + c]; rem[c] -= Pw[3 * ci + c]; }",
+                   "for (int c = 0; c < 3; ++c) { rem[c] -= Pw[3 * ci + c]; wsplat[c] = 0; }",
+                   ["test_lrb3_restatement_equals_naive_ad_per_seed"]),
+    # reservoir replacement probability w/Omega replaced by w/(Omega+w)
+    "reservoir_prob": ("if (u[i] < w[i] / Om) { R = (int)i; wR = w[i]; }",
+                       "if (u[i] < w[i] / (Om + w[i])) { R = (int)i; wR = w[i]; }",
+                       ["test_reservoir_selection_pmf_and_unbiasedness"]),
+    # attached slide: intersection parameter with the wrong sign
+    "slide_sign": ("T tt = dot(o - xprev, n) / dot(din, n);", "T tt = dot(xprev - o, n) / dot(din, n);",
+                   ["test_attached_height_gradient_vs_frozen_central_differences"]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_detect_planted_mistake(oracle, name):
+    old, new, tests = MUTANTS[name]
+    src = open(oracle.SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found: {name}"
+    tmpdir = tempfile.mkdtemp(prefix="lt_mut_")
+    cpp = os.path.join(tmpdir, "mut.cpp")
+    so = os.path.join(tmpdir, "libmut.so")
+    open(cpp, "w").write(src.replace(old, new))
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-pthread",
+                           "-Wno-dangling-pointer", "-o", so, cpp])
+    mod = importlib.import_module("oracle.oracle")
+    saved_lib, saved_path = mod._lib, mod.LIB
+    failed = []
+    try:
+        mod._lib, mod.LIB = None, so
+        for t in tests:
+            fn = getattr(pins, t)
+            kwargs = {}
+            if t == "test_attached_height_gradient_vs_frozen_central_differences":
+                kwargs["which"] = "slab"
+            try:
+                fn(mod, **kwargs)
+            except (AssertionError, ValueError, FloatingPointError):
+                failed.append(t)
+    finally:
+        mod._lib, mod.LIB = saved_lib, saved_path
+    assert failed, f"no pin caught mutant {name}"

@@ -1,0 +1,322 @@
+"""Pins of the FP64 CPU oracle against things other than itself: closed forms,
+reciprocity with a path tracer, finite differences, exact invariants, special cases
+and statistical properties the paper states (CPU only)."""
+import numpy as np
+import pytest
+
+from paper_2609_32920_gb300 import inputs as I
+
+
+# ----------------------------------------------------------------------------- RNG
+def test_philox_uniformity_and_avalanche(oracle):
+    """Counter-based generator (Salmon et al. 2011): uniform words, independent counters,
+    and each counter bit flips about half of the output bits."""
+    n = 1 << 15
+    words = np.array([oracle.philox((0x1234, 0x9876), (i, 0, 7, 0)) for i in range(n)], dtype=np.uint64)
+    for w in range(4):
+        hist = np.bincount((words[:, w] >> 26).astype(np.int64), minlength=64)
+        chi2 = ((hist - n / 64) ** 2 / (n / 64)).sum()
+        assert chi2 < 120, chi2  # 63 dof, p ~ 1e-5
+        bits = np.unpackbits(words[:, w].astype(np.uint32).view(np.uint8)).reshape(n, 32).mean(0)
+        assert np.all(np.abs(bits - 0.5) < 0.02)
+    base = oracle.philox((5, 6), (1, 2, 3, 4)).astype(np.uint32)
+    flips = []
+    for word in range(4):
+        for bit in range(32):
+            c = [1, 2, 3, 4]
+            c[word] ^= 1 << bit
+            o = oracle.philox((5, 6), c).astype(np.uint32)
+            flips.append(np.unpackbits((o ^ base).view(np.uint8)).sum())
+    assert 56 < np.mean(flips) < 72  # of 128 bits
+    # key changes the stream too
+    assert not np.array_equal(oracle.philox((5, 7), (1, 2, 3, 4)), base)
+
+
+def test_uniforms_exact_in_float32(oracle):
+    """24-bit uniforms are exactly representable in fp32, so both precisions see the same numbers."""
+    u = np.array([oracle.uniforms(99, i, d) for i in range(200) for d in range(3)]).ravel()
+    assert np.all(u >= 0) and np.all(u < 1)
+    assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
+    assert np.array_equal(np.round(u * 2 ** 24), u * 2 ** 24)
+
+
+# ----------------------------------------------------------------------- dielectric
+def test_dielectric_fresnel_and_snell(oracle):
+    n = np.array([0.0, 1.0, 0.0])
+    # normal incidence: F = ((n1-n2)/(n1+n2))^2
+    d, F, refl = oracle.dielectric([0, -1.0, 0], n, 1.5, 0.9)
+    assert F == pytest.approx(0.04, abs=1e-12) and not refl
+    assert np.allclose(d, [0, -1, 0])
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        th = rng.uniform(0, np.pi / 2 * 0.99)
+        phi = rng.uniform(0, 2 * np.pi)
+        din = np.array([np.sin(th) * np.cos(phi), -np.cos(th), np.sin(th) * np.sin(phi)])
+        out, F, refl = oracle.dielectric(din, n, 1.5, 1.0 - 1e-12)  # force refraction when possible
+        assert not refl
+        sin_t = np.linalg.norm(np.cross(out, n))
+        assert sin_t == pytest.approx(np.sin(th) / 1.5, abs=1e-12)  # Snell
+        assert np.linalg.norm(out) == pytest.approx(1.0, abs=1e-12)
+        assert np.dot(np.cross(din, n), out) == pytest.approx(0.0, abs=1e-12)  # plane of incidence
+        rl, F2, refl2 = oracle.dielectric(din, n, 1.5, 0.0)
+        assert refl2 and np.allclose(rl, din - 2 * np.dot(din, n) * n)
+    # Brewster angle: p-polarised reflectance vanishes, F = Rs/2
+    tb = np.arctan(1.5)
+    din = np.array([np.sin(tb), -np.cos(tb), 0])
+    _, F, _ = oracle.dielectric(din, n, 1.5, 0.5)
+    ct = np.sqrt(1 - (np.sin(tb) / 1.5) ** 2)
+    rs = (np.cos(tb) - 1.5 * ct) / (np.cos(tb) + 1.5 * ct)
+    assert F == pytest.approx(rs * rs / 2, rel=1e-10)
+    # total internal reflection beyond the critical angle from inside
+    tc = np.arcsin(1 / 1.5)
+    for th in (tc + 0.01, 1.2):
+        din = np.array([np.sin(th), np.cos(th), 0])  # travelling +y, exiting through normal +y
+        out, F, refl = oracle.dielectric(din, n, 1.5, 0.999)
+        assert refl and F == 1.0 and np.allclose(out, [np.sin(th), -np.cos(th), 0])
+    # just below the critical angle the ray exits and bends away from the normal
+    th = tc - 0.05
+    out, F, refl = oracle.dielectric([np.sin(th), np.cos(th), 0], n, 1.5, 0.999)
+    assert not refl and np.linalg.norm(np.cross(out, n)) == pytest.approx(1.5 * np.sin(th), abs=1e-12)
+
+
+# ------------------------------------------------------------------------ reservoir
+def test_reservoir_selection_pmf_and_unbiasedness(oracle):
+    """Eq. 8: Pr(R=i) = w_i / Omega_k; Eq. 10: E[(Omega_k/w_R) x_R] = sum_i x_i."""
+    rng = np.random.default_rng(1)
+    w = np.array([0.3, 0.0, 1.7, 0.05, 0.9, 2.2])
+    x = rng.normal(size=w.size)
+    M = 40000
+    counts = np.zeros(w.size)
+    est = np.zeros(M)
+    for m in range(M):
+        R, rw = oracle.reservoir(w, rng.random(w.size))
+        counts[R] += 1
+        est[m] = rw * x[R]
+        assert rw == pytest.approx(w.sum() / w[R])
+    p = w / w.sum()
+    nz = p > 0
+    chi2 = ((counts[nz] - M * p[nz]) ** 2 / (M * p[nz])).sum()
+    assert counts[~nz].sum() == 0
+    assert chi2 < 25  # 4 dof
+    assert abs(est.mean() - x[nz].sum()) < 4 * est.std() / np.sqrt(M)
+    R, rw = oracle.reservoir(np.zeros(3), np.zeros(3))
+    assert R == -1 and rw == 0
+
+
+# ----------------------------------------------------------------------- primal image
+def _lambert_polygon_irradiance(x, corners, Le):
+    """Irradiance at x on a +y-facing plane from a Lambertian polygon (Lambert's formula)."""
+    n = np.array([0, 1.0, 0])
+    v = [(c - x) / np.linalg.norm(c - x) for c in corners]
+    tot = 0.0
+    for k in range(len(v)):
+        a, b = v[k], v[(k + 1) % len(v)]
+        cr = np.cross(a, b)
+        tot += np.arccos(np.clip(a @ b, -1, 1)) * (n @ cr) / np.linalg.norm(cr)
+    return abs(Le * tot / 2)
+
+
+def test_primal_closed_form_area_light_over_plane(oracle):
+    """Direct light (depth 1) on a diffuse plane under a square Lambertian emitter: pixel =
+    tent-weighted average over the on-film footprint of rho E / pi, E from Lambert's formula."""
+    sc = I.plane_under_light(res=16)
+    rho = sc.meta["albedo"]
+    q = sc.quads[sc.emitter_quad]
+    o, e1, e2 = q[:3], q[3:6], q[6:9]
+    corners = [o, o + e1, o + e1 + e2, o + e2]
+    f = sc.cam_look - sc.cam_pos
+    f /= np.linalg.norm(f)
+    r = np.cross(f, sc.cam_up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    tany = np.tan(np.radians(sc.fov_y_deg) / 2)
+    tanx = tany * sc.W / sc.H
+    g = (np.arange(12) + 0.5) / 12 * 2 - 1
+    tw = 1 - np.abs(g)
+    tw /= tw.sum()
+    ref = np.zeros((sc.H, sc.W))
+    for py in range(sc.H):
+        for px in range(sc.W):
+            acc = 0.0
+            for a, wa in zip(g, tw):
+                for b, wb in zip(g, tw):
+                    ux, uy = px + 0.5 + a, py + 0.5 + b
+                    if not (0 <= ux < sc.W and 0 <= uy < sc.H):
+                        continue  # the light tracer only splats connections landing on the film
+                    d = f + r * (2 * ux / sc.W - 1) * tanx + u * (1 - 2 * uy / sc.H) * tany
+                    x = sc.cam_pos + (-sc.cam_pos[1] / d[1]) * d
+                    acc += wa * wb * rho * _lambert_polygon_irradiance(x, corners, 1.0) / np.pi
+            ref[py, px] = acc
+    B, N = 16, 1 << 17
+    imgs = np.array([oracle.render(sc, seed=s, n_paths=N, max_depth=1)[..., 0] for s in range(B)])
+    m = imgs.mean(0)
+    se = imgs.std(0, ddof=1) / np.sqrt(B)
+    z = (m - ref) / se
+    assert np.mean(z ** 2) < 1.6
+    assert np.mean(np.abs(z) > 3) < 0.03
+    assert abs(m.sum() / ref.sum() - 1) < 4 * np.sqrt((se ** 2).sum()) / ref.sum()
+    # the three channels are identical for a grey scene
+    img = oracle.render(sc, seed=0, n_paths=1 << 12, max_depth=1)
+    assert np.array_equal(img[..., 0], img[..., 1])
+
+
+def test_primal_reciprocity_with_path_tracer(oracle):
+    """Light tracing and camera-side path tracing estimate the same image (box with a
+    diffuse height field, depth 3): per-pixel agreement within Monte Carlo error."""
+    sc = I.box_scene(12, heightmap=4, hm_std=0.05)
+    D, B = 3, 16
+    lts = np.array([oracle.render(sc, seed=s, n_paths=1 << 17, max_depth=D) for s in range(B)])
+    pts = np.array([oracle.render_pt(sc, seed=100 + s, spp=96, max_depth=D) for s in range(B)])
+    se = np.sqrt(lts.var(0, ddof=1) / B + pts.var(0, ddof=1) / B)
+    z = (lts.mean(0) - pts.mean(0)) / se
+    assert np.mean(z ** 2) < 1.5
+    assert np.mean(np.abs(z) > 3.5) < 0.02
+    tot = lts.mean(0).sum() / pts.mean(0).sum()
+    assert abs(tot - 1) < 0.01
+
+
+# ------------------------------------------------------------------ gradients (exact)
+def _loss_fd(oracle, sc, dI, p0, p1, **kw):
+    return oracle.frozen_loss(sc, dI, p0, p1, **kw)
+
+
+def test_detached_albedo_gradient_vs_central_differences(oracle):
+    """With geometry fixed the per-seed image is a polynomial in the albedos, so FP64
+    central differences pin naive AD to ~1e-7 relative."""
+    sc = I.box_scene(24)
+    dI = I.smooth_adjoint(sc.W, sc.H, 11)
+    kw = dict(seed=3, n_paths=1 << 11, max_depth=4)
+    g = oracle.gradient(sc, dI, method=oracle.NAIVE, **kw)
+    a0 = sc.albedo.copy()
+    for k in np.argsort(-np.abs(g["d_albedo"]))[:5]:
+        h = 1e-4
+        ap, am = a0.copy(), a0.copy()
+        ap[k] += h
+        am[k] -= h
+        fd = (_loss_fd(oracle, sc, dI, (a0, sc.Le, sc.heights), (ap, sc.Le, sc.heights), **kw)
+              - _loss_fd(oracle, sc, dI, (a0, sc.Le, sc.heights), (am, sc.Le, sc.heights), **kw)) / (2 * h)
+        assert g["d_albedo"][k] == pytest.approx(fd, rel=1e-7, abs=1e-14)
+    # emitted radiance: the image is linear in Le, so dL/dLe_c = <dI_c, I_c>/Le_c exactly
+    img = oracle.render(sc, seed=3, n_paths=1 << 11, max_depth=4)
+    assert np.allclose(g["d_Le"], (dI * img).sum(axis=(0, 1)) / sc.Le, rtol=1e-12)
+    assert g["loss"] == pytest.approx((dI * img).sum(), rel=1e-12)
+
+
+@pytest.mark.parametrize("which", ["box_hm", "slab"])
+def test_attached_height_gradient_vs_frozen_central_differences(oracle, which):
+    if which == "box_hm":
+        sc, D = I.box_scene(24, heightmap=6), 5
+    else:
+        sc, D = I.slab_scene(48, n=12), 8
+    dI = I.smooth_adjoint(sc.W, sc.H, 13)
+    kw = dict(seed=1, n_paths=1 << 11, max_depth=D)
+    g = oracle.gradient(sc, dI, method=oracle.NAIVE, attached=1, **kw)
+    h0 = sc.heights.copy()
+    for k in np.argsort(-np.abs(g["d_heights"]))[:4]:
+        h = 1e-6
+        hp, hm = h0.copy(), h0.copy()
+        hp[k] += h
+        hm[k] -= h
+        fd = (_loss_fd(oracle, sc, dI, (sc.albedo, sc.Le, h0), (sc.albedo, sc.Le, hp), **kw)
+              - _loss_fd(oracle, sc, dI, (sc.albedo, sc.Le, h0), (sc.albedo, sc.Le, hm), **kw)) / (2 * h)
+        assert g["d_heights"][k] == pytest.approx(fd, rel=2e-5)
+    # the attached and detached albedo gradients agree (albedo moves no vertex)
+    gd = oracle.gradient(sc, dI, method=oracle.NAIVE, attached=0, **kw)
+    assert np.allclose(g["d_albedo"], gd["d_albedo"], rtol=1e-12, atol=1e-300)
+    assert np.allclose(g["d_Le"], gd["d_Le"], rtol=1e-12)
+
+
+def test_attached_gradient_unbiased_for_derivative_of_expected_image(oracle):
+    """The attached frozen-decision gradient has the expectation of d/dtheta E[<dI, I>]
+    (interior derivative; no visibility boundary moves in this scene): compared with
+    common-random-number central differences of the full, re-decided renderer."""
+    sc = I.plane_under_light(res=16, heightmap=9, hm_std=0.05, plane_half=1.5, light_h=0.8, light_size=0.3)
+    dI = np.ones((sc.H, sc.W, 3)) / (sc.W * sc.H)
+    D, N, S, h = 1, 1 << 15, 32, 2e-3
+    ks = [40, 31]
+    h0 = sc.heights.copy()
+    diffs = []
+    for s in range(S):
+        g = oracle.gradient(sc, dI, seed=s, n_paths=N, max_depth=D, attached=1)["d_heights"][ks]
+        fd = []
+        for k in ks:
+            hp, hm = h0.copy(), h0.copy()
+            hp[k] += h
+            hm[k] -= h
+            lp = oracle.gradient(sc, dI, seed=s, n_paths=N, max_depth=D, heights=hp)["loss"]
+            lm = oracle.gradient(sc, dI, seed=s, n_paths=N, max_depth=D, heights=hm)["loss"]
+            fd.append((lp - lm) / (2 * h))
+        diffs.append(g - np.array(fd))
+    d = np.array(diffs)
+    z = d.mean(0) / (d.std(0, ddof=1) / np.sqrt(S))
+    assert np.all(np.abs(z) < 4), z
+
+
+# ------------------------------------------------------------- methods vs naive AD
+def test_lrb3_restatement_equals_naive_ad_per_seed(oracle):
+    """LRB-3-pass (Eq. 14-17) reaches exactly the naive reverse-mode gradient per seed."""
+    sc = I.box_scene(24)
+    dI = I.smooth_adjoint(sc.W, sc.H, 5)
+    for seed, D in ((0, 4), (1, 9)):
+        kw = dict(seed=seed, n_paths=1 << 11, max_depth=D)
+        a = oracle.gradient(sc, dI, method=oracle.NAIVE, **kw)
+        b = oracle.gradient(sc, dI, method=oracle.LRB3_RESTATED, **kw)
+        assert np.linalg.norm(a["d_albedo"] - b["d_albedo"]) <= 1e-12 * np.linalg.norm(a["d_albedo"])
+        assert np.allclose(a["d_Le"], b["d_Le"], rtol=1e-12)
+
+
+def test_reslrb_restatement_equals_ad_of_reservoir_estimator(oracle):
+    sc = I.box_scene(24)
+    dI = I.smooth_adjoint(sc.W, sc.H, 6)
+    kw = dict(seed=2, n_paths=1 << 11, max_depth=6)
+    a = oracle.gradient(sc, dI, method=oracle.RESLRB_AD, **kw)
+    b = oracle.gradient(sc, dI, method=oracle.RESLRB_RESTATED, **kw)
+    assert np.linalg.norm(a["d_albedo"] - b["d_albedo"]) <= 1e-12 * np.linalg.norm(a["d_albedo"])
+    assert np.allclose(a["d_Le"], b["d_Le"], rtol=1e-12)
+    # the ResLRB primal splats the reservoir winner S = (Omega/w_R) L_R (Eq. 9); its
+    # image is linear in Le too
+    img = oracle.render(sc, seed=2, n_paths=1 << 11, max_depth=6, estimator=1)
+    assert np.allclose(a["d_Le"], (dI * img).sum(axis=(0, 1)) / sc.Le, rtol=1e-12)
+
+
+@pytest.mark.parametrize("attached", [0, 1])
+def test_depth_one_all_methods_coincide(oracle, attached):
+    """Depth 1: every path has at most one connection, so ResLRB selects it with weight 1
+    and equals naive AD (and LRB-3) per seed."""
+    sc = I.box_scene(24, heightmap=5)
+    dI = I.smooth_adjoint(sc.W, sc.H, 7)
+    kw = dict(seed=4, n_paths=1 << 12, max_depth=1, attached=attached)
+    a = oracle.gradient(sc, dI, method=oracle.NAIVE, **kw)
+    b = oracle.gradient(sc, dI, method=oracle.RESLRB_AD, **kw)
+    for k in ("d_albedo", "d_Le", "d_heights"):
+        assert np.allclose(a[k], b[k], rtol=1e-12, atol=1e-300)
+    i0 = oracle.render(sc, seed=4, n_paths=1 << 12, max_depth=1)
+    i1 = oracle.render(sc, seed=4, n_paths=1 << 12, max_depth=1, estimator=1)
+    assert np.allclose(i0, i1, rtol=1e-12, atol=1e-300)
+
+
+def test_reslrb_gradient_unbiased_paired(oracle):
+    """Eq. 10: over seeds, the ResLRB gradient matches the naive gradient in expectation
+    (paired per seed to cancel path noise; mean difference within 3 standard errors)."""
+    sc = I.box_scene(16)
+    dI = I.smooth_adjoint(sc.W, sc.H, 8)
+    S = 64
+    rng = np.random.default_rng(3)
+    proj = rng.normal(size=sc.albedo.size)
+    dd, dp = [], []
+    for s in range(S):
+        kw = dict(seed=1000 + s, n_paths=1 << 10, max_depth=6)
+        a = oracle.gradient(sc, dI, method=oracle.NAIVE, **kw)
+        b = oracle.gradient(sc, dI, method=oracle.RESLRB_AD, **kw)
+        dd.append(np.concatenate([b["d_Le"] - a["d_Le"], [proj @ (b["d_albedo"] - a["d_albedo"])]]))
+        dp.append(b["d_albedo"] - a["d_albedo"])
+    dd = np.array(dd)
+    z = dd.mean(0) / (dd.std(0, ddof=1) / np.sqrt(S))
+    assert np.all(np.abs(z) < 3.5), z
+    dp = np.array(dp)
+    sd = dp.std(0, ddof=1)
+    ok = sd > 0
+    zp = dp.mean(0)[ok] / (sd[ok] / np.sqrt(S))
+    assert np.mean(np.abs(zp) > 3) < 0.02
+    # and it is a different per-seed estimator (variance strictly positive)
+    assert np.all(dd.std(0) > 0)
