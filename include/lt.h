@@ -1,0 +1,189 @@
+/* lt.h -- C ABI of liblt: constant-memory reverse-mode differentiable light tracing on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * The problem (paper "Constant-Memory Differentiable Light Tracing", Sec. 3.2): given a
+ * scene with parameters theta (diffuse albedo textures, emitted radiance Le, height-field
+ * vertex heights), render the light-traced image I (Sec. 3.1, Eq. 1-2: every light path
+ * x0..xk splats each unoccluded non-specular vertex's sensor connection L_i at film
+ * position u_i through a reconstruction filter, Eq. 20), and given the image-space adjoint
+ * dI = dLoss/dI compute dLoss/dtheta = d<dI, I>/dtheta without a tape that grows with path
+ * depth.  Two constant-memory methods: ResLRB (Sec. 4.2) and LRB-3-pass (Sec. 4.3), each
+ * detached (values only) or attached (vertices and splat positions move, Sec. 3.3, 4.4).
+ * A naive reverse-mode baseline with a per-vertex tape is provided for comparison.
+ *
+ * Conventions
+ *  - Every call is asynchronous on the CUDA stream passed as `stream` (a cudaStream_t;
+ *    NULL = legacy default stream) unless stated otherwise.
+ *  - "DEVICE" pointers are CUDA device memory owned by the caller; "HOST" pointers are
+ *    read before the call returns.  The library never frees caller memory.
+ *  - Errors: host-side validation returns immediately with a status and a message
+ *    readable through lt_last_error() (thread-local).  Device-side checks (index bounds,
+ *    bounded waits) set an error word in the scene; lt_sync_status() reads and clears it.
+ *    No call aborts the process or traps the GPU; no C++ exception crosses the ABI.
+ *  - Float images are row-major [H][W][3] (row 0 at the top of the film), FP32.
+ *  - Random numbers: Philox4x32-10 keyed by the 64-bit seed, counter (path index, vertex
+ *    depth, stream); every path is replayed from its index, nothing else is stored.
+ */
+#ifndef LT_H
+#define LT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LT_OK = 0,
+  LT_ERR_INVALID_ARG = 1,   /* a host-side argument check failed                    */
+  LT_ERR_OOM = 2,           /* allocation failed or caller workspace too small      */
+  LT_ERR_CUDA = 3,          /* a CUDA runtime call failed                           */
+  LT_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up                   */
+  LT_ERR_DEVICE_CHECK = 5,  /* a device-side bounds/consistency check fired         */
+  LT_ERR_UNSUPPORTED = 6    /* valid request this build does not implement          */
+} lt_status;
+
+enum { LT_MAT_DIFFUSE = 0, LT_MAT_DIELECTRIC = 1, LT_MAT_EMITTER = 2 };
+enum { LT_EST_PLAIN = 0, LT_EST_RESLRB = 1, LT_EST_NAIVE = 2 };
+enum { LT_TARGET_LUMINANCE = 0, LT_TARGET_MLP = 1 };
+
+typedef struct lt_scene lt_scene; /* opaque: device geometry, BVH, error word */
+
+/* Scene description (all HOST pointers, copied by lt_scene_create).
+ * Primitives: quads first (ids 0..n_quads-1), then triangles.  A quad is the
+ * parallelogram o + s e1 + t e2, s,t in [0,1]; a triangle is (v0, v1, v2) with
+ * vertex k at verts[tris[3i+k]] plus (0, heights[vert_h[.]], 0) when vert_h >= 0.
+ * Geometric normal = cross(e1, e2) (cross(v1-v0, v2-v0)).  Diffuse surfaces are
+ * two-sided Lambertian with albedo texture h x w x 3 at albedo[mat_tex_off...]
+ * (bilinear, texel centres, clamp to edge, texture coordinates = (s, t) on quads and the
+ * barycentrics (b1, b2) on triangles).  Dielectrics are smooth with index mat_ior.
+ * The emitter is a one-sided Lambertian quad emitting along its normal; it absorbs
+ * any ray that hits it.  Pinhole camera: image plane at distance 1, vertical field of
+ * view fov_y_deg, width x height pixels. */
+typedef struct {
+  int n_quads;
+  const float* quads;      /* [n_quads][9] o, e1, e2                               */
+  int n_verts;
+  const float* verts;      /* [n_verts][3] base positions                          */
+  const int* vert_h;       /* [n_verts] height-parameter index or -1               */
+  int n_tris;
+  const int* tris;         /* [n_tris][3] vertex indices                           */
+  const int* prim_mat;     /* [n_quads + n_tris] material index                    */
+  int n_mats;
+  const int* mat_type;     /* [n_mats] LT_MAT_*                                    */
+  const float* mat_ior;    /* [n_mats]                                             */
+  const int* mat_tex_off;  /* [n_mats] offset (floats) into the albedo array       */
+  const int* mat_tex_w;    /* [n_mats]                                             */
+  const int* mat_tex_h;    /* [n_mats]                                             */
+  int emitter_quad;        /* quad index of the area emitter                       */
+  float cam_pos[3], cam_look[3], cam_up[3];
+  float fov_y_deg;
+  int width, height;
+  int n_albedo;            /* length of the albedo parameter array                 */
+  int n_heights;           /* length of the heights parameter array                */
+} lt_scene_desc;
+
+/* Per-call parameters theta (DEVICE pointers, FP32, caller-owned, read only). */
+typedef struct {
+  const float* albedo;   /* [n_albedo] */
+  const float* Le;       /* [3]        */
+} lt_params;
+
+typedef struct {
+  uint64_t seed;        /* Philox key                                               */
+  int64_t path_offset;  /* first path index (Philox counter) traced by this call    */
+  int64_t n_paths;      /* number of paths traced by this call                      */
+  int64_t n_norm;       /* N of the estimator's 1/N; 0 means n_paths                */
+  int max_depth;        /* traced intersections x1..xD per path, 1..64              */
+  int attached;         /* 0 detached, 1 attached (geometry derivatives)            */
+  int target;           /* reservoir target: LT_TARGET_LUMINANCE or LT_TARGET_MLP   */
+  const void* mlp;      /* DEVICE lt_mlp weights when target == LT_TARGET_MLP       */
+  int block_size;       /* threads per block, 0 = library default                   */
+  int blocks_per_sm;    /* resident blocks per SM for the persistent grid, 0 = auto */
+  const uint8_t* path_mask; /* DEVICE [n_paths] optional: 0 = skip path (testing)   */
+  uint32_t* path_hash;  /* DEVICE [n_paths] optional out: decision hash per path    */
+  float* path_dbg;      /* DEVICE [n_paths][4] optional out (see each call)         */
+} lt_render_opts;
+
+/* Gradient outputs (DEVICE, FP32, caller-owned).  NULL skips a parameter group.
+ * Overwritten unless accumulate != 0. */
+typedef struct {
+  float* d_albedo;   /* [n_albedo]  */
+  float* d_Le;       /* [3]         */
+  float* d_heights;  /* [n_heights] */
+  int accumulate;
+} lt_grads;
+
+/* Build the scene: copies the description to the device, builds a binned-SAH BVH over
+ * all primitives (host, once) and uploads it.  Heights start at zero; call
+ * lt_scene_refit to set them.  Returns LT_ERR_INVALID_ARG for inconsistent arrays. */
+lt_status lt_scene_create(const lt_scene_desc* desc, void* stream, lt_scene** out);
+
+/* Set the height-field parameters (DEVICE [n_heights]) and refit triangle geometry and
+ * BVH bounds on the device (topology unchanged).  Must precede any render call that
+ * should see the heights.  Attached derivatives are taken at these heights. */
+lt_status lt_scene_refit(lt_scene* scene, const float* heights, void* stream);
+
+void lt_scene_destroy(lt_scene* scene);
+
+/* Primal light tracing (Sec. 3.1; ResLRB primal Sec. 4.2 and its listing; naive AD
+ * forward pass).  image: DEVICE [H][W][3], overwritten.
+ *   estimator LT_EST_PLAIN : splat every valid connection (LRB-3-pass pass 1).
+ *   estimator LT_EST_RESLRB: stream connections into a capacity-1 weighted reservoir
+ *       (Eq. 8) and splat only the winner reweighted by Omega_k/omega_R (Eq. 9); writes
+ *       one record per path into `aux` (DEVICE, n_paths * lt_record_size()).
+ *   estimator LT_EST_NAIVE : splat every connection and write the per-vertex tape into
+ *       `aux` (DEVICE workspace of aux_bytes >= lt_naive_workspace_bytes(opts), else
+ *       LT_ERR_OOM).
+ * path_dbg (optional): [n_paths][4] = (n valid connections, depth reached, 0, 0). */
+lt_status lt_primal(lt_scene* scene, const lt_params* params, const lt_render_opts* opts, int estimator,
+                    float* image, void* aux, size_t aux_bytes, void* stream);
+
+/* LRB-3-pass backward (Sec. 4.3, Eq. 14-19): pass 2 accumulates
+ * delta_total = sum_i Lbar_i * L_i (and in the attached case the positional adjoint),
+ * pass 3 replays again, backpropagates each splat with Lbar_i (Eq. 15), subtracts
+ * (Eq. 16) and backpropagates the scattering factors with delta_rem (Eq. 17).  Both
+ * passes run fused per path; no per-path state reaches global memory.
+ * d_image: DEVICE [H][W][3] adjoint dI.  path_dbg (optional) [n_paths][4] =
+ * (delta_total rgb, n valid connections). */
+lt_status lt_backward_lrb3(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                           const float* d_image, const lt_grads* grads, void* stream);
+
+/* ResLRB backward (Sec. 4.2.1-4.2.2, Eq. 11-13): reads each path's record written by
+ * lt_primal(LT_EST_RESLRB) with the same opts, replays the path up to the selected
+ * vertex R and applies the log-derivative identity weighted by Lbar_R * S, plus the
+ * splat-position channel in the attached case. */
+lt_status lt_backward_reslrb(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                             const float* d_image, const void* records, const lt_grads* grads, void* stream);
+
+/* Naive reverse-mode baseline: reverse sweep over the tape written by
+ * lt_primal(LT_EST_NAIVE) with the same opts (memory linear in max_depth). */
+lt_status lt_backward_naive(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                            const float* d_image, const void* workspace, size_t ws_bytes,
+                            const lt_grads* grads, void* stream);
+
+/* Film pipeline (Sec. 4.3.1 pass 1, "develop, evaluate loss, backpropagate"): L2 loss
+ * loss = sum (I - T)^2 / n and d_image = 2 (I - T) / n over n floats.  DEVICE pointers;
+ * loss: DEVICE [1] (overwritten). */
+lt_status lt_film_l2(const float* image, const float* target, int64_t n, float* d_image, float* loss,
+                     void* stream);
+
+/* Bytes of one ResLRB record (constant per path). */
+size_t lt_record_size(const lt_render_opts* opts);
+/* Bytes of the naive-AD tape for opts (n_paths * max_depth * record). */
+size_t lt_naive_workspace_bytes(const lt_render_opts* opts);
+
+/* Read and clear the scene's device error word (synchronises `stream`). */
+lt_status lt_sync_status(lt_scene* scene, void* stream);
+
+/* Thread-local message describing the last failed call on this thread. */
+const char* lt_last_error(void);
+
+/* Library build string (architecture, version). */
+const char* lt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LT_H */

@@ -1,0 +1,543 @@
+// lt_api.cu -- host side of liblt: argument validation, scene construction (binned-SAH
+// BVH build, flattened to a threaded depth-first layout), device buffers and the
+// extern "C" entry points declared in include/lt.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lt.h"
+#include "lt_device.cuh"
+#include "lt_launch.h"
+
+using namespace lt;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lt_status fail(lt_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define LT_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(LT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct HV {
+  float x, y, z;
+};
+HV hv(float x, float y, float z) { return HV{x, y, z}; }
+HV operator+(HV a, HV b) { return hv(a.x + b.x, a.y + b.y, a.z + b.z); }
+HV operator-(HV a, HV b) { return hv(a.x - b.x, a.y - b.y, a.z - b.z); }
+HV operator*(HV a, float s) { return hv(a.x * s, a.y * s, a.z * s); }
+float hdot(HV a, HV b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+HV hcross(HV a, HV b) { return hv(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+HV hnorm(HV a) { return a * (1.0f / std::sqrt(hdot(a, a))); }
+
+// ------------------------------------------------------------------ BVH build (host)
+struct Box {
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  void grow(const Box& b) {
+    for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], b.lo[k]); hi[k] = std::max(hi[k], b.hi[k]); }
+  }
+  void grow(const float* p) {
+    for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], p[k]); hi[k] = std::max(hi[k], p[k]); }
+  }
+  float area() const {
+    if (hi[0] < lo[0]) return 0.0f;
+    float d0 = hi[0] - lo[0], d1 = hi[1] - lo[1], d2 = hi[2] - lo[2];
+    return 2.0f * (d0 * d1 + d1 * d2 + d2 * d0);
+  }
+};
+
+struct BNode {
+  Box box;
+  int left = -1, right = -1;
+  int begin = 0, end = 0;  // primitive index range in the build order
+};
+
+struct Builder {
+  const std::vector<Box>& pb;
+  std::vector<float> cen;  // [n][3]
+  std::vector<int> idx;
+  std::vector<BNode> nodes;
+  static constexpr int kBins = 16, kMaxLeaf = 8;
+
+  explicit Builder(const std::vector<Box>& boxes) : pb(boxes) {
+    int n = (int)boxes.size();
+    cen.resize(3 * n);
+    idx.resize(n);
+    for (int i = 0; i < n; ++i) {
+      idx[i] = i;
+      for (int k = 0; k < 3; ++k) cen[3 * i + k] = 0.5f * (boxes[i].lo[k] + boxes[i].hi[k]);
+    }
+  }
+
+  int build(int begin, int end, int depth) {
+    int me = (int)nodes.size();
+    nodes.emplace_back();
+    Box b, cb;
+    for (int i = begin; i < end; ++i) { b.grow(pb[idx[i]]); cb.grow(&cen[3 * idx[i]]); }
+    nodes[me].box = b;
+    nodes[me].begin = begin;
+    nodes[me].end = end;
+    int n = end - begin;
+    if (n <= 2 || depth > 60) return me;
+    // binned SAH over the axis of largest centroid extent, then the other axes
+    float best = 3e38f;
+    int best_axis = -1, best_bin = -1;
+    for (int axis = 0; axis < 3; ++axis) {
+      float lo = cb.lo[axis], ext = cb.hi[axis] - cb.lo[axis];
+      if (!(ext > 0)) continue;
+      Box bins[kBins];
+      int cnt[kBins] = {0};
+      for (int i = begin; i < end; ++i) {
+        int bi = std::min(kBins - 1, (int)((cen[3 * idx[i] + axis] - lo) / ext * kBins));
+        bins[bi].grow(pb[idx[i]]);
+        ++cnt[bi];
+      }
+      float rightA[kBins];
+      int rightN[kBins];
+      Box acc;
+      int an = 0;
+      for (int k = kBins - 1; k > 0; --k) {
+        acc.grow(bins[k]);
+        an += cnt[k];
+        rightA[k] = acc.area();
+        rightN[k] = an;
+      }
+      Box lacc;
+      int ln = 0;
+      for (int k = 1; k < kBins; ++k) {
+        lacc.grow(bins[k - 1]);
+        ln += cnt[k - 1];
+        if (ln == 0 || rightN[k] == 0) continue;
+        float cost = lacc.area() * ln + rightA[k] * rightN[k];
+        if (cost < best) { best = cost; best_axis = axis; best_bin = k; }
+      }
+    }
+    float leaf_cost = b.area() * n;
+    const float trav = 1.0f;
+    bool split = best_axis >= 0 && (best + trav * b.area() < leaf_cost || n > kMaxLeaf);
+    if (!split && n <= kMaxLeaf) return me;
+    int mid;
+    if (best_axis >= 0) {
+      float lo = cb.lo[best_axis], ext = cb.hi[best_axis] - cb.lo[best_axis];
+      int* p = std::partition(idx.data() + begin, idx.data() + end, [&](int i) {
+        return std::min(kBins - 1, (int)((cen[3 * i + best_axis] - lo) / ext * kBins)) < best_bin;
+      });
+      mid = (int)(p - idx.data());
+      if (mid == begin || mid == end) mid = begin + n / 2;
+    } else {
+      mid = begin + n / 2;  // coincident centroids: split by count
+    }
+    int l = build(begin, mid, depth + 1);
+    int r = build(mid, end, depth + 1);
+    nodes[me].left = l;
+    nodes[me].right = r;
+    return me;
+  }
+};
+
+}  // namespace
+
+struct lt_scene {
+  DevScene dev{};
+  int device = 0;
+  int n_albedo = 0, n_heights = 0, n_tris_h = 0;
+  bool has_dielectric = false;
+  int sms = 1;
+  // device buffers
+  float4* d_prim = nullptr;
+  int4* d_prim_h = nullptr;
+  float4* d_tri_base = nullptr;
+  float4* d_node = nullptr;
+  int2* d_range = nullptr;
+  int4* d_mat = nullptr;
+  float* d_ior = nullptr;
+  int* d_err = nullptr;
+  int n_nodes = 0, n_prims = 0;
+};
+
+namespace {
+
+void free_scene(lt_scene* s) {
+  if (!s) return;
+  cudaFree(s->d_prim); cudaFree(s->d_prim_h); cudaFree(s->d_tri_base); cudaFree(s->d_node);
+  cudaFree(s->d_range); cudaFree(s->d_mat); cudaFree(s->d_ior); cudaFree(s->d_err);
+  delete s;
+}
+
+lt_status validate_desc(const lt_scene_desc* d) {
+  if (!d) return fail(LT_ERR_INVALID_ARG, "desc is NULL");
+  if (d->n_quads < 1 || !d->quads) return fail(LT_ERR_INVALID_ARG, "need at least one quad (the emitter)");
+  if (d->n_tris < 0 || d->n_verts < 0) return fail(LT_ERR_INVALID_ARG, "negative counts");
+  if (d->n_tris > 0 && (!d->tris || !d->verts || !d->vert_h)) return fail(LT_ERR_INVALID_ARG, "triangle arrays missing");
+  if ((int64_t)d->n_quads + d->n_tris >= (1 << 23)) return fail(LT_ERR_INVALID_ARG, "too many primitives");
+  if (!d->prim_mat || d->n_mats < 1 || !d->mat_type || !d->mat_ior || !d->mat_tex_off || !d->mat_tex_w ||
+      !d->mat_tex_h)
+    return fail(LT_ERR_INVALID_ARG, "material arrays missing");
+  if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384)
+    return fail(LT_ERR_INVALID_ARG, "film size out of range");
+  if (!(d->fov_y_deg > 0 && d->fov_y_deg < 179)) return fail(LT_ERR_INVALID_ARG, "fov_y_deg out of range");
+  if (d->emitter_quad < 0 || d->emitter_quad >= d->n_quads) return fail(LT_ERR_INVALID_ARG, "emitter_quad out of range");
+  for (int i = 0; i < d->n_mats; ++i) {
+    int t = d->mat_type[i];
+    if (t < 0 || t > 2) return fail(LT_ERR_INVALID_ARG, "unknown material type");
+    if (t == LT_MAT_DIFFUSE) {
+      int64_t end = (int64_t)d->mat_tex_off[i] + 3ll * d->mat_tex_w[i] * d->mat_tex_h[i];
+      if (d->mat_tex_w[i] < 1 || d->mat_tex_h[i] < 1 || d->mat_tex_off[i] < 0 || end > d->n_albedo)
+        return fail(LT_ERR_INVALID_ARG, "diffuse texture outside the albedo array");
+    }
+    if (t == LT_MAT_DIELECTRIC && !(d->mat_ior[i] > 0)) return fail(LT_ERR_INVALID_ARG, "ior must be positive");
+  }
+  for (int i = 0; i < d->n_quads + d->n_tris; ++i)
+    if (d->prim_mat[i] < 0 || d->prim_mat[i] >= d->n_mats) return fail(LT_ERR_INVALID_ARG, "prim_mat out of range");
+  if (d->mat_type[d->prim_mat[d->emitter_quad]] != LT_MAT_EMITTER)
+    return fail(LT_ERR_INVALID_ARG, "emitter_quad must have an emitter material");
+  for (int i = 0; i < 3 * d->n_tris; ++i)
+    if (d->tris[i] < 0 || d->tris[i] >= d->n_verts) return fail(LT_ERR_INVALID_ARG, "triangle vertex index out of range");
+  for (int i = 0; i < d->n_verts; ++i)
+    if (d->vert_h[i] < -1 || d->vert_h[i] >= d->n_heights) return fail(LT_ERR_INVALID_ARG, "vert_h out of range");
+  return LT_OK;
+}
+
+LaunchCfg cfg_for(const lt_scene* s, const lt_render_opts* o) {
+  LaunchCfg L;
+  L.block = (o && o->block_size > 0) ? o->block_size : 128;
+  L.blocks_per_sm = (o && o->blocks_per_sm > 0) ? o->blocks_per_sm : 8;
+  L.sms = s->sms;
+  return L;
+}
+
+lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts* o) {
+  if (!s) return fail(LT_ERR_INVALID_ARG, "scene is NULL");
+  if (!p || !p->Le || (s->n_albedo > 0 && !p->albedo)) return fail(LT_ERR_INVALID_ARG, "params missing");
+  if (!o) return fail(LT_ERR_INVALID_ARG, "opts is NULL");
+  if (o->max_depth < 1 || o->max_depth > kMaxDepth) return fail(LT_ERR_INVALID_ARG, "max_depth must be in 1..64");
+  if (o->n_paths < 0 || o->path_offset < 0 || o->n_norm < 0) return fail(LT_ERR_INVALID_ARG, "negative path counts");
+  if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 1024 || o->block_size % 32))
+    return fail(LT_ERR_INVALID_ARG, "block_size must be a multiple of 32 in 32..1024 (or 0)");
+  if (o->block_size > 128) return fail(LT_ERR_INVALID_ARG, "kernels are compiled for at most 128 threads per block");
+  if (o->target == LT_TARGET_MLP) return fail(LT_ERR_UNSUPPORTED, "learned reservoir target not available in this call");
+  if (o->target != LT_TARGET_LUMINANCE) return fail(LT_ERR_INVALID_ARG, "unknown reservoir target");
+  return LT_OK;
+}
+
+KParams kparams(const lt_params* p, const lt_render_opts* o) {
+  KParams k;
+  k.seed = o->seed;
+  k.path_offset = o->path_offset;
+  k.n_paths = o->n_paths;
+  k.max_depth = o->max_depth;
+  k.inv_n = 1.0f / (float)(o->n_norm > 0 ? o->n_norm : (o->n_paths > 0 ? o->n_paths : 1));
+  k.Le = p->Le;
+  k.albedo = p->albedo;
+  k.mask = o->path_mask;
+  k.hash = o->path_hash;
+  k.dbg = o->path_dbg;
+  k.tape_offset = ((size_t)o->n_paths * sizeof(int) + 255) & ~(size_t)255;
+  return k;
+}
+
+lt_status prep_grads(const lt_scene* s, const lt_grads* g, cudaStream_t st, GradPtrs& gp) {
+  if (!g) return fail(LT_ERR_INVALID_ARG, "grads is NULL");
+  gp.d_albedo = g->d_albedo;
+  gp.d_Le = g->d_Le;
+  gp.d_heights = g->d_heights;
+  if (!g->accumulate) {
+    if (g->d_albedo && s->n_albedo) LT_CUDA(cudaMemsetAsync(g->d_albedo, 0, sizeof(float) * s->n_albedo, st));
+    if (g->d_Le) LT_CUDA(cudaMemsetAsync(g->d_Le, 0, sizeof(float) * 3, st));
+    if (g->d_heights && s->n_heights) LT_CUDA(cudaMemsetAsync(g->d_heights, 0, sizeof(float) * s->n_heights, st));
+  }
+  return LT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lt_last_error(void) { return g_last_error.c_str(); }
+
+const char* lt_version(void) { return "liblt 0.1 (sm_103a)"; }
+
+lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) {
+  if (!out) return fail(LT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  lt_status v = validate_desc(d);
+  if (v != LT_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nq = d->n_quads, nt = d->n_tris, np = nq + nt;
+  // host geometry at zero heights
+  std::vector<HV> O(np), E1(np), E2(np);
+  std::vector<Box> boxes(np);
+  for (int i = 0; i < np; ++i) {
+    HV o, e1, e2;
+    if (i < nq) {
+      const float* q = d->quads + 9 * i;
+      o = hv(q[0], q[1], q[2]); e1 = hv(q[3], q[4], q[5]); e2 = hv(q[6], q[7], q[8]);
+    } else {
+      const int* t = d->tris + 3 * (i - nq);
+      HV v0 = hv(d->verts[3 * t[0]], d->verts[3 * t[0] + 1], d->verts[3 * t[0] + 2]);
+      HV v1 = hv(d->verts[3 * t[1]], d->verts[3 * t[1] + 1], d->verts[3 * t[1] + 2]);
+      HV v2 = hv(d->verts[3 * t[2]], d->verts[3 * t[2] + 1], d->verts[3 * t[2] + 2]);
+      o = v0; e1 = v1 - v0; e2 = v2 - v0;
+    }
+    O[i] = o; E1[i] = e1; E2[i] = e2;
+    float pts[4][3] = {{o.x, o.y, o.z}, {o.x + e1.x, o.y + e1.y, o.z + e1.z}, {o.x + e2.x, o.y + e2.y, o.z + e2.z},
+                       {o.x + e1.x + e2.x, o.y + e1.y + e2.y, o.z + e1.z + e2.z}};
+    for (int k = 0; k < (i < nq ? 4 : 3); ++k) boxes[i].grow(pts[k]);
+  }
+  Builder B(boxes);
+  B.build(0, np, 0);
+  // flatten in depth-first preorder; leaves take consecutive slots of the leaf order
+  std::vector<float4> node;
+  std::vector<int2> range;
+  std::vector<int> order;  // leaf order -> original primitive
+  std::vector<int> pre;  // preorder of builder nodes
+  {
+    std::vector<int> stk = {0};
+    while (!stk.empty()) {
+      int b = stk.back();
+      stk.pop_back();
+      pre.push_back(b);
+      if (B.nodes[b].left >= 0) { stk.push_back(B.nodes[b].right); stk.push_back(B.nodes[b].left); }
+    }
+  }
+  int nn = (int)pre.size();
+  std::vector<int> flat_of(B.nodes.size());
+  for (int i = 0; i < nn; ++i) flat_of[pre[i]] = i;
+  // subtree sizes for skip indices
+  std::vector<int> size(B.nodes.size(), 1);
+  for (int i = nn - 1; i >= 0; --i) {
+    const BNode& bn = B.nodes[pre[i]];
+    if (bn.left >= 0) size[pre[i]] = 1 + size[bn.left] + size[bn.right];
+  }
+  node.resize(2 * nn);
+  range.resize(nn);
+  for (int i = 0; i < nn; ++i) {
+    const BNode& bn = B.nodes[pre[i]];
+    int skip = i + size[pre[i]];
+    int leafinfo = 0;
+    if (bn.left < 0) {
+      int first = (int)order.size();
+      for (int k = bn.begin; k < bn.end; ++k) order.push_back(B.idx[k]);
+      leafinfo = (first << 8) | (bn.end - bn.begin);
+    }
+    node[2 * i] = make_float4(bn.box.lo[0], bn.box.lo[1], bn.box.lo[2], 0.0f);
+    node[2 * i + 1] = make_float4(bn.box.hi[0], bn.box.hi[1], bn.box.hi[2], 0.0f);
+    std::memcpy(&node[2 * i].w, &skip, 4);
+    std::memcpy(&node[2 * i + 1].w, &leafinfo, 4);
+  }
+  // prim ranges: the builder kept each subtree contiguous in B.idx and leaves were
+  // emitted in preorder, so build-order positions equal leaf-order positions
+  for (int i = 0; i < nn; ++i) range[i] = make_int2(B.nodes[pre[i]].begin, B.nodes[pre[i]].end);
+  for (int i = 0; i < np; ++i)
+    if (order[i] != B.idx[i]) return fail(LT_ERR_INVALID_ARG, "internal: BVH leaf order mismatch");
+  // leaf-order primitive arrays
+  std::vector<float4> prim(3 * np), tri_base(3 * np, make_float4(0, 0, 0, 0));
+  std::vector<int4> prim_h(np, make_int4(-1, -1, -1, -1));
+  bool has_diel = false;
+  int emitter_leaf = -1;
+  for (int j = 0; j < np; ++j) {
+    int i = order[j];
+    int mat = d->prim_mat[i];
+    int is_tri = i >= nq ? 1 : 0;
+    float fm, fo, ft;
+    std::memcpy(&fm, &mat, 4); std::memcpy(&fo, &i, 4); std::memcpy(&ft, &is_tri, 4);
+    prim[3 * j] = make_float4(O[i].x, O[i].y, O[i].z, fm);
+    prim[3 * j + 1] = make_float4(E1[i].x, E1[i].y, E1[i].z, fo);
+    prim[3 * j + 2] = make_float4(E2[i].x, E2[i].y, E2[i].z, ft);
+    if (is_tri) {
+      const int* t = d->tris + 3 * (i - nq);
+      for (int k = 0; k < 3; ++k)
+        tri_base[3 * j + k] = make_float4(d->verts[3 * t[k]], d->verts[3 * t[k] + 1], d->verts[3 * t[k] + 2], 0.0f);
+      prim_h[j] = make_int4(d->vert_h[t[0]], d->vert_h[t[1]], d->vert_h[t[2]], i);
+    }
+    if (d->mat_type[mat] == LT_MAT_DIELECTRIC) has_diel = true;
+    if (i == d->emitter_quad) emitter_leaf = j;
+  }
+  std::vector<int4> mats(d->n_mats);
+  std::vector<float> iors(d->n_mats);
+  for (int m = 0; m < d->n_mats; ++m) {
+    mats[m] = make_int4(d->mat_type[m], d->mat_tex_off[m], d->mat_tex_w[m], d->mat_tex_h[m]);
+    iors[m] = d->mat_ior[m];
+  }
+  lt_scene* s = new lt_scene();
+  cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  s->n_albedo = d->n_albedo;
+  s->n_heights = d->n_heights;
+  s->has_dielectric = has_diel;
+  s->n_nodes = nn;
+  s->n_prims = np;
+  auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  cudaError_t e = cudaSuccess;
+  if (!e) e = up((void**)&s->d_prim, prim.data(), prim.size() * sizeof(float4));
+  if (!e) e = up((void**)&s->d_prim_h, prim_h.data(), prim_h.size() * sizeof(int4));
+  if (!e) e = up((void**)&s->d_tri_base, tri_base.data(), tri_base.size() * sizeof(float4));
+  if (!e) e = up((void**)&s->d_node, node.data(), node.size() * sizeof(float4));
+  if (!e) e = up((void**)&s->d_range, range.data(), range.size() * sizeof(int2));
+  if (!e) e = up((void**)&s->d_mat, mats.data(), mats.size() * sizeof(int4));
+  if (!e) e = up((void**)&s->d_ior, iors.data(), iors.size() * sizeof(float));
+  if (!e) e = cudaMalloc((void**)&s->d_err, sizeof(int) * 4);
+  if (!e) e = cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, st);
+  if (e) {
+    free_scene(s);
+    return fail(e == cudaErrorMemoryAllocation ? LT_ERR_OOM : LT_ERR_CUDA,
+                std::string("lt_scene_create: ") + cudaGetErrorString(e));
+  }
+  DevScene& S = s->dev;
+  S.prim = s->d_prim; S.prim_h = s->d_prim_h; S.node = s->d_node; S.n_nodes = nn; S.n_prims = np;
+  S.mat = s->d_mat; S.mat_ior = s->d_ior; S.emitter_prim = emitter_leaf; S.err = s->d_err;
+  const float* q = d->quads + 9 * d->emitter_quad;
+  HV lo = hv(q[0], q[1], q[2]), le1 = hv(q[3], q[4], q[5]), le2 = hv(q[6], q[7], q[8]);
+  HV lnr = hcross(le1, le2);
+  HV ln = hnorm(lnr);
+  S.lo = make_float3(lo.x, lo.y, lo.z); S.le1 = make_float3(le1.x, le1.y, le1.z);
+  S.le2 = make_float3(le2.x, le2.y, le2.z); S.ln = make_float3(ln.x, ln.y, ln.z);
+  S.light_area = std::sqrt(hdot(lnr, lnr));
+  HV cp = hv(d->cam_pos[0], d->cam_pos[1], d->cam_pos[2]);
+  HV look = hv(d->cam_look[0], d->cam_look[1], d->cam_look[2]);
+  HV upv = hv(d->cam_up[0], d->cam_up[1], d->cam_up[2]);
+  HV cf = hnorm(look - cp), cr = hnorm(hcross(cf, upv)), cu = hcross(cr, cf);
+  S.cpos = make_float3(cp.x, cp.y, cp.z); S.cf = make_float3(cf.x, cf.y, cf.z);
+  S.cr = make_float3(cr.x, cr.y, cr.z); S.cu = make_float3(cu.x, cu.y, cu.z);
+  double tany = std::tan(0.5 * d->fov_y_deg * 3.14159265358979323846 / 180.0);
+  double tanx = tany * d->width / d->height;
+  S.tanx = (float)tanx; S.tany = (float)tany;
+  S.K0 = (float)((double)d->width * d->height / (4.0 * tanx * tany * 3.14159265358979323846));
+  S.W = d->width; S.H = d->height;
+  // initial bounds
+  RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, nullptr, np, s->d_node, s->d_range, nn};
+  e = launch_refit(ra, st);
+  if (e) { free_scene(s); return fail(LT_ERR_CUDA, std::string("refit: ") + cudaGetErrorString(e)); }
+  *out = s;
+  return LT_OK;
+}
+
+lt_status lt_scene_refit(lt_scene* s, const float* heights, void* stream) {
+  if (!s) return fail(LT_ERR_INVALID_ARG, "scene is NULL");
+  if (s->n_heights > 0 && !heights) return fail(LT_ERR_INVALID_ARG, "heights is NULL");
+  RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, heights, s->n_prims, s->d_node, s->d_range, s->n_nodes};
+  cudaError_t e = launch_refit(ra, (cudaStream_t)stream);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_scene_refit: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+void lt_scene_destroy(lt_scene* s) { free_scene(s); }
+
+size_t lt_record_size(const lt_render_opts*) { return 32; }
+
+size_t lt_naive_workspace_bytes(const lt_render_opts* o) {
+  if (!o || o->n_paths < 0 || o->max_depth < 1) return 0;
+  size_t head = ((size_t)o->n_paths * sizeof(int) + 255) & ~(size_t)255;
+  return head + (size_t)o->n_paths * (size_t)o->max_depth * 32;
+}
+
+lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, int est, float* image, void* aux,
+                    size_t aux_bytes, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!image) return fail(LT_ERR_INVALID_ARG, "image is NULL");
+  if (est < LT_EST_PLAIN || est > LT_EST_NAIVE) return fail(LT_ERR_INVALID_ARG, "unknown estimator");
+  if (est == LT_EST_RESLRB && (!aux || aux_bytes < (size_t)o->n_paths * lt_record_size(o)))
+    return fail(LT_ERR_INVALID_ARG, "ResLRB records buffer missing or too small");
+  if (est == LT_EST_NAIVE && (!aux || aux_bytes < lt_naive_workspace_bytes(o)))
+    return fail(LT_ERR_OOM, "naive-AD workspace missing or smaller than lt_naive_workspace_bytes()");
+  cudaStream_t st = (cudaStream_t)stream;
+  LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
+  if (o->n_paths == 0) return LT_OK;
+  KParams kp = kparams(p, o);
+  cudaError_t e = launch_primal(s->dev, kp, est, image, aux, cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_primal: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts* o, const float* dI,
+                           const lt_grads* g, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!dI) return fail(LT_ERR_INVALID_ARG, "d_image is NULL");
+  if (o->attached && s->has_dielectric) return fail(LT_ERR_UNSUPPORTED, "attached LRB-3 with dielectrics");
+  cudaStream_t st = (cudaStream_t)stream;
+  GradPtrs gp;
+  v = prep_grads(s, g, st, gp);
+  if (v != LT_OK) return v;
+  if (o->n_paths == 0) return LT_OK;
+  cudaError_t e = launch_lrb3(s->dev, kparams(p, o), o->attached != 0, dI, gp, cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_backward_reslrb(lt_scene* s, const lt_params* p, const lt_render_opts* o, const float* dI,
+                             const void* rec, const lt_grads* g, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!dI || !rec) return fail(LT_ERR_INVALID_ARG, "d_image or records is NULL");
+  if (o->attached && s->has_dielectric) return fail(LT_ERR_UNSUPPORTED, "attached ResLRB with dielectrics");
+  cudaStream_t st = (cudaStream_t)stream;
+  GradPtrs gp;
+  v = prep_grads(s, g, st, gp);
+  if (v != LT_OK) return v;
+  if (o->n_paths == 0) return LT_OK;
+  cudaError_t e = launch_reslrb(s->dev, kparams(p, o), o->attached != 0, dI, rec, gp, cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_reslrb: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_backward_naive(lt_scene* s, const lt_params* p, const lt_render_opts* o, const float* dI,
+                            const void* ws, size_t ws_bytes, const lt_grads* g, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!dI) return fail(LT_ERR_INVALID_ARG, "d_image is NULL");
+  if (!ws || ws_bytes < lt_naive_workspace_bytes(o))
+    return fail(LT_ERR_OOM, "naive-AD workspace missing or smaller than lt_naive_workspace_bytes()");
+  if (o->attached && s->has_dielectric) return fail(LT_ERR_UNSUPPORTED, "attached naive AD with dielectrics");
+  cudaStream_t st = (cudaStream_t)stream;
+  GradPtrs gp;
+  v = prep_grads(s, g, st, gp);
+  if (v != LT_OK) return v;
+  if (o->n_paths == 0) return LT_OK;
+  cudaError_t e = launch_naive(s->dev, kparams(p, o), o->attached != 0, dI, ws, gp, cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_naive: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, void* stream) {
+  if (!I || !T || !dI || !loss || n <= 0) return fail(LT_ERR_INVALID_ARG, "lt_film_l2: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  LT_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
+  cudaError_t e = launch_film_l2(I, T, n, dI, loss, sms, st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_film_l2: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_sync_status(lt_scene* s, void* stream) {
+  if (!s) return fail(LT_ERR_INVALID_ARG, "scene is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  LT_CUDA(cudaStreamSynchronize(st));
+  int h = 0;
+  LT_CUDA(cudaMemcpy(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  LT_CUDA(cudaMemset(s->d_err, 0, sizeof(int)));
+  if (h & ERR_TIMEOUT) return fail(LT_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (h) return fail(LT_ERR_DEVICE_CHECK, "device-side check failed (bits " + std::to_string(h) + ")");
+  return LT_OK;
+}
+
+}  // extern "C"

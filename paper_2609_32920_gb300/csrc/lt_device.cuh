@@ -1,0 +1,378 @@
+// lt_device.cuh -- device-side scene layout and per-vertex building blocks of the light
+// tracer (sm_103a).  Everything a light path needs for one vertex: Philox random numbers,
+// emitter sampling, closest-hit and any-hit traversal of a threaded (stackless) BVH,
+// sensor connection with its importance, tent-filter splat/read, dielectric scattering.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lt {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTMin = 1e-5f;  // ray t lower bound (metres), also the shadow-ray end margin
+constexpr int kMaxDepth = 64;
+
+enum { MAT_DIFFUSE = 0, MAT_DIELECTRIC = 1, MAT_EMITTER = 2 };
+enum { K_EMITTER = 0, K_DIFFUSE = 1, K_SPECULAR = 2 };
+
+enum ErrBits : int { ERR_BOUNDS = 1, ERR_TIMEOUT = 2, ERR_NAN = 4 };
+
+// Scene as seen by kernels (passed by value).  Primitives are stored in BVH leaf order:
+//   prim[3i+0] = (o.xyz,  material id as int bits)
+//   prim[3i+1] = (e1.xyz, original primitive id as int bits)
+//   prim[3i+2] = (e2.xyz, 1 if triangle else 0 as int bits)
+//   prim_h[i]  = height-parameter indices of the three triangle vertices (or -1)
+//   node[2j+0] = (lo.xyz, skip index)  node[2j+1] = (hi.xyz, leaf first*256 + count)
+// Threaded BVH in depth-first preorder: the first child of an inner node j is j+1, and
+// `skip` is the next node after j's subtree; leaves have count > 0.
+struct DevScene {
+  const float4* prim;
+  const int4* prim_h;
+  const float4* node;
+  int n_nodes, n_prims;
+  const int4* mat;        // (type, tex_off, tex_w, tex_h)
+  const float* mat_ior;
+  int emitter_prim;       // index in leaf order
+  float3 lo, le1, le2, ln;  // emitter quad and unit normal
+  float light_area;
+  float3 cpos, cf, cr, cu;  // camera position and frame (forward, right, up)
+  float tanx, tany;
+  float K0;               // W * H / (A_img * pi); per call divided by N
+  int W, H;
+  int* err;               // device error word
+};
+
+// ------------------------------------------------------------------ small vector ops
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 mul(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float length(float3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float3 normalize(float3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+__device__ __forceinline__ float hsum(float3 a) { return a.x + a.y + a.z; }
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
+__device__ __forceinline__ uint4 philox(uint32_t k0, uint32_t k1, uint4 c) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+// Four uniforms in [0,1) with 24-bit mantissas for (path n, vertex depth d, stream s).
+__device__ __forceinline__ float4 rand4(uint64_t seed, uint64_t n, uint32_t d, uint32_t s = 0) {
+  uint4 o = philox((uint32_t)seed, (uint32_t)(seed >> 32), make_uint4((uint32_t)n, (uint32_t)(n >> 32), d, s));
+  const float k = 1.0f / 16777216.0f;
+  return make_float4((float)(o.x >> 8) * k, (float)(o.y >> 8) * k, (float)(o.z >> 8) * k, (float)(o.w >> 8) * k);
+}
+
+// Orthonormal basis from a unit normal (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
+  float sign = copysignf(1.0f, n.z);
+  float a = -1.0f / (sign + n.z);
+  float bb = n.x * n.y * a;
+  t = f3(1.0f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+  b = f3(bb, sign + n.y * n.y * a, -n.y);
+}
+// Cosine-weighted direction about n from two uniforms.
+__device__ __forceinline__ float3 cosine_dir(float3 n, float u0, float u1) {
+  float3 t, b;
+  onb(n, t, b);
+  float r = sqrtf(u0), s, c;
+  sincospif(2.0f * u1, &s, &c);
+  return t * (r * c) + b * (r * s) + n * sqrtf(fmaxf(0.0f, 1.0f - u0));
+}
+
+// FNV-1a over the four bytes of x.
+__device__ __forceinline__ void fnv(uint32_t& h, uint32_t x) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { h ^= (x >> (8 * i)) & 0xffu; h *= 16777619u; }
+}
+
+// ------------------------------------------------------------------ primitives
+struct Prim {
+  float3 o, e1, e2;
+  int mat, orig, is_tri;
+};
+__device__ __forceinline__ Prim load_prim(const DevScene& S, int i) {
+  float4 a = __ldg(S.prim + 3 * i), b = __ldg(S.prim + 3 * i + 1), c = __ldg(S.prim + 3 * i + 2);
+  Prim p;
+  p.o = xyz(a); p.e1 = xyz(b); p.e2 = xyz(c);
+  p.mat = __float_as_int(a.w); p.orig = __float_as_int(b.w); p.is_tri = __float_as_int(c.w);
+  return p;
+}
+
+// Moller-Trumbore (1997) for triangles (s,t >= 0, s+t <= 1) and parallelograms (s,t in [0,1]).
+__device__ __forceinline__ bool hit_prim(float3 o, float3 e1, float3 e2, bool tri, float3 org, float3 dir,
+                                         float& t, float& u, float& v) {
+  float3 pv = cross(dir, e2);
+  float det = dot(e1, pv);
+  if (det == 0.0f) return false;
+  float inv = 1.0f / det;
+  float3 tv = org - o;
+  u = dot(tv, pv) * inv;
+  float3 qv = cross(tv, e1);
+  v = dot(dir, qv) * inv;
+  t = dot(e2, qv) * inv;
+  if (tri) return u >= 0.0f && v >= 0.0f && u + v <= 1.0f;
+  return u >= 0.0f && u <= 1.0f && v >= 0.0f && v <= 1.0f;
+}
+
+__device__ __forceinline__ bool hit_box(float4 lo, float4 hi, float3 org, float3 inv, float tmax) {
+  float tx0 = (lo.x - org.x) * inv.x, tx1 = (hi.x - org.x) * inv.x;
+  float ty0 = (lo.y - org.y) * inv.y, ty1 = (hi.y - org.y) * inv.y;
+  float tz0 = (lo.z - org.z) * inv.z, tz1 = (hi.z - org.z) * inv.z;
+  float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+  float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+  return tn <= tf;
+}
+
+__device__ __forceinline__ float3 safe_inv(float3 d) {
+  const float big = 1e30f;
+  return f3(d.x != 0.0f ? 1.0f / d.x : copysignf(big, d.x), d.y != 0.0f ? 1.0f / d.y : copysignf(big, d.y),
+            d.z != 0.0f ? 1.0f / d.z : copysignf(big, d.z));
+}
+
+struct HitRec {
+  int prim;  // leaf-order index, -1 = miss
+  float t, b1, b2;
+};
+
+// Closest hit: smallest t > kTMin, ties to the smaller original primitive id; `skip`
+// (leaf-order index) is the primitive the ray leaves.  Stackless threaded traversal.
+__device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, float3 dir, int skip) {
+  HitRec h;
+  h.prim = -1; h.t = 3.0e38f; h.b1 = 0; h.b2 = 0;
+  int best_orig = 0x7fffffff;
+  float3 inv = safe_inv(dir);
+  int i = 0;
+  while (i < S.n_nodes) {
+    float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
+    int skipi = __float_as_int(lo.w);
+    if (hit_box(lo, hi, org, inv, h.t)) {
+      int leaf = __float_as_int(hi.w);
+      int cnt = leaf & 255;
+      if (cnt) {
+        int first = leaf >> 8;
+        for (int k = first; k < first + cnt; ++k) {
+          if (k == skip) continue;
+          Prim p = load_prim(S, k);
+          float t, u, v;
+          if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
+              (t < h.t || (t == h.t && p.orig < best_orig))) {
+            h.prim = k; h.t = t; h.b1 = u; h.b2 = v; best_orig = p.orig;
+          }
+        }
+        i = skipi;
+      } else {
+        i = i + 1;
+      }
+    } else {
+      i = skipi;
+    }
+  }
+  return h;
+}
+
+// Any hit in (kTMin, dist - kTMin) (sensor-connection visibility).
+__device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 dir, float dist, int skip) {
+  float3 inv = safe_inv(dir);
+  float tmax = dist - kTMin;
+  int i = 0;
+  while (i < S.n_nodes) {
+    float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
+    int skipi = __float_as_int(lo.w);
+    if (hit_box(lo, hi, org, inv, tmax)) {
+      int leaf = __float_as_int(hi.w);
+      int cnt = leaf & 255;
+      if (cnt) {
+        int first = leaf >> 8;
+        for (int k = first; k < first + cnt; ++k) {
+          if (k == skip) continue;
+          Prim p = load_prim(S, k);
+          float t, u, v;
+          if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) return true;
+        }
+        i = skipi;
+      } else {
+        i = i + 1;
+      }
+    } else {
+      i = skipi;
+    }
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ camera / film
+// Film coordinates in pixels (row 0 at the top); false when behind the camera.
+__device__ __forceinline__ bool project(const DevScene& S, float3 x, float& ux, float& uy, float& zc) {
+  float3 d = x - S.cpos;
+  zc = dot(d, S.cf);
+  if (zc <= 0.0f) return false;
+  float px = dot(d, S.cr) / zc, py = dot(d, S.cu) / zc;
+  ux = 0.5f * (float)S.W * (1.0f + px / S.tanx);
+  uy = 0.5f * (float)S.H * (1.0f - py / S.tany);
+  return true;
+}
+
+// Sensor connection at a diffuse vertex x with arrival-side unit normal ns (Sec. 3.1,
+// Eq. 1): valid when the camera lies in the arrival hemisphere, in front of the camera,
+// on the film and unoccluded.  geo = |n . w_c| * W*H / (A_img * pi * r^2 * cos^3 theta_c)
+// (the importance of a pinhole with image plane at distance 1, with the Lambertian 1/pi).
+struct Conn {
+  bool valid;
+  float ux, uy, geo;
+};
+__device__ __forceinline__ Conn connect(const DevScene& S, float3 x, float3 ns, int prim, bool test_vis = true) {
+  Conn c;
+  c.valid = false; c.ux = c.uy = c.geo = 0.0f;
+  float3 cv = S.cpos - x;
+  float dist = length(cv);
+  float3 wc = cv * (1.0f / dist);
+  float cosc = dot(ns, wc);
+  if (!(cosc > 0.0f)) return c;
+  float zc;
+  if (!project(S, x, c.ux, c.uy, zc)) return c;
+  if (!(c.ux >= 0.0f && c.ux < (float)S.W && c.uy >= 0.0f && c.uy < (float)S.H)) return c;
+  if (test_vis && occluded(S, x, wc, dist, prim)) return c;
+  float cc = zc / dist;
+  c.geo = cosc * S.K0 / (dist * dist * cc * cc * cc);
+  c.valid = true;
+  return c;
+}
+
+// Tent (bilinear) reconstruction filter of radius 1 pixel over pixel centres: the two
+// taps per axis around u and their weights; taps off the film are dropped.
+struct Taps {
+  int x0, y0;
+  float fx, fy;
+};
+__device__ __forceinline__ Taps taps(float ux, float uy) {
+  float gx = ux - 0.5f, gy = uy - 0.5f;
+  float x0 = floorf(gx), y0 = floorf(gy);
+  Taps t;
+  t.x0 = (int)x0; t.y0 = (int)y0; t.fx = gx - x0; t.fy = gy - y0;
+  return t;
+}
+
+__device__ __forceinline__ void splat(float* img, int W, int H, float ux, float uy, float3 L) {
+  Taps t = taps(ux, uy);
+  const float wx[2] = {1.0f - t.fx, t.fx}, wy[2] = {1.0f - t.fy, t.fy};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    int Y = t.y0 + j;
+    if (Y < 0 || Y >= H) continue;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int X = t.x0 + i;
+      if (X < 0 || X >= W) continue;
+      float w = wx[i] * wy[j];
+      float* p = img + 3 * ((size_t)Y * W + X);
+      atomicAdd(p + 0, w * L.x);
+      atomicAdd(p + 1, w * L.y);
+      atomicAdd(p + 2, w * L.z);
+    }
+  }
+}
+
+// Filter-weighted adjoint read Lbar = sum_p F(u,p) dI[p] (Eq. 21 with the same filter as
+// the splat) and, when wanted, the position adjoint q = d(Lbar . L)/du (Eq. 20-21).
+__device__ __forceinline__ float3 adjoint_read(const float* dI, int W, int H, float ux, float uy, float3 L,
+                                               float2* q) {
+  Taps t = taps(ux, uy);
+  const float wx[2] = {1.0f - t.fx, t.fx}, wy[2] = {1.0f - t.fy, t.fy};
+  const float sx[2] = {-1.0f, 1.0f};
+  float3 Lb = f3(0, 0, 0);
+  float qx = 0.0f, qy = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    int Y = t.y0 + j;
+    if (Y < 0 || Y >= H) continue;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int X = t.x0 + i;
+      if (X < 0 || X >= W) continue;
+      const float* p = dI + 3 * ((size_t)Y * W + X);
+      float3 v = f3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+      Lb = Lb + v * (wx[i] * wy[j]);
+      float lv = dot(v, L);
+      qx += sx[i] * wy[j] * lv;
+      qy += sx[j] * wx[i] * lv;
+    }
+  }
+  if (q) *q = make_float2(qx, qy);
+  return Lb;
+}
+
+// ------------------------------------------------------------------ materials
+__device__ __forceinline__ float3 texel(const float* albedo, int idx) {
+  return f3(__ldg(albedo + idx), __ldg(albedo + idx + 1), __ldg(albedo + idx + 2));
+}
+// Bilinear lookup at texture coordinates (s,t): texel centres (i+0.5)/w, clamp to edge.
+// Returns the four texel offsets and weights too (for the albedo gradient scatter).
+struct TexFoot {
+  int idx[4];
+  float w[4];
+};
+__device__ __forceinline__ float3 tex_lookup(const float* albedo, int4 m, float s, float t, TexFoot* foot) {
+  int tw = m.z, th = m.w, off = m.y;
+  float tx = s * (float)tw - 0.5f, ty = t * (float)th - 0.5f;
+  float fx0 = floorf(tx), fy0 = floorf(ty);
+  float fx = tx - fx0, fy = ty - fy0;
+  int x0 = (int)fx0, y0 = (int)fy0;
+  int xa = min(max(x0, 0), tw - 1), xb = min(max(x0 + 1, 0), tw - 1);
+  int ya = min(max(y0, 0), th - 1), yb = min(max(y0 + 1, 0), th - 1);
+  int i00 = off + (ya * tw + xa) * 3, i10 = off + (ya * tw + xb) * 3;
+  int i01 = off + (yb * tw + xa) * 3, i11 = off + (yb * tw + xb) * 3;
+  float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
+  if (foot) {
+    foot->idx[0] = i00; foot->idx[1] = i10; foot->idx[2] = i01; foot->idx[3] = i11;
+    foot->w[0] = w00; foot->w[1] = w10; foot->w[2] = w01; foot->w[3] = w11;
+  }
+  return texel(albedo, i00) * w00 + texel(albedo, i10) * w10 + texel(albedo, i01) * w01 + texel(albedo, i11) * w11;
+}
+
+// Smooth dielectric: Fresnel reflectance F for unpolarised light, reflected and
+// refracted directions; `entering` when arriving against the geometric normal n.
+struct Dielectric {
+  float F, ci, ct, eta;
+  bool tir, entering;
+  float3 ns, refl, refr;
+};
+__device__ __forceinline__ Dielectric dielectric(float3 din, float3 n, float ior) {
+  Dielectric D;
+  D.entering = dot(din, n) < 0.0f;
+  D.ns = D.entering ? n : -n;
+  D.eta = D.entering ? 1.0f / ior : ior;
+  D.ci = -dot(din, D.ns);
+  D.refl = din + D.ns * (2.0f * D.ci);
+  float s2t = D.eta * D.eta * (1.0f - D.ci * D.ci);
+  D.tir = s2t >= 1.0f;
+  if (D.tir) { D.F = 1.0f; D.ct = 0.0f; D.refr = D.refl; return D; }
+  D.ct = sqrtf(1.0f - s2t);
+  float rs = (D.eta * D.ci - D.ct) / (D.eta * D.ci + D.ct);
+  float rp = (D.ci - D.eta * D.ct) / (D.ci + D.eta * D.ct);
+  D.F = 0.5f * (rs * rs + rp * rp);
+  D.refr = din * D.eta + D.ns * (D.eta * D.ci - D.ct);
+  return D;
+}
+
+__device__ __forceinline__ float luminance(float3 L) { return 0.2126f * L.x + 0.7152f * L.y + 0.0722f * L.z; }
+
+__device__ __forceinline__ void set_err(const DevScene& S, int bit) { atomicOr(S.err, bit); }
+
+}  // namespace lt

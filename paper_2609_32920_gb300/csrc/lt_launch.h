@@ -1,0 +1,60 @@
+// lt_launch.h -- internal interface between the C-ABI host code and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lt {
+
+struct DevScene;
+
+// Per-call kernel parameters (by value).
+struct KParams {
+  uint64_t seed;
+  int64_t path_offset;
+  int64_t n_paths;
+  int max_depth;
+  float inv_n;               // 1 / N of the estimator
+  const float* Le;           // DEVICE [3]
+  const float* albedo;       // DEVICE [n_albedo]
+  const uint8_t* mask;       // DEVICE [n_paths] or null
+  uint32_t* hash;            // DEVICE [n_paths] or null
+  float* dbg;                // DEVICE [n_paths][4] or null
+  size_t tape_offset;        // naive tape: bytes before the first record
+};
+
+struct GradPtrs {
+  float* d_albedo;
+  float* d_Le;
+  float* d_heights;
+};
+
+struct LaunchCfg {
+  int block;
+  int blocks_per_sm;
+  int sms;
+};
+
+struct RefitArgs {
+  float4* prim;
+  const int4* prim_h;
+  const float4* tri_base;
+  const float* heights;
+  int n_prims;
+  float4* node;
+  const int2* range;
+  int n_nodes;
+};
+
+cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
+cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux,
+                          const LaunchCfg& L, cudaStream_t st);
+cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, const float* dI, const GradPtrs& g,
+                        const LaunchCfg& L, cudaStream_t st);
+cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, const float* dI, const void* rec,
+                          const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, const float* dI, const void* ws,
+                         const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,
+                           cudaStream_t st);
+
+}  // namespace lt

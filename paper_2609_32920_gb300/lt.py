@@ -1,0 +1,265 @@
+"""Thin Python binding of liblt (include/lt.h): argument marshalling only.
+
+Every step of the light-tracing path runs in the library's CUDA kernels; PyTorch only
+supplies device memory and the current CUDA stream.  There is no CPU fallback: if the
+compiled library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import inputs as _inputs
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblt.so")
+
+LT_OK, LT_ERR_INVALID_ARG, LT_ERR_OOM, LT_ERR_CUDA, LT_ERR_TIMEOUT, LT_ERR_DEVICE_CHECK, LT_ERR_UNSUPPORTED = range(7)
+EST_PLAIN, EST_RESLRB, EST_NAIVE = 0, 1, 2
+TARGET_LUMINANCE, TARGET_MLP = 0, 1
+STATUS_NAMES = {0: "LT_OK", 1: "LT_ERR_INVALID_ARG", 2: "LT_ERR_OOM", 3: "LT_ERR_CUDA", 4: "LT_ERR_TIMEOUT",
+                5: "LT_ERR_DEVICE_CHECK", 6: "LT_ERR_UNSUPPORTED"}
+
+
+class LTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+F3 = C.c_float * 3
+
+
+class lt_scene_desc(C.Structure):
+    _fields_ = [("n_quads", C.c_int), ("quads", C.c_void_p), ("n_verts", C.c_int), ("verts", C.c_void_p),
+                ("vert_h", C.c_void_p), ("n_tris", C.c_int), ("tris", C.c_void_p), ("prim_mat", C.c_void_p),
+                ("n_mats", C.c_int), ("mat_type", C.c_void_p), ("mat_ior", C.c_void_p),
+                ("mat_tex_off", C.c_void_p), ("mat_tex_w", C.c_void_p), ("mat_tex_h", C.c_void_p),
+                ("emitter_quad", C.c_int), ("cam_pos", F3), ("cam_look", F3), ("cam_up", F3),
+                ("fov_y_deg", C.c_float), ("width", C.c_int), ("height", C.c_int), ("n_albedo", C.c_int),
+                ("n_heights", C.c_int)]
+
+
+class lt_params(C.Structure):
+    _fields_ = [("albedo", C.c_void_p), ("Le", C.c_void_p)]
+
+
+class lt_render_opts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("path_offset", C.c_int64), ("n_paths", C.c_int64), ("n_norm", C.c_int64),
+                ("max_depth", C.c_int), ("attached", C.c_int), ("target", C.c_int), ("mlp", C.c_void_p),
+                ("block_size", C.c_int), ("blocks_per_sm", C.c_int), ("path_mask", C.c_void_p),
+                ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p)]
+
+
+class lt_grads(C.Structure):
+    _fields_ = [("d_albedo", C.c_void_p), ("d_Le", C.c_void_p), ("d_heights", C.c_void_p), ("accumulate", C.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# Every symbol include/lt.h declares (checked by the CPU test-suite against the .so).
+EXPORTS = ["lt_scene_create", "lt_scene_refit", "lt_scene_destroy", "lt_primal", "lt_backward_lrb3",
+           "lt_backward_reslrb", "lt_backward_naive", "lt_film_l2", "lt_record_size", "lt_naive_workspace_bytes",
+           "lt_sync_status", "lt_last_error", "lt_version"]
+
+
+def lib():
+    """Load liblt.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise LTError(LT_ERR_UNSUPPORTED, f"{LIB_PATH} is missing: build it with paper_2609_32920_gb300.build")
+            L = C.CDLL(LIB_PATH)
+            P, V = C.POINTER, C.c_void_p
+            L.lt_scene_create.argtypes = [P(lt_scene_desc), V, P(V)]
+            L.lt_scene_refit.argtypes = [V, V, V]
+            L.lt_scene_destroy.argtypes = [V]
+            L.lt_scene_destroy.restype = None
+            L.lt_primal.argtypes = [V, P(lt_params), P(lt_render_opts), C.c_int, V, V, C.c_size_t, V]
+            L.lt_backward_lrb3.argtypes = [V, P(lt_params), P(lt_render_opts), V, P(lt_grads), V]
+            L.lt_backward_reslrb.argtypes = [V, P(lt_params), P(lt_render_opts), V, V, P(lt_grads), V]
+            L.lt_backward_naive.argtypes = [V, P(lt_params), P(lt_render_opts), V, V, C.c_size_t, P(lt_grads), V]
+            L.lt_film_l2.argtypes = [V, V, C.c_int64, V, V, V]
+            L.lt_record_size.argtypes = [P(lt_render_opts)]
+            L.lt_record_size.restype = C.c_size_t
+            L.lt_naive_workspace_bytes.argtypes = [P(lt_render_opts)]
+            L.lt_naive_workspace_bytes.restype = C.c_size_t
+            L.lt_sync_status.argtypes = [V, V]
+            L.lt_last_error.restype = C.c_char_p
+            L.lt_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != LT_OK:
+        raise LTError(status, lib().lt_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Scene:
+    """A scene on the current CUDA device: geometry + BVH in liblt, parameters as torch tensors."""
+
+    def __init__(self, sc: "_inputs.Scene", device=None, stream=None):
+        if not torch.cuda.is_available():
+            raise LTError(LT_ERR_UNSUPPORTED, "liblt needs a CUDA device")
+        self.src = sc
+        self.device = torch.device(device or "cuda")
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        d = lt_scene_desc()
+        d.n_quads = sc.n_quads
+        d.quads = arr(sc.quads.reshape(-1), np.float32)
+        d.n_verts = int(sc.verts.shape[0])
+        d.verts = arr(sc.verts.reshape(-1), np.float32) if sc.verts.size else None
+        d.vert_h = arr(sc.vert_h, np.int32) if sc.vert_h.size else None
+        d.n_tris = sc.n_tris
+        d.tris = arr(sc.tris.reshape(-1), np.int32) if sc.tris.size else None
+        d.prim_mat = arr(sc.prim_mat, np.int32)
+        d.n_mats = int(sc.mat_type.size)
+        d.mat_type = arr(sc.mat_type, np.int32)
+        d.mat_ior = arr(sc.mat_ior, np.float32)
+        d.mat_tex_off = arr(sc.mat_tex_off, np.int32)
+        d.mat_tex_w = arr(sc.mat_tex_w, np.int32)
+        d.mat_tex_h = arr(sc.mat_tex_h, np.int32)
+        d.emitter_quad = sc.emitter_quad
+        d.cam_pos = F3(*sc.cam_pos)
+        d.cam_look = F3(*sc.cam_look)
+        d.cam_up = F3(*sc.cam_up)
+        d.fov_y_deg = sc.fov_y_deg
+        d.width, d.height = sc.W, sc.H
+        d.n_albedo = int(sc.albedo.size)
+        d.n_heights = int(sc.heights.size)
+        self.W, self.H = sc.W, sc.H
+        self.n_albedo, self.n_heights = d.n_albedo, d.n_heights
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().lt_scene_create(C.byref(d), _stream(stream), C.byref(h)))
+        self._h = h
+        f32 = dict(device=self.device, dtype=torch.float32)
+        self.albedo = torch.tensor(sc.albedo, **f32) if sc.albedo.size else torch.zeros(1, **f32)
+        self.Le = torch.tensor(sc.Le, **f32)
+        self.heights = torch.tensor(sc.heights, **f32) if sc.heights.size else torch.zeros(1, **f32)
+        if self.n_heights:
+            self.refit(self.heights, stream)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            try:
+                torch.cuda.synchronize(self.device)
+            except Exception:
+                pass
+            _lib.lt_scene_destroy(h)
+            self._h = None
+
+    # ------------------------------------------------------------------ calls
+    def refit(self, heights, stream=None):
+        heights = heights.contiguous()
+        self.heights = heights
+        _check(lib().lt_scene_refit(self._h, _ptr(heights), _stream(stream)))
+
+    def params(self, albedo=None, Le=None):
+        a = (albedo if albedo is not None else self.albedo).contiguous()
+        le = (Le if Le is not None else self.Le).contiguous()
+        self._keep_params = (a, le)
+        return lt_params(a.data_ptr(), le.data_ptr())
+
+    @staticmethod
+    def opts(seed=0, n_paths=1 << 14, max_depth=4, attached=0, path_offset=0, n_norm=0, block_size=0,
+             blocks_per_sm=0, mask=None, hash_out=None, dbg_out=None, target=TARGET_LUMINANCE, mlp=None):
+        o = lt_render_opts()
+        o.seed, o.path_offset, o.n_paths, o.n_norm = int(seed), int(path_offset), int(n_paths), int(n_norm)
+        o.max_depth, o.attached, o.target = int(max_depth), int(attached), int(target)
+        o.mlp = None if mlp is None else mlp.data_ptr()
+        o.block_size, o.blocks_per_sm = int(block_size), int(blocks_per_sm)
+        o.path_mask = None if mask is None else mask.data_ptr()
+        o.path_hash = None if hash_out is None else hash_out.data_ptr()
+        o.path_dbg = None if dbg_out is None else dbg_out.data_ptr()
+        return o
+
+    def record_size(self, o) -> int:
+        return int(lib().lt_record_size(C.byref(o)))
+
+    def naive_workspace_bytes(self, o) -> int:
+        return int(lib().lt_naive_workspace_bytes(C.byref(o)))
+
+    def new_image(self):
+        return torch.empty((self.H, self.W, 3), device=self.device, dtype=torch.float32)
+
+    def primal(self, o, estimator=EST_PLAIN, image=None, aux=None, albedo=None, Le=None, stream=None):
+        img = image if image is not None else self.new_image()
+        p = self.params(albedo, Le)
+        nbytes = 0 if aux is None else aux.numel() * aux.element_size()
+        _check(lib().lt_primal(self._h, C.byref(p), C.byref(o), int(estimator), _ptr(img), _ptr(aux), nbytes,
+                               _stream(stream)))
+        return img
+
+    def _grads(self, d_albedo, d_Le, d_heights, accumulate):
+        return lt_grads(None if d_albedo is None else d_albedo.data_ptr(), None if d_Le is None else d_Le.data_ptr(),
+                        None if d_heights is None else d_heights.data_ptr(), int(accumulate))
+
+    def new_grads(self):
+        f32 = dict(device=self.device, dtype=torch.float32)
+        return (torch.zeros(max(1, self.n_albedo), **f32), torch.zeros(3, **f32),
+                torch.zeros(max(1, self.n_heights), **f32))
+
+    def backward_lrb3(self, o, d_image, grads=None, accumulate=False, albedo=None, Le=None, stream=None):
+        g = grads if grads is not None else self.new_grads()
+        p = self.params(albedo, Le)
+        gr = self._grads(*g, accumulate)
+        _check(lib().lt_backward_lrb3(self._h, C.byref(p), C.byref(o), _ptr(d_image.contiguous()), C.byref(gr),
+                                      _stream(stream)))
+        return g
+
+    def backward_reslrb(self, o, d_image, records, grads=None, accumulate=False, albedo=None, Le=None, stream=None):
+        g = grads if grads is not None else self.new_grads()
+        p = self.params(albedo, Le)
+        gr = self._grads(*g, accumulate)
+        _check(lib().lt_backward_reslrb(self._h, C.byref(p), C.byref(o), _ptr(d_image.contiguous()), _ptr(records),
+                                        C.byref(gr), _stream(stream)))
+        return g
+
+    def backward_naive(self, o, d_image, workspace, grads=None, accumulate=False, albedo=None, Le=None, stream=None):
+        g = grads if grads is not None else self.new_grads()
+        p = self.params(albedo, Le)
+        gr = self._grads(*g, accumulate)
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().lt_backward_naive(self._h, C.byref(p), C.byref(o), _ptr(d_image.contiguous()), _ptr(workspace),
+                                       nbytes, C.byref(gr), _stream(stream)))
+        return g
+
+    def sync_status(self, stream=None):
+        _check(lib().lt_sync_status(self._h, _stream(stream)))
+
+
+def film_l2(image, target, d_image=None, loss=None, stream=None):
+    """L2 film loss and its image adjoint (lt_film_l2)."""
+    d = d_image if d_image is not None else torch.empty_like(image)
+    l = loss if loss is not None else torch.empty(1, device=image.device, dtype=torch.float32)
+    _check(lib().lt_film_l2(_ptr(image.contiguous()), _ptr(target.contiguous()), image.numel(), _ptr(d), _ptr(l),
+                            _stream(stream)))
+    return l, d
+
+
+def version() -> str:
+    return lib().lt_version().decode()

@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/lt.h
+declares; host-only calls and argument validation work without a GPU (CPU only)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def liblt():
+    from paper_2609_32920_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lt_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(liblt):
+    syms = declared_symbols()
+    assert len(syms) >= 13
+    for s in syms:
+        assert hasattr(liblt, s), f"{s} declared in lt.h but not exported"
+    from paper_2609_32920_gb300 import lt
+    assert sorted(lt.EXPORTS) == syms
+
+
+def test_built_for_sm_103a():
+    from paper_2609_32920_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_host_only_calls(liblt):
+    from paper_2609_32920_gb300 import lt
+    liblt.lt_version.restype = C.c_char_p
+    assert b"sm_103a" in liblt.lt_version()
+    o = lt.lt_render_opts()
+    o.n_paths, o.max_depth = 1000, 16
+    liblt.lt_record_size.restype = C.c_size_t
+    liblt.lt_naive_workspace_bytes.restype = C.c_size_t
+    assert liblt.lt_record_size(C.byref(o)) == 32
+    assert liblt.lt_naive_workspace_bytes(C.byref(o)) == 4096 + 1000 * 16 * 32
+
+
+def test_argument_validation_without_gpu(liblt):
+    liblt.lt_last_error.restype = C.c_char_p
+    out = C.c_void_p()
+    assert liblt.lt_scene_create(None, None, C.byref(out)) == 1
+    assert b"desc" in liblt.lt_last_error()
+    assert liblt.lt_scene_create(None, None, None) == 1
+    assert liblt.lt_primal(None, None, None, 0, None, None, 0, None) == 1
+    assert liblt.lt_backward_lrb3(None, None, None, None, None, None) == 1
+    assert liblt.lt_backward_reslrb(None, None, None, None, None, None, None) == 1
+    assert liblt.lt_backward_naive(None, None, None, None, None, 0, None, None) == 1
+    assert liblt.lt_film_l2(None, None, 0, None, None, None) == 1
+    assert liblt.lt_scene_refit(None, None, None) == 1
+    assert liblt.lt_sync_status(None, None) == 1

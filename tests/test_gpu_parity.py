@@ -1,0 +1,198 @@
+"""GPU (liblt, CUDA) vs FP64 oracle on the same seeded inputs.
+
+Tolerances: primal pixels |a-b| <= 1e-4 max(|b|, 1e-3 mean|b|); per-seed gradients
+relative L2 <= 1e-3; discrete decisions (hashes, reservoir winners, connection counts)
+bit-exact on every path whose decisions agree (paths whose FP32 and FP64 decisions
+differ are counted, bounded, and masked out on both sides)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2609_32920_gb300 import inputs as I
+from paper_2609_32920_gb300 import lt
+from tests.gpu_util import agree_mask, primal_close, rel_l2, t32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def box64():
+    sc = I.box_scene(64)
+    return sc, lt.Scene(sc)
+
+
+@pytest.fixture(scope="module")
+def boxhm():
+    sc = I.box_scene(64, heightmap=8, hm_std=0.03)
+    return sc, lt.Scene(sc)
+
+
+def _dev_mask(m):
+    return torch.tensor(m, dtype=torch.uint8, device="cuda")
+
+
+@pytest.mark.parametrize("seed,n,D", [(0, 1 << 14, 4), (3, 5000, 7)])
+def test_primal_matches_oracle(box64, seed, n, D):
+    sc, S = box64
+    mask = agree_mask(S, sc, seed, n, D)
+    img = S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask))).cpu().numpy()
+    ref = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask)
+    ok = primal_close(img, ref)
+    assert ok.all(), f"{(~ok).sum()} pixels off; max rel {np.abs(img - ref).max() / np.abs(ref).max()}"
+
+
+def test_primal_connection_counts_exact(box64):
+    sc, S = box64
+    n, D = 1 << 13, 6
+    dbg = torch.zeros((n, 4), device="cuda")
+    S.primal(S.opts(seed=5, n_paths=n, max_depth=D, dbg_out=dbg))
+    ref = O.gradient(sc, I.smooth_adjoint(sc.W, sc.H, 0), seed=5, n_paths=n, max_depth=D, want_dbg=True,
+                     want_hash=True)
+    mask = agree_mask(S, sc, 5, n, D).astype(bool)
+    assert np.array_equal(dbg.cpu().numpy()[mask, 0], ref["dbg"][mask, 3])
+
+
+@pytest.mark.parametrize("seed,D", [(0, 4), (1, 12)])
+def test_lrb3_detached_matches_naive_ad(box64, seed, D):
+    sc, S = box64
+    n = 1 << 14
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 10 + seed)
+    mask = agree_mask(S, sc, seed, n, D)
+    dbg = torch.zeros((n, 4), device="cuda")
+    gA, gL, _ = S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask), dbg_out=dbg),
+                                t32(dI_np))
+    ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, mask=mask, want_dbg=True)
+    assert rel_l2(gA.cpu().numpy(), ref["d_albedo"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+    m = mask.astype(bool)
+    d = dbg.cpu().numpy()
+    assert np.array_equal(d[m, 3], ref["dbg"][m, 3])  # connection counts per path
+    assert rel_l2(d[m, :3], ref["dbg"][m, :3]) < 1e-4  # delta_total per path (Eq. 14)
+
+
+def test_reslrb_detached_records_and_gradient(box64):
+    sc, S = box64
+    n, D, seed = 1 << 14, 8, 2
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 21)
+    mask = agree_mask(S, sc, seed, n, D)
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask))
+    rec = torch.zeros((n, 8), device="cuda")
+    img = S.primal(o, estimator=lt.EST_RESLRB, aux=rec).cpu().numpy()
+    ref_img, ref_rec = O.render(sc, seed=seed, n_paths=n, max_depth=D, estimator=1, mask=mask, want_records=True)
+    r = rec.cpu().numpy()
+    R = r[:, 0].view(np.int32)
+    m = mask.astype(bool)
+    assert np.array_equal(R[m], ref_rec[m, 0].astype(np.int32)), "reservoir winners differ"
+    sel = m & (R >= 0)
+    assert np.allclose(r[sel, 1], ref_rec[sel, 1], rtol=1e-5)          # Omega / omega_R
+    assert np.allclose(r[sel, 2:4], ref_rec[sel, 2:4], rtol=0, atol=1e-3)  # u_R (pixels)
+    assert rel_l2(r[sel, 4:7], ref_rec[sel, 4:7]) < 1e-5                # S
+    assert primal_close(img, ref_img).all()
+    gA, gL, _ = S.backward_reslrb(o, t32(dI_np), rec)
+    refg = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, method=O.RESLRB_AD, mask=mask)
+    assert rel_l2(gA.cpu().numpy(), refg["d_albedo"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), refg["d_Le"]) < 1e-3
+
+
+def test_naive_detached_matches_oracle(box64):
+    sc, S = box64
+    n, D, seed = 1 << 14, 6, 4
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 31)
+    mask = agree_mask(S, sc, seed, n, D)
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask))
+    ws = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device="cuda")
+    S.primal(o, estimator=lt.EST_NAIVE, aux=ws)
+    gA, gL, _ = S.backward_naive(o, t32(dI_np), ws)
+    ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, mask=mask)
+    assert rel_l2(gA.cpu().numpy(), ref["d_albedo"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+
+
+@pytest.mark.parametrize("method", ["lrb3", "reslrb", "naive"])
+def test_attached_height_field_matches_oracle(boxhm, method):
+    sc, S = boxhm
+    n, D, seed = 1 << 14, 6, 6
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 41)
+    mask = agree_mask(S, sc, seed, n, D)
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask))
+    dI = t32(dI_np)
+    if method == "lrb3":
+        gA, gL, gH = S.backward_lrb3(o, dI)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
+    elif method == "reslrb":
+        rec = torch.zeros((n, 8), device="cuda")
+        S.primal(o, estimator=lt.EST_RESLRB, aux=rec)
+        gA, gL, gH = S.backward_reslrb(o, dI, rec)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, method=O.RESLRB_AD, mask=mask)
+    else:
+        ws = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device="cuda")
+        S.primal(o, estimator=lt.EST_NAIVE, aux=ws)
+        gA, gL, gH = S.backward_naive(o, dI, ws)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
+    assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+    assert rel_l2(gA.cpu().numpy(), ref["d_albedo"]) < 1e-3
+
+
+def test_ragged_offset_and_depth_limits(box64):
+    sc, S = box64
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 51)
+    for n, off, D in [(1, 0, 1), (1000, 12345, 5), (777, (1 << 33) + 5, 64)]:
+        mask = agree_mask(S, sc, 9, n, D, path_offset=off, n_norm=1 << 20)
+        o = S.opts(seed=9, n_paths=n, max_depth=D, path_offset=off, n_norm=1 << 20, mask=_dev_mask(mask))
+        img = S.primal(o).cpu().numpy()
+        ref = O.render(sc, seed=9, n_paths=n, max_depth=D, path_begin=off, n_norm=1 << 20, mask=mask)
+        assert primal_close(img, ref).all()
+        gA, gL, _ = S.backward_lrb3(o, t32(dI_np))
+        r = O.gradient(sc, dI_np, seed=9, n_paths=n, max_depth=D, path_begin=off, n_norm=1 << 20, mask=mask)
+        assert rel_l2(gA.cpu().numpy(), r["d_albedo"]) < 1e-3
+
+
+def test_empty_and_degenerate_inputs(box64):
+    sc, S = box64
+    o = S.opts(seed=0, n_paths=0, max_depth=4)
+    img = S.primal(o)
+    assert float(img.abs().sum()) == 0.0
+    gA, gL, _ = S.backward_lrb3(o, torch.ones((sc.H, sc.W, 3), device="cuda"))
+    assert float(gA.abs().sum()) == 0 and float(gL.abs().sum()) == 0
+    # camera facing away: no connection is ever valid, so image and gradients vanish
+    away = I.box_scene(16)
+    away.cam_look = np.array([0.5, 0.5, -3.0])
+    S2 = lt.Scene(away)
+    o = S2.opts(seed=1, n_paths=4096, max_depth=4)
+    assert float(S2.primal(o).abs().sum()) == 0.0
+    gA, gL, _ = S2.backward_lrb3(o, torch.ones((16, 16, 3), device="cuda"))
+    assert float(gA.abs().sum()) == 0.0
+    # zero adjoint: zero gradient
+    gA, gL, _ = S.backward_lrb3(S.opts(seed=0, n_paths=4096, max_depth=4), torch.zeros((sc.H, sc.W, 3), device="cuda"))
+    assert float(gA.abs().sum()) == 0.0
+
+
+def test_invalid_arguments_raise(box64):
+    sc, S = box64
+    with pytest.raises(lt.LTError) as e:
+        S.primal(S.opts(n_paths=16, max_depth=0))
+    assert e.value.status == lt.LT_ERR_INVALID_ARG
+    with pytest.raises(lt.LTError):
+        S.primal(S.opts(n_paths=16, max_depth=65))
+    o = S.opts(n_paths=1024, max_depth=8)
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lt.LTError) as e:
+        S.primal(o, estimator=lt.EST_NAIVE, aux=small)
+    assert e.value.status == lt.LT_ERR_OOM
+    with pytest.raises(lt.LTError) as e:
+        S.primal(o, estimator=lt.EST_RESLRB, aux=None)
+    assert e.value.status == lt.LT_ERR_INVALID_ARG
+    S.sync_status()
+
+
+def test_film_l2_kernel():
+    torch.manual_seed(0)
+    I_ = torch.rand(64, 64, 3, device="cuda")
+    T = torch.rand(64, 64, 3, device="cuda")
+    loss, d = lt.film_l2(I_, T)
+    n = I_.numel()
+    ref_loss = float(((I_.double() - T.double()) ** 2).sum() / n)
+    assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
+    assert torch.allclose(d, 2 * (I_ - T) / n, rtol=1e-6, atol=1e-12)
