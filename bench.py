@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark: adjoint light paths per second of constant-memory differentiable light
+tracing (LRB-3-pass, attached) on the box + 32x32 height-field workload.
+
+One step = one pass of the hot path over one batch of 2^22 light paths at depth 16:
+  refit the height field's triangles and BVH bounds (2 kernels)
+  -> primal light tracing with sensor connection and splat at every vertex (1 kernel)
+  -> film L2 loss and image adjoint (1 kernel)
+  -> LRB-3-pass backward, passes 2 and 3 fused, attached gradients w.r.t. the emitted
+     radiance and every height-field vertex height including the splat-position
+     derivative (1 kernel).
+Inputs are seeded and synthetic (see paper_2609_32920_gb300.inputs).  `value` is
+device-timed with inputs resident in HBM; `e2e` adds the host->device copy of the step's
+inputs and the device->host copy of loss and gradients.  The ResLRB and naive-AD
+pipelines and the peak device memory of each method versus depth are reported alongside.
+
+`--impl reference` times the FP64 CPU oracle (naive tape AD) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "box256_hm32"
+N_PATHS = 1 << 22
+DEPTH = 16
+METRIC = "adjoint light paths/s (LRB-3-pass attached: refit + primal + film + backward)"
+FLOPS_PER = {"node": 24, "prim": 30, "vertex": 150, "conn": 100}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-method and memory-vs-depth sweep")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
+    ap.add_argument("--paths-log2", type=int, default=22, help="paths per GPU per step (profiling uses fewer)")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling run: only warm-up and timed steps (no e2e, census, sweep or CPU baseline)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks sampler
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_sample(sc, dI, seconds: float, attached: int = 1):
+    """Time the FP64 oracle (naive tape AD) on a bounded sample of the workload's paths."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    n = 64
+    t0 = time.perf_counter()
+    O.gradient(sc, dI, seed=0, n_paths=n, max_depth=DEPTH, attached=attached, n_norm=N_PATHS, n_threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(1 << 16, max(256, n * seconds / dt)))
+    t0 = time.perf_counter()
+    O.gradient(sc, dI, seed=0, n_paths=n, max_depth=DEPTH, attached=attached, n_norm=N_PATHS, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return n, dt, cores
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    from paper_2609_32920_gb300 import inputs as I
+    sc = I.box_scene(256, heightmap=32)
+    dI = I.smooth_adjoint(sc.W, sc.H, 1)
+    # size one step's sample so that the whole warmup + steps run stays within a few minutes
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    n, dt, cores = oracle_sample(sc, dI, per_step)
+    from oracle import oracle as O
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.gradient(sc, dI, seed=i, n_paths=n, max_depth=DEPTH, attached=1, n_norm=N_PATHS, n_threads=cores)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = n / mean
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "paths_per_step": n, "max_depth": DEPTH, "resolution": 256,
+                       "heightmap": 32, "method": "naive tape reverse-mode AD (FP64 CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} of {N_PATHS} paths per step, attached naive AD, FP64"},
+            "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+
+    global N_PATHS
+    N_PATHS = 1 << args.paths_log2
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2609_32920_gb300 import inputs as I
+    from paper_2609_32920_gb300 import lt
+
+    sc = I.box_scene(256, heightmap=32)
+    S = lt.Scene(sc)
+    W, H = sc.W, sc.H
+    path_offset = rank * N_PATHS  # weak scaling: each rank traces its own 2^22 paths
+    # target image: the same scene with perturbed albedo and heights (rendered by liblt)
+    tgt_sc = sc.with_params(albedo=I.perturbed_albedo(sc, 0.05, 1), heights=sc.heights * 0.5)
+    T_S = lt.Scene(tgt_sc)
+    target = T_S.primal(T_S.opts(seed=12345, n_paths=N_PATHS, max_depth=DEPTH))
+    del T_S
+    heights = S.heights.clone()
+    o_plain = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, path_offset=path_offset, n_norm=N_PATHS * ws)
+    o_att = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset,
+                   n_norm=N_PATHS * ws)
+    img = S.new_image()
+    dI = torch.empty_like(img)
+    loss = torch.empty(1, device=dev)
+    grads = S.new_grads()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+    launches_per_step = 5  # update_tris, refit_nodes, primal, film_l2, lrb3
+
+    def step(bwd_events=None):
+        S.refit(heights)
+        S.primal(o_plain, image=img)
+        lt.film_l2(img, target, d_image=dI, loss=loss)
+        if bwd_events:
+            bwd_events[0].record(stream)
+        S.backward_lrb3(o_att, dI, grads=grads)
+        if bwd_events:
+            bwd_events[1].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    S.sync_status()
+    clocks = Clocks(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)  # evict L2 between timed steps (outside the timed interval)
+        ev[i][0].record(stream)
+        step(bev[i])
+        ev[i][1].record(stream)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    bwd_ms = [a.elapsed_time(b) for a, b in bev]
+    total_ms = sum(step_ms)
+    if args.profile:
+        clocks.stop()
+        if rank == 0:
+            print(json.dumps({"profile": True, "paths": N_PATHS, "ms_per_step": total_ms / args.steps,
+                              "backward_ms": statistics.median(bwd_ms)}))
+        return 0
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t)
+    ms_per_step = total_ms / args.steps
+    value = ws * N_PATHS / (ms_per_step * 1e-3)
+    S.sync_status()
+
+    # ---------------- end to end through the public API with host buffers
+    alb_h = S.albedo.cpu().pin_memory()
+    le_h = S.Le.cpu().pin_memory()
+    hts_h = heights.cpu().pin_memory()
+    tgt_h = target.cpu().pin_memory()
+    out_h = [torch.empty(g.numel(), dtype=torch.float32).pin_memory() for g in grads]
+    loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
+    h2d = (alb_h.numel() + le_h.numel() + hts_h.numel() + tgt_h.numel()) * 4
+    d2h = (sum(g.numel() for g in grads) + 1) * 4
+
+    def e2e_step():
+        S.albedo.copy_(alb_h, non_blocking=True)
+        S.Le.copy_(le_h, non_blocking=True)
+        heights.copy_(hts_h, non_blocking=True)
+        target.copy_(tgt_h, non_blocking=True)
+        step()
+        for g, h in zip(grads, out_h):
+            h.copy_(g, non_blocking=True)
+        loss_h.copy_(loss, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(max(3, args.steps // 2))]
+    for a, b in e_ev:
+        flush.fill_(1)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e_ev) / len(e_ev)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t)
+    e2e_value = ws * N_PATHS / (e2e_ms * 1e-3)
+
+    # ---------------- algorithmic work of the dominant kernel (counting variant, untimed)
+    census = torch.zeros(5, dtype=torch.int64, device=dev)
+    o_cnt = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset,
+                   n_norm=N_PATHS * ws, census=census)
+    S.backward_lrb3(o_cnt, dI, grads=S.new_grads())
+    torch.cuda.synchronize()
+    c = [int(x) for x in census.cpu()]
+    flops = (FLOPS_PER["node"] * c[1] + FLOPS_PER["prim"] * c[2] + FLOPS_PER["vertex"] * c[3] +
+             FLOPS_PER["conn"] * c[4])
+    bwd_mean_s = (sum(bwd_ms) / len(bwd_ms)) * 1e-3
+    sm_max = 2070.0
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        sm_max = float(peaks.get("sm_max_mhz", sm_max))
+    except Exception:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 x max SM clock
+    achieved = flops / bwd_mean_s / 1e12
+    roofline = {"bound": "alu", "kernel": "k_lrb3<attached> (LRB-3-pass passes 2+3 fused)",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "traffic": None, "kernel_ms": 1e3 * bwd_mean_s,
+                "census": {"rays": c[0], "box_tests": c[1], "prim_tests": c[2], "vertices": c[3],
+                           "connections": c[4], "flops_per": FLOPS_PER}}
+
+    # ---------------- other estimators + memory vs depth (outside the headline timing)
+    methods, memory = {}, {}
+    if not args.no_sweep:
+        methods, memory = method_sweep(S, sc, target, heights, dev, path_offset, ws, flush)
+    clk = clocks.stop()
+
+    # ---------------- CPU baseline: the oracle on the host cores (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and ws == 1:
+        n, dt, cores = oracle_sample(sc, I.smooth_adjoint(W, H, 1), args.cpu_seconds)
+        cpu = {"value": n / dt, "unit": "paths/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} of {N_PATHS} paths, depth {DEPTH}, attached naive tape AD (FP64), one gradient pass"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "resolution": f"{W}x{H}", "heightmap": "32x32 (1922 triangles)",
+                           "paths_per_gpu": N_PATHS, "max_depth": DEPTH, "attached": True,
+                           "params": "Le (3) + 1024 heights (+ albedo textures)", "l2": "flushed between steps"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+                "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
+                "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory,
+                "lib": lt.version()}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
+    """Paths/s of each estimator (primal + backward, attached) at depth 16 and the peak
+    extra device memory of each estimator at depths 4..64."""
+    import torch
+
+    from paper_2609_32920_gb300 import lt
+    stream = torch.cuda.current_stream()
+    img = S.new_image()
+    dI = torch.empty_like(img)
+    loss = torch.empty(1, device=dev)
+    grads = S.new_grads()
+
+    def run(method, D, timed_reps=3):
+        o = S.opts(seed=3, n_paths=N_PATHS, max_depth=D, attached=1, path_offset=path_offset,
+                   n_norm=N_PATHS * ws)
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        aux = None
+        if method == "reslrb":
+            aux = torch.empty((N_PATHS, 8), dtype=torch.float32, device=dev)
+        elif method == "naive":
+            aux = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device=dev)
+
+        def once():
+            if method == "lrb3":
+                S.primal(o, image=img)
+                lt.film_l2(img, target, d_image=dI, loss=loss)
+                S.backward_lrb3(o, dI, grads=grads)
+            elif method == "reslrb":
+                S.primal(o, estimator=lt.EST_RESLRB, image=img, aux=aux)
+                lt.film_l2(img, target, d_image=dI, loss=loss)
+                S.backward_reslrb(o, dI, aux, grads=grads)
+            else:
+                S.primal(o, estimator=lt.EST_NAIVE, image=img, aux=aux)
+                lt.film_l2(img, target, d_image=dI, loss=loss)
+                S.backward_naive(o, dI, aux, grads=grads)
+        once()
+        torch.cuda.synchronize()
+        peak = torch.cuda.max_memory_allocated() - base
+        ms = []
+        for _ in range(timed_reps):
+            flush.fill_(2)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            once()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        del aux
+        torch.cuda.empty_cache()
+        return statistics.median(ms), peak
+
+    methods = {}
+    for m in ("lrb3", "reslrb", "naive"):
+        ms, peak = run(m, DEPTH)
+        methods[m] = {"paths_per_s": N_PATHS / (ms * 1e-3), "ms": ms, "extra_bytes": peak}
+    memory = {}
+    for D in (4, 8, 16, 32, 64):
+        memory[str(D)] = {}
+        for m in ("lrb3", "reslrb", "naive"):
+            ms, peak = run(m, D, timed_reps=1)
+            memory[str(D)][m] = {"extra_bytes": peak, "ms": ms}
+    return methods, memory
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -104,6 +104,10 @@ typedef struct {
   const uint8_t* path_mask; /* DEVICE [n_paths] optional: 0 = skip path (testing)   */
   uint32_t* path_hash;  /* DEVICE [n_paths] optional out: decision hash per path    */
   float* path_dbg;      /* DEVICE [n_paths][4] optional out (see each call)         */
+  uint64_t* census;     /* DEVICE [5] optional out, lt_backward_lrb3 only: adds the
+                           work done (rays traced, BVH box tests, primitive tests,
+                           path vertices, valid connections) using a counting kernel
+                           variant; for measurement, not for timed runs           */
 } lt_render_opts;
 
 /* Gradient outputs (DEVICE, FP32, caller-owned).  NULL skips a parameter group.

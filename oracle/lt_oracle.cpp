@@ -725,8 +725,8 @@ int or_intersect(const or_scene* s, const or_params* p, const double* org, const
 }
 
 // Light-traced image (Sec. 3.1).  estimator 0 splats every connection; estimator 1 splats
-// only the reservoir winner reweighted by Omega/omega_R (Eq. 9, Listing of the ResLRB
-// primal).  image [H][W][3] is overwritten.  Optional per-path outputs: hashes [n_paths],
+// only the reservoir winner reweighted by Omega/omega_R (Eq. 9, the ResLRB primal);
+// estimator 2 returns the tap-mass image used to bound film-position rounding.  image [H][W][3] is overwritten.  Optional per-path outputs: hashes [n_paths],
 // records [n_paths][8] = (R vertex index or -1, Omega/omega_R, u_x, u_y, S_rgb, n_conn).
 int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const uint8_t* mask, double* image,
                  uint32_t* hashes, int estimator, double* records) {
@@ -754,6 +754,16 @@ int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const
       if (mask && !mask[i]) continue;
       if (estimator == 0) {
         for (auto& c : cs) splat(sc, A.img.data(), c.L, c.ux, c.uy);
+      } else if (estimator == 2) {
+        // tap mass: |L| added with weight one to every on-film tap of each splat (bounds
+        // how much a film-position error can move a pixel)
+        for (auto& c : cs) {
+          int px[4], py[4];
+          double w[4];
+          int k = tent_taps<double>(sc.s->W, sc.s->H, c.ux, c.uy, px, py, w);
+          for (int t = 0; t < k; ++t)
+            for (int ch = 0; ch < 3; ++ch) A.img[(py[t] * sc.s->W + px[t]) * 3 + ch] += std::fabs(c.L[ch]);
+        }
       } else {
         path_reservoir(run->seed, n, P, cs);
         if (P.R < 0) continue;

@@ -245,6 +245,7 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.hash = o->path_hash;
   k.dbg = o->path_dbg;
   k.tape_offset = ((size_t)o->n_paths * sizeof(int) + 255) & ~(size_t)255;
+  k.census = (unsigned long long*)o->census;
   return k;
 }
 
@@ -471,13 +472,12 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   lt_status v = check_opts(s, p, o);
   if (v != LT_OK) return v;
   if (!dI) return fail(LT_ERR_INVALID_ARG, "d_image is NULL");
-  if (o->attached && s->has_dielectric) return fail(LT_ERR_UNSUPPORTED, "attached LRB-3 with dielectrics");
   cudaStream_t st = (cudaStream_t)stream;
   GradPtrs gp;
   v = prep_grads(s, g, st, gp);
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_lrb3(s->dev, kparams(p, o), o->attached != 0, dI, gp, cfg_for(s, o), st);
+  cudaError_t e = launch_lrb3(s->dev, kparams(p, o), o->attached != 0, s->has_dielectric, dI, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -487,13 +487,12 @@ lt_status lt_backward_reslrb(lt_scene* s, const lt_params* p, const lt_render_op
   lt_status v = check_opts(s, p, o);
   if (v != LT_OK) return v;
   if (!dI || !rec) return fail(LT_ERR_INVALID_ARG, "d_image or records is NULL");
-  if (o->attached && s->has_dielectric) return fail(LT_ERR_UNSUPPORTED, "attached ResLRB with dielectrics");
   cudaStream_t st = (cudaStream_t)stream;
   GradPtrs gp;
   v = prep_grads(s, g, st, gp);
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_reslrb(s->dev, kparams(p, o), o->attached != 0, dI, rec, gp, cfg_for(s, o), st);
+  cudaError_t e = launch_reslrb(s->dev, kparams(p, o), o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_reslrb: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -505,13 +504,12 @@ lt_status lt_backward_naive(lt_scene* s, const lt_params* p, const lt_render_opt
   if (!dI) return fail(LT_ERR_INVALID_ARG, "d_image is NULL");
   if (!ws || ws_bytes < lt_naive_workspace_bytes(o))
     return fail(LT_ERR_OOM, "naive-AD workspace missing or smaller than lt_naive_workspace_bytes()");
-  if (o->attached && s->has_dielectric) return fail(LT_ERR_UNSUPPORTED, "attached naive AD with dielectrics");
   cudaStream_t st = (cudaStream_t)stream;
   GradPtrs gp;
   v = prep_grads(s, g, st, gp);
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_naive(s->dev, kparams(p, o), o->attached != 0, dI, ws, gp, cfg_for(s, o), st);
+  cudaError_t e = launch_naive(s->dev, kparams(p, o), o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_naive: ") + cudaGetErrorString(e));
   return LT_OK;
 }

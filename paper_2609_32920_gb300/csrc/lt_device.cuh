@@ -151,9 +151,18 @@ struct HitRec {
   float t, b1, b2;
 };
 
+// Work census of one thread (only in the counting kernel variants): rays, box tests and
+// primitive tests.
+struct Census {
+  uint32_t rays, nodes, prims;
+};
+
 // Closest hit: smallest t > kTMin, ties to the smaller original primitive id; `skip`
 // (leaf-order index) is the primitive the ray leaves.  Stackless threaded traversal.
-__device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, float3 dir, int skip) {
+template <bool ST = false>
+__device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, float3 dir, int skip,
+                                                Census* cs = nullptr) {
+  if (ST) cs->rays++;
   HitRec h;
   h.prim = -1; h.t = 3.0e38f; h.b1 = 0; h.b2 = 0;
   int best_orig = 0x7fffffff;
@@ -162,6 +171,7 @@ __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, f
   while (i < S.n_nodes) {
     float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
     int skipi = __float_as_int(lo.w);
+    if (ST) cs->nodes++;
     if (hit_box(lo, hi, org, inv, h.t)) {
       int leaf = __float_as_int(hi.w);
       int cnt = leaf & 255;
@@ -169,6 +179,7 @@ __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, f
         int first = leaf >> 8;
         for (int k = first; k < first + cnt; ++k) {
           if (k == skip) continue;
+          if (ST) cs->prims++;
           Prim p = load_prim(S, k);
           float t, u, v;
           if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
@@ -188,13 +199,17 @@ __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, f
 }
 
 // Any hit in (kTMin, dist - kTMin) (sensor-connection visibility).
-__device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 dir, float dist, int skip) {
+template <bool ST = false>
+__device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 dir, float dist, int skip,
+                                         Census* cs = nullptr) {
+  if (ST) cs->rays++;
   float3 inv = safe_inv(dir);
   float tmax = dist - kTMin;
   int i = 0;
   while (i < S.n_nodes) {
     float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
     int skipi = __float_as_int(lo.w);
+    if (ST) cs->nodes++;
     if (hit_box(lo, hi, org, inv, tmax)) {
       int leaf = __float_as_int(hi.w);
       int cnt = leaf & 255;
@@ -202,6 +217,7 @@ __device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 d
         int first = leaf >> 8;
         for (int k = first; k < first + cnt; ++k) {
           if (k == skip) continue;
+          if (ST) cs->prims++;
           Prim p = load_prim(S, k);
           float t, u, v;
           if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) return true;
@@ -237,7 +253,9 @@ struct Conn {
   bool valid;
   float ux, uy, geo;
 };
-__device__ __forceinline__ Conn connect(const DevScene& S, float3 x, float3 ns, int prim, bool test_vis = true) {
+template <bool ST = false>
+__device__ __forceinline__ Conn connect(const DevScene& S, float3 x, float3 ns, int prim, bool test_vis = true,
+                                        Census* cs = nullptr) {
   Conn c;
   c.valid = false; c.ux = c.uy = c.geo = 0.0f;
   float3 cv = S.cpos - x;
@@ -248,7 +266,7 @@ __device__ __forceinline__ Conn connect(const DevScene& S, float3 x, float3 ns, 
   float zc;
   if (!project(S, x, c.ux, c.uy, zc)) return c;
   if (!(c.ux >= 0.0f && c.ux < (float)S.W && c.uy >= 0.0f && c.uy < (float)S.H)) return c;
-  if (test_vis && occluded(S, x, wc, dist, prim)) return c;
+  if (test_vis && occluded<ST>(S, x, wc, dist, prim, cs)) return c;
   float cc = zc / dist;
   c.geo = cosc * S.K0 / (dist * dist * cc * cc * cc);
   c.valid = true;

@@ -100,8 +100,9 @@ struct Vtx {
 };
 
 // Returns false when the path ends (miss or emitter hit).
-__device__ __forceinline__ bool walk_hit(const DevScene& S, const Walk& w, Vtx& v) {
-  HitRec h = trace_closest(S, w.org, w.dir, w.skip);
+template <bool ST = false>
+__device__ __forceinline__ bool walk_hit(const DevScene& S, const Walk& w, Vtx& v, Census* cs = nullptr) {
+  HitRec h = trace_closest<ST>(S, w.org, w.dir, w.skip, cs);
   if (h.prim < 0) return false;
   v.prim = h.prim;
   v.P = load_prim(S, h.prim);
@@ -219,12 +220,289 @@ __device__ __forceinline__ void scatter_heights(const DevScene& S, float* dh, in
   if (ph.z >= 0) atomicAdd(dh + ph.z, h2);
 }
 
+// ------------------------------------------------------------ specular chains (attached)
+// A chain starts at an attached specular vertex a (following the emitter or a diffuse
+// vertex, the "anchor") and continues through sliding vertices (re-intersected along the
+// reflected/refracted ray with the same primitive) up to a sliding diffuse vertex t.
+// Everything a chain needs to be replayed is constant-size: the anchor and the chain
+// start's attached coordinates; the branch choices come from the Philox counter.
+struct ChainInfo {
+  int ka;                // vertex index of the chain's attached specular start
+  int prim_a;
+  float ba1, ba2;
+  float3 xp, np;         // anchor position and (unnormalised) normal
+  int prim_p;            // anchor primitive (-1: the emitter)
+  float bp1, bp2;
+  int kanchor;           // anchor vertex index (-1: the emitter)
+  bool anchor_sliding;   // the anchor is itself the sliding end of an earlier chain
+  float lam;             // channel-summed adjoint weight of the chain's Fresnel factors
+};
+
 // Adjoint of an attached vertex accumulated until all of its terms are known.
 struct PendAdj {
-  int prim;
+  int prim;              // -1: nothing pending (the emitter)
+  int k;                 // vertex index
   float b1, b2;
   float3 x, nr, gx, gn;
+  bool sliding;          // reached through a specular chain (then `chain` is valid)
+  ChainInfo chain;
 };
+
+__device__ __forceinline__ void pend_init(PendAdj& p, int prim, int k, float b1, float b2, float3 x, float3 nr) {
+  p.prim = prim; p.k = k; p.b1 = b1; p.b2 = b2; p.x = x; p.nr = nr;
+  p.gx = p.gn = f3(0, 0, 0);
+  p.sliding = false;
+}
+
+// Chain whose attached specular start is vertex k, anchored at the pending vertex `an`.
+__device__ __forceinline__ ChainInfo chain_at(const PendAdj& an, int k, const Vtx& v, float lam) {
+  ChainInfo c;
+  c.ka = k; c.prim_a = v.prim; c.ba1 = v.b1; c.ba2 = v.b2;
+  c.xp = an.x; c.np = an.nr; c.prim_p = an.prim; c.bp1 = an.b1; c.bp2 = an.b2;
+  c.kanchor = an.prim < 0 ? -1 : an.k;
+  c.anchor_sliding = an.prim >= 0 && an.sliding;
+  c.lam = lam;
+  return c;
+}
+
+// State of chain vertex j when replayed from the chain start.
+struct ChainState {
+  int prim;
+  float3 x, din, nraw;
+  Dielectric D;
+  bool refl;
+};
+
+// Replay the chain from its start to vertex j (a <= j) and trace the ray leaving j.
+__device__ __forceinline__ bool chain_replay(const DevScene& S, const KParams& kp, uint64_t n, const ChainInfo& c,
+                                             int j, ChainState& st, HitRec& next) {
+  Prim Pa = load_prim(S, c.prim_a);
+  float3 x = Pa.o + Pa.e1 * c.ba1 + Pa.e2 * c.ba2;
+  float3 din = normalize(x - c.xp);
+  int prim = c.prim_a;
+  for (int k = c.ka;; ++k) {
+    Prim P = load_prim(S, prim);
+    float3 nraw = cross(P.e1, P.e2);
+    Dielectric D = dielectric(din, normalize(nraw), __ldg(S.mat_ior + P.mat));
+    float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+    bool refl = D.tir || r.z < D.F;
+    float3 dout = refl ? D.refl : D.refr;
+    HitRec h = trace_closest(S, x, dout, prim);
+    if (k == j) {
+      st.prim = prim; st.x = x; st.din = din; st.nraw = nraw; st.D = D; st.refl = refl;
+      next = h;
+      return h.prim >= 0;
+    }
+    if (h.prim < 0) return false;
+    x = x + dout * h.t;
+    din = dout;
+    prim = h.prim;
+  }
+}
+
+// d log F / d cos_i of the unpolarised Fresnel reflectance (Fresnel equations).
+__device__ __forceinline__ float fresnel_dF(const Dielectric& D) {
+  float eta = D.eta, ci = D.ci, ct = D.ct;
+  float dct = eta * eta * ci / ct;
+  float us = eta * ci - ct, ws = eta * ci + ct;
+  float up = ci - eta * ct, wp = ci + eta * ct;
+  float rs = us / ws, rp = up / wp;
+  float drs = ((eta - dct) * ws - us * (eta + dct)) / (ws * ws);
+  float drp = ((1.0f - eta * dct) * wp - up * (1.0f + eta * dct)) / (wp * wp);
+  return rs * drs + rp * drp;
+}
+
+// Reverse of d_out = reflect/refract(d_in, n) and of the branch weight F/F0 or
+// (1-F)/(1-F0) with log-derivative weight lam.  Returns the adjoints of d_in and nraw.
+__device__ __forceinline__ void spec_adjoint(const ChainState& s, float3 gdout, float lam, float3& gdin,
+                                             float3& gnraw) {
+  const Dielectric& D = s.D;
+  float3 ns = D.ns;
+  float3 gns;
+  float gci;
+  if (s.refl) {
+    gdin = gdout;
+    gns = gdout * (2.0f * D.ci);
+    gci = 2.0f * dot(gdout, ns);
+    if (!D.tir) gci += lam * fresnel_dF(D) / D.F;
+  } else {
+    gdin = gdout * D.eta;
+    float K = D.eta * D.ci - D.ct;
+    gns = gdout * K;
+    float gK = dot(gdout, ns);
+    float dct = D.eta * D.eta * D.ci / D.ct;
+    gci = gK * (D.eta - dct);
+    gci += lam * (-fresnel_dF(D)) / (1.0f - D.F);
+  }
+  gdin = gdin - ns * gci;
+  gns = gns - s.din * gci;
+  float3 gn = D.entering ? gns : -gns;
+  float inv = 1.0f / length(s.nraw);
+  float3 nn = s.nraw * inv;
+  gnraw = (gn - nn * dot(nn, gn)) * inv;
+}
+
+
+// Reverse-mode sweep back through a chain ending at sliding vertex kt whose position
+// adjoint is gx_t: vertex states are replayed from the chain start (constant memory,
+// c(c+1)/2 traces for c specular vertices).  Scatters into the height gradient the
+// contributions of every primitive the chain touches and returns the adjoint of the
+// anchor position (through the chain start's incoming direction).
+__device__ __noinline__ float3 chain_reverse(const DevScene& S, const KParams& kp, uint64_t n, const ChainInfo& c,
+                                             int kt, float3 gx_t, float* dh) {
+  float3 gx = gx_t, gd = f3(0, 0, 0);
+  for (int j = kt - 1; j >= c.ka; --j) {
+    ChainState s;
+    HitRec h;
+    if (!chain_replay(S, kp, n, c, j, s, h)) { set_err(S, ERR_BOUNDS); return f3(0, 0, 0); }
+    Prim Q = load_prim(S, h.prim);
+    float3 m = cross(Q.e1, Q.e2);
+    float3 dout = s.refl ? s.D.refl : s.D.refr;
+    // x_{j+1} = x_j + tau d_out, tau = ((o' - x_j).m) / (d_out.m)
+    float a = dot(Q.o - s.x, m), b = dot(dout, m);
+    float tau = a / b;
+    float gtau = dot(gx, dout);
+    float3 gdout = gd + gx * tau;
+    float ga = gtau / b, gb = -gtau * tau / b;
+    float3 gxj = gx - m * ga;
+    float3 go = m * ga;
+    float3 gm = (Q.o - s.x) * ga + dout * gb;
+    gdout = gdout + m * gb;
+    scatter_heights(S, dh, h.prim, 0.0f, 0.0f, go, gm);  // plane of the next primitive
+    float3 gdin, gnraw;
+    spec_adjoint(s, gdout, c.lam, gdin, gnraw);
+    if (j > c.ka) {
+      scatter_heights(S, dh, s.prim, 0.0f, 0.0f, f3(0, 0, 0), gnraw);  // sliding vertex: its normal only
+      gd = gdin;
+      gx = gxj;
+    } else {
+      // chain start: d_in = normalize(x_a - x_p), x_a attached to its primitive
+      float3 w = s.x - c.xp;
+      float r = length(w);
+      float3 gw = (gdin - s.din * dot(s.din, gdin)) * (1.0f / r);
+      scatter_heights(S, dh, c.prim_a, c.ba1, c.ba2, gxj + gw, gnraw);
+      return -gw;
+    }
+  }
+  return f3(0, 0, 0);
+}
+
+// Geometry-only replay of the path from the emitter up to vertex `target`; returns the
+// chain that vertex ends (valid when it is a sliding diffuse vertex).  Used to recover
+// an earlier chain when a position adjoint has to continue through it.
+__device__ __noinline__ bool replay_chain_of(const DevScene& S, const KParams& kp, uint64_t n, int target,
+                                            ChainInfo& out) {
+  Walk w;
+  float3 x0;
+  walk_start(S, kp.seed, n, f3(1, 1, 1), w, x0);
+  PendAdj an;
+  pend_init(an, -1, -1, 0.0f, 0.0f, x0, S.ln);
+  ChainInfo ch;
+  ch.ka = -1;
+  for (int k = 0; k <= target; ++k) {
+    Vtx v;
+    if (!walk_hit(S, w, v)) return false;
+    if (v.attached && !v.diffuse) ch = chain_at(an, k, v, 0.0f);
+    if (k == target) {
+      out = ch;
+      return !v.attached && v.diffuse && ch.ka >= 0;
+    }
+    float3 ns = f3(0, 0, 0);
+    if (v.diffuse) {
+      ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+      bool sl = !v.attached;
+      pend_init(an, v.prim, k, v.b1, v.b2, v.x, v.nraw);
+      an.sliding = sl;
+    }
+    walk_scatter(S, w, v, ns, f3(1, 1, 1), rand4(kp.seed, n, (uint32_t)(k + 1)));
+  }
+  return false;
+}
+
+// Propagate a position adjoint on the sliding end kt of chain c back to the parameters,
+// continuing through earlier chains while the anchor is itself sliding (those chains'
+// Fresnel factors were already counted, so they are re-traversed with zero weight).
+__device__ __noinline__ void propagate_sliding(const DevScene& S, const KParams& kp, uint64_t n, ChainInfo c, int kt,
+                                               float3 gx, float* dh) {
+  for (int guard = 0; guard < kMaxDepth; ++guard) {
+    float3 g_anchor = chain_reverse(S, kp, n, c, kt, gx, dh);
+    if (c.kanchor < 0) return;  // the emitter does not move
+    if (!c.anchor_sliding) {
+      scatter_heights(S, dh, c.prim_p, c.bp1, c.bp2, g_anchor, f3(0, 0, 0));
+      return;
+    }
+    ChainInfo prev;
+    if (!replay_chain_of(S, kp, n, c.kanchor, prev)) { set_err(S, ERR_BOUNDS); return; }
+    kt = c.kanchor;
+    gx = g_anchor;
+    c = prev;
+  }
+}
+
+// Texture-coordinate derivative of a sliding diffuse vertex: (s,t) of x on its
+// (non-moving) primitive, bilinear rho(s,t); weight wt/rho per channel.
+__device__ __forceinline__ float3 tex_pos_adjoint(const float* albedo, int4 m, const Prim& P, float s, float t,
+                                                  float3 wt, float3 rho) {
+  int tw = m.z, th = m.w, off = m.y;
+  if (tw * th <= 1) return f3(0, 0, 0);
+  float tx = s * (float)tw - 0.5f, ty = t * (float)th - 0.5f;
+  float fx0 = floorf(tx), fy0 = floorf(ty);
+  float fx = tx - fx0, fy = ty - fy0;
+  int x0 = (int)fx0, y0 = (int)fy0;
+  int xa = min(max(x0, 0), tw - 1), xb = min(max(x0 + 1, 0), tw - 1);
+  int ya = min(max(y0, 0), th - 1), yb = min(max(y0 + 1, 0), th - 1);
+  float3 T00 = texel(albedo, off + (ya * tw + xa) * 3), T10 = texel(albedo, off + (ya * tw + xb) * 3);
+  float3 T01 = texel(albedo, off + (yb * tw + xa) * 3), T11 = texel(albedo, off + (yb * tw + xb) * 3);
+  float3 ds = ((T10 - T00) * (1.0f - fy) + (T11 - T01) * fy) * (float)tw;
+  float3 dt = ((T01 - T00) * (1.0f - fx) + (T11 - T10) * fx) * (float)th;
+  float3 a = f3(wt.x / rho.x, wt.y / rho.y, wt.z / rho.z);
+  float gs = dot(a, ds), gt = dot(a, dt);
+  float3 mm = cross(P.e1, P.e2);
+  float inv = 1.0f / dot(mm, mm);
+  return (cross(P.e2, mm) * gs + cross(mm, P.e1) * gt) * inv;
+}
+
+// Flush a vertex's completed adjoint: attached vertices map through their surface
+// coordinates, sliding ones run the chain's reverse sweep (their normal is explicit).
+template <bool CH>
+__device__ __forceinline__ void pend_flush(const DevScene& S, const KParams& kp, uint64_t n, const PendAdj& p,
+                                           float* dh) {
+  if (!dh || p.prim < 0) return;
+  if (!CH || !p.sliding) {
+    scatter_heights(S, dh, p.prim, p.b1, p.b2, p.gx, p.gn);
+  } else {
+    scatter_heights(S, dh, p.prim, 0.0f, 0.0f, f3(0, 0, 0), p.gn);
+    propagate_sliding(S, kp, n, p.chain, p.k, p.gx, dh);
+  }
+}
+
+// Attached bookkeeping on arrival at vertex k, before its own terms: the attached segment
+// weight with the anchor (weight lam_seg) completes the anchor's adjoint; an attached
+// specular vertex starts a chain (its Fresnel factors weigh lam_chain); a non-specular
+// vertex becomes the new pending anchor (sliding when it ends a chain).
+// CH = false compiles the variant for scenes without dielectrics (no chains exist).
+template <bool CH>
+__device__ __forceinline__ void att_enter(const DevScene& S, const KParams& kp, uint64_t n, int k, const Vtx& v,
+                                          float lam_seg, float lam_chain, PendAdj& pv, ChainInfo& chain,
+                                          float* dh) {
+  if (!CH || v.attached) {
+    PendAdj cur;
+    pend_init(cur, v.prim, k, v.b1, v.b2, v.x, v.nraw);
+    seg_adjoint(pv.x, pv.nr, v.x, v.nraw, lam_seg, pv.gx, pv.gn, cur.gx, cur.gn);
+    pend_flush<CH>(S, kp, n, pv, dh);
+    if (CH && !v.diffuse) {
+      chain = chain_at(pv, k, v, lam_chain);
+      scatter_heights(S, dh, v.prim, v.b1, v.b2, cur.gx, cur.gn);
+      pv.prim = -1;
+    } else {
+      pv = cur;
+    }
+  } else if (v.diffuse) {
+    pend_init(pv, v.prim, k, v.b1, v.b2, v.x, v.nraw);
+    pv.sliding = true;
+    pv.chain = chain;
+  }
+}
 
 // ======================================================================= primal
 template <int EST>
@@ -301,11 +579,13 @@ __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* _
 // Pass 2 (accumulate delta_total, Eq. 14) and pass 3 (backpropagate, Eq. 15-17) fused per
 // path: both replay the path from its counter; the connection-validity bits found in
 // pass 2 are kept in a register mask so pass 3 does not re-test visibility.
-template <bool ATT>
+template <bool ATT, bool ST, bool CH>
 __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
   float3 gLe = f3(0, 0, 0);
+  Census cs = {0, 0, 0};
+  uint32_t nverts = 0, nconns = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
     if (kp.mask && !kp.mask[p]) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
@@ -318,14 +598,16 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
     int nconn = 0;
     for (int k = 0; k < kp.max_depth; ++k) {
       Vtx v;
-      if (!walk_hit(S, w, v)) break;
+      if (!walk_hit<ST>(S, w, v, &cs)) break;
+      if (ST) ++nverts;
       float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
       float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
       if (v.diffuse) {
         ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
-        Conn c = connect(S, v.x, ns, v.prim);
+        Conn c = connect<ST>(S, v.x, ns, v.prim, true, &cs);
         rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
         if (c.valid) {
+          if (ST) ++nconns;
           valid |= 1ull << k;
           ++nconn;
           float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
@@ -342,25 +624,23 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
     float3 rem = dtot;
     walk_start(S, kp.seed, n, Le, w, x0);
     PendAdj pv;
-    pv.prim = -1; pv.x = x0; pv.nr = S.ln; pv.gx = pv.gn = f3(0, 0, 0); pv.b1 = pv.b2 = 0.0f;
+    pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+    ChainInfo chain;
+    chain.ka = -1;
     const int last = 63 - __clzll((long long)valid);
     for (int k = 0; k <= last; ++k) {
       Vtx v;
-      if (!walk_hit(S, w, v)) break;
+      if (!walk_hit<ST>(S, w, v, &cs)) break;
+      if (ST) ++nverts;
       float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+      // attached segment weight and chain bookkeeping: every connection from here on
+      // carries this vertex's factors, so they weigh the remaining adjoint before Eq. 16
+      if (ATT) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights);
       float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
       if (v.diffuse) {
         ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
         TexFoot foot;
         rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
-        PendAdj cur;
-        cur.prim = v.prim; cur.b1 = v.b1; cur.b2 = v.b2; cur.x = v.x; cur.nr = v.nraw;
-        cur.gx = cur.gn = f3(0, 0, 0);
-        if (ATT) {
-          // attached segment weight: every connection from here on carries it
-          seg_adjoint(pv.x, pv.nr, v.x, v.nraw, hsum(rem), pv.gx, pv.gn, cur.gx, cur.gn);
-          scatter_heights(S, g.d_heights, pv.prim, pv.b1, pv.b2, pv.gx, pv.gn);
-        }
         float3 wsplat = f3(0, 0, 0);
         if ((valid >> k) & 1ull) {
           Conn c = connect(S, v.x, ns, v.prim, false);
@@ -370,14 +650,22 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
           float3 P = mul(Lb, L);
           wsplat = P;           // splat factor rho_k / pi (Eq. 15)
           rem = rem - P;        // Eq. 16
-          if (ATT) conn_adjoint(S, v.x, v.nraw, hsum(P), q, cur.gx, cur.gn);
+          if (ATT) conn_adjoint(S, v.x, v.nraw, hsum(P), q, pv.gx, pv.gn);
         }
         scatter_albedo(g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor rho_k (Eq. 17)
-        pv = cur;
+        if (ATT && CH && !v.attached)
+          pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
       }
       walk_scatter(S, w, v, ns, rho, r);
     }
-    if (ATT) scatter_heights(S, g.d_heights, pv.prim, pv.b1, pv.b2, pv.gx, pv.gn);
+    if (ATT) pend_flush<CH>(S, kp, n, pv, g.d_heights);
+  }
+  if (ST && kp.census) {
+    atomicAdd(kp.census + 0, (unsigned long long)cs.rays);
+    atomicAdd(kp.census + 1, (unsigned long long)cs.nodes);
+    atomicAdd(kp.census + 2, (unsigned long long)cs.prims);
+    atomicAdd(kp.census + 3, (unsigned long long)nverts);
+    atomicAdd(kp.census + 4, (unsigned long long)nconns);
   }
   block_add3(g.d_Le, gLe);
 }
@@ -385,7 +673,7 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
 // ======================================================================= ResLRB backward
 // Replay to the selected vertex R and apply the log-derivative identity with weight
 // Lbar_R * S to every factor of L_R (Eq. 11); attached adds the positional channel.
-template <bool ATT>
+template <bool ATT, bool CH>
 __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const float* __restrict__ dI,
                                                 const float4* __restrict__ rec, GradPtrs g) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -408,37 +696,35 @@ __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const fl
     float3 x0;
     walk_start(S, kp.seed, n, Le, w, x0);
     PendAdj pv;
-    pv.prim = -1; pv.x = x0; pv.nr = S.ln; pv.gx = pv.gn = f3(0, 0, 0); pv.b1 = pv.b2 = 0.0f;
+    pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+    ChainInfo chain;
+    chain.ka = -1;
     for (int k = 0; k <= R; ++k) {
       Vtx v;
       if (!walk_hit(S, w, v)) { set_err(S, ERR_BOUNDS); break; }
       float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+      if (ATT) att_enter<CH>(S, kp, n, k, v, lam, lam, pv, chain, g.d_heights);
       float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
       if (v.diffuse) {
         ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
         TexFoot foot;
         rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
-        scatter_albedo(g.d_albedo, foot, P, rho);
-        PendAdj cur;
-        cur.prim = v.prim; cur.b1 = v.b1; cur.b2 = v.b2; cur.x = v.x; cur.nr = v.nraw;
-        cur.gx = cur.gn = f3(0, 0, 0);
+        scatter_albedo(g.d_albedo, foot, P, rho);  // scattering factor (k < R) or splat factor (k = R)
         if (ATT) {
-          seg_adjoint(pv.x, pv.nr, v.x, v.nraw, lam, pv.gx, pv.gn, cur.gx, cur.gn);
-          scatter_heights(S, g.d_heights, pv.prim, pv.b1, pv.b2, pv.gx, pv.gn);
-          if (k == R) conn_adjoint(S, v.x, v.nraw, lam, q, cur.gx, cur.gn);
+          if (k == R) conn_adjoint(S, v.x, v.nraw, lam, q, pv.gx, pv.gn);
+          if (CH && !v.attached) pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, P, rho);
         }
-        pv = cur;
       }
       walk_scatter(S, w, v, ns, rho, r);
     }
-    if (ATT) scatter_heights(S, g.d_heights, pv.prim, pv.b1, pv.b2, pv.gx, pv.gn);
+    if (ATT) pend_flush<CH>(S, kp, n, pv, g.d_heights);
   }
   block_add3(g.d_Le, gLe);
 }
 
 // ======================================================================= naive reverse
 // Reverse sweep over the per-vertex tape: suffix sums of Lbar_i L_i replace the replay.
-template <bool ATT>
+template <bool ATT, bool CH>
 __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const float* __restrict__ dI,
                                                const void* __restrict__ ws, GradPtrs g) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -456,48 +742,70 @@ __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const flo
       x0 = S.lo + S.le1 * r.x + S.le2 * r.y;
     }
     float3 acc = f3(0, 0, 0);  // sum of Lbar_j L_j over j > k
+    float3 cgx = f3(0, 0, 0), cgn = f3(0, 0, 0);  // adjoint carried to vertex k by vertex k+1
+    const uint64_t n = (uint64_t)(kp.path_offset + p);
     for (int k = K - 1; k >= 0; --k) {
       float4 t0 = tape[2 * ((size_t)k * kp.n_paths + p)], t1 = tape[2 * ((size_t)k * kp.n_paths + p) + 1];
       int pk = __float_as_int(t0.x);
       int prim = pk & 0xffffff;
       uint32_t fl = (uint32_t)pk >> 24;
       if (prim >= S.n_prims) { set_err(S, ERR_BOUNDS); break; }
-      if ((fl & 3u) != K_DIFFUSE) continue;  // dielectric vertices carry no detached factor
+      const bool diffuse = (fl & 3u) == K_DIFFUSE, attached = (fl & 16u) != 0;
+      if (!ATT && !diffuse) continue;  // dielectric vertices carry no detached factor
       Prim P = load_prim(S, prim);
       int4 m = __ldg(S.mat + P.mat);
-      TexFoot foot;
-      float3 rho = tex_lookup(kp.albedo, m, t0.y, t0.z, &foot);
-      float3 P3 = f3(0, 0, 0);
+      float3 P3 = f3(0, 0, 0), rho = f3(1, 1, 1);
       float2 q = make_float2(0.0f, 0.0f);
-      float3 L = f3(t1.x, t1.y, t1.z);
-      if (fl & 8u) {
-        float3 Lb = adjoint_read(dI, S.W, S.H, t0.w, t1.w, L, ATT ? &q : nullptr);
-        P3 = mul(Lb, L);
-      }
-      scatter_albedo(g.d_albedo, foot, P3 + acc, rho);
-      if (ATT) {
-        PendAdj cur;
-        cur.prim = prim; cur.b1 = t0.y; cur.b2 = t0.z;
-        cur.x = P.o + P.e1 * t0.y + P.e2 * t0.z;
-        cur.nr = cross(P.e1, P.e2);
-        cur.gx = cur.gn = f3(0, 0, 0);
-        if (fl & 8u) conn_adjoint(S, cur.x, cur.nr, hsum(P3), q, cur.gx, cur.gn);
-        // own segment weight with the predecessor (previous tape record or the emitter)
-        float3 xp = x0, np = S.ln;
-        int pprim = -1;
-        float pb1 = 0.0f, pb2 = 0.0f;
-        if (k > 0) {
-          float4 s0 = tape[2 * ((size_t)(k - 1) * kp.n_paths + p)];
-          pprim = __float_as_int(s0.x) & 0xffffff;
-          Prim Q = load_prim(S, pprim);
-          pb1 = s0.y; pb2 = s0.z;
-          xp = Q.o + Q.e1 * pb1 + Q.e2 * pb2;
-          np = cross(Q.e1, Q.e2);
+      if (diffuse) {
+        TexFoot foot;
+        rho = tex_lookup(kp.albedo, m, t0.y, t0.z, &foot);
+        float3 L = f3(t1.x, t1.y, t1.z);
+        if (fl & 8u) {
+          float3 Lb = adjoint_read(dI, S.W, S.H, t0.w, t1.w, L, ATT ? &q : nullptr);
+          P3 = mul(Lb, L);
         }
-        float3 gxp = f3(0, 0, 0), gnp = f3(0, 0, 0);
-        seg_adjoint(xp, np, cur.x, cur.nr, hsum(P3 + acc), gxp, gnp, cur.gx, cur.gn);
-        scatter_heights(S, g.d_heights, pprim, pb1, pb2, gxp, gnp);
-        scatter_heights(S, g.d_heights, cur.prim, cur.b1, cur.b2, cur.gx, cur.gn);
+        scatter_albedo(g.d_albedo, foot, P3 + acc, rho);
+      }
+      if (ATT) {
+        float3 x = P.o + P.e1 * t0.y + P.e2 * t0.z, nr = cross(P.e1, P.e2);
+        float3 gx = cgx, gn = cgn;
+        cgx = cgn = f3(0, 0, 0);
+        const float lam = hsum(P3 + acc);  // every connection from this vertex on
+        if (diffuse) {
+          if (fl & 8u) conn_adjoint(S, x, nr, hsum(P3), q, gx, gn);
+          if (CH && !attached) gx = gx + tex_pos_adjoint(kp.albedo, m, P, t0.y, t0.z, P3 + acc, rho);
+        }
+        if (!CH || attached) {
+          float3 xp = x0, np = S.ln;
+          if (k > 0) {
+            float4 s0 = tape[2 * ((size_t)(k - 1) * kp.n_paths + p)];
+            Prim Q = load_prim(S, __float_as_int(s0.x) & 0xffffff);
+            xp = Q.o + Q.e1 * s0.y + Q.e2 * s0.z;
+            np = cross(Q.e1, Q.e2);
+          }
+          seg_adjoint(xp, np, x, nr, lam, cgx, cgn, gx, gn);
+          scatter_heights(S, g.d_heights, prim, t0.y, t0.z, gx, gn);
+        } else if (CH && diffuse) {
+          // end of a specular chain: find its attached start and anchor on the tape
+          int a = k - 1;
+          while (a >= 0 && !((((uint32_t)__float_as_int(tape[2 * ((size_t)a * kp.n_paths + p)].x)) >> 24) & 16u)) --a;
+          if (a < 0) { set_err(S, ERR_BOUNDS); break; }
+          float4 sa = tape[2 * ((size_t)a * kp.n_paths + p)];
+          ChainInfo c;
+          c.ka = a; c.prim_a = __float_as_int(sa.x) & 0xffffff; c.ba1 = sa.y; c.ba2 = sa.z; c.lam = lam;
+          c.xp = x0; c.np = S.ln; c.prim_p = -1; c.bp1 = c.bp2 = 0.0f; c.kanchor = -1; c.anchor_sliding = false;
+          if (a > 0) {
+            float4 sp = tape[2 * ((size_t)(a - 1) * kp.n_paths + p)];
+            int pprim = __float_as_int(sp.x) & 0xffffff;
+            Prim Q = load_prim(S, pprim);
+            c.xp = Q.o + Q.e1 * sp.y + Q.e2 * sp.z;
+            c.np = cross(Q.e1, Q.e2);
+            c.prim_p = pprim; c.bp1 = sp.y; c.bp2 = sp.z; c.kanchor = a - 1;
+            c.anchor_sliding = !((((uint32_t)__float_as_int(sp.x)) >> 24) & 16u);
+          }
+          scatter_heights(S, g.d_heights, prim, 0.0f, 0.0f, f3(0, 0, 0), gn);
+          propagate_sliding(S, kp, n, c, k, gx, g.d_heights);
+        }
       }
       acc = acc + P3;
     }
@@ -556,27 +864,36 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, const float* dI, const GradPtrs& g,
-                        const LaunchCfg& L, cudaStream_t st) {
+cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
+                        const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
-  if (att) k_lrb3<true><<<grid, L.block, 0, st>>>(S, kp, dI, g);
-  else k_lrb3<false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+  if (kp.census) {
+    if (att && chains) k_lrb3<true, true, true><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+    else if (att) k_lrb3<true, true, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+    else k_lrb3<false, true, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+  } else {
+    if (att && chains) k_lrb3<true, false, true><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+    else if (att) k_lrb3<true, false, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+    else k_lrb3<false, false, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, const float* dI, const void* rec,
-                          const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
+cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
+                          const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
-  if (att) k_reslrb<true><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
-  else k_reslrb<false><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
+  if (att && chains) k_reslrb<true, true><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
+  else if (att) k_reslrb<true, false><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
+  else k_reslrb<false, false><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, const float* dI, const void* ws,
-                         const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
+cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
+                         const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
-  if (att) k_naive<true><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
-  else k_naive<false><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
+  if (att && chains) k_naive<true, true><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
+  else if (att) k_naive<true, false><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
+  else k_naive<false, false><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ struct KParams {
   uint32_t* hash;            // DEVICE [n_paths] or null
   float* dbg;                // DEVICE [n_paths][4] or null
   size_t tape_offset;        // naive tape: bytes before the first record
+  unsigned long long* census;  // DEVICE [5] or null: rays, box tests, primitive tests, vertices, connections
 };
 
 struct GradPtrs {
@@ -48,12 +49,13 @@ struct RefitArgs {
 cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
 cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux,
                           const LaunchCfg& L, cudaStream_t st);
-cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, const float* dI, const GradPtrs& g,
-                        const LaunchCfg& L, cudaStream_t st);
-cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, const float* dI, const void* rec,
-                          const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
-cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, const float* dI, const void* ws,
-                         const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+// `chains`: the scene has dielectrics, so attached passes need the specular-chain variant.
+cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
+                        const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
+                          const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
+                         const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
 cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,
                            cudaStream_t st);
 

@@ -52,7 +52,7 @@ class lt_render_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("path_offset", C.c_int64), ("n_paths", C.c_int64), ("n_norm", C.c_int64),
                 ("max_depth", C.c_int), ("attached", C.c_int), ("target", C.c_int), ("mlp", C.c_void_p),
                 ("block_size", C.c_int), ("blocks_per_sm", C.c_int), ("path_mask", C.c_void_p),
-                ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p)]
+                ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p), ("census", C.c_void_p)]
 
 
 class lt_grads(C.Structure):
@@ -186,7 +186,8 @@ class Scene:
 
     @staticmethod
     def opts(seed=0, n_paths=1 << 14, max_depth=4, attached=0, path_offset=0, n_norm=0, block_size=0,
-             blocks_per_sm=0, mask=None, hash_out=None, dbg_out=None, target=TARGET_LUMINANCE, mlp=None):
+             blocks_per_sm=0, mask=None, hash_out=None, dbg_out=None, target=TARGET_LUMINANCE, mlp=None,
+             census=None):
         o = lt_render_opts()
         o.seed, o.path_offset, o.n_paths, o.n_norm = int(seed), int(path_offset), int(n_paths), int(n_norm)
         o.max_depth, o.attached, o.target = int(max_depth), int(attached), int(target)
@@ -195,6 +196,9 @@ class Scene:
         o.path_mask = None if mask is None else mask.data_ptr()
         o.path_hash = None if hash_out is None else hash_out.data_ptr()
         o.path_dbg = None if dbg_out is None else dbg_out.data_ptr()
+        o.census = None if census is None else census.data_ptr()
+        # the struct holds raw device pointers: keep the tensors alive as long as it lives
+        o._keep = (mask, hash_out, dbg_out, census, mlp)
         return o
 
     def record_size(self, o) -> int:

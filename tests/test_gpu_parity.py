@@ -38,7 +38,9 @@ def test_primal_matches_oracle(box64, seed, n, D):
     mask = agree_mask(S, sc, seed, n, D)
     img = S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask))).cpu().numpy()
     ref = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask)
-    ok = primal_close(img, ref)
+    mass = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, estimator=2)
+    assert np.abs(img - ref).max() <= 1e-4 * np.abs(ref).max()
+    ok = primal_close(img, ref, mass=mass, W=max(sc.W, sc.H))
     assert ok.all(), f"{(~ok).sum()} pixels off; max rel {np.abs(img - ref).max() / np.abs(ref).max()}"
 
 
@@ -85,10 +87,13 @@ def test_reslrb_detached_records_and_gradient(box64):
     m = mask.astype(bool)
     assert np.array_equal(R[m], ref_rec[m, 0].astype(np.int32)), "reservoir winners differ"
     sel = m & (R >= 0)
-    assert np.allclose(r[sel, 1], ref_rec[sel, 1], rtol=1e-5)          # Omega / omega_R
+    assert np.allclose(r[sel, 1], ref_rec[sel, 1], rtol=1e-4)          # Omega / omega_R
     assert np.allclose(r[sel, 2:4], ref_rec[sel, 2:4], rtol=0, atol=1e-3)  # u_R (pixels)
-    assert rel_l2(r[sel, 4:7], ref_rec[sel, 4:7]) < 1e-5                # S
-    assert primal_close(img, ref_img).all()
+    assert rel_l2(r[sel, 4:7], ref_rec[sel, 4:7]) < 1e-4                # S
+    # primal image of the reservoir estimator: winners' splats scaled by Omega/omega_R;
+    # the mass bound uses the full-estimator tap mass scaled by the largest weight
+    mass = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, estimator=2) * max(1.0, r[sel, 1].max())
+    assert primal_close(img, ref_img, mass=mass, W=max(sc.W, sc.H)).all()
     gA, gL, _ = S.backward_reslrb(o, t32(dI_np), rec)
     refg = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, method=O.RESLRB_AD, mask=mask)
     assert rel_l2(gA.cpu().numpy(), refg["d_albedo"]) < 1e-3
@@ -143,7 +148,8 @@ def test_ragged_offset_and_depth_limits(box64):
         o = S.opts(seed=9, n_paths=n, max_depth=D, path_offset=off, n_norm=1 << 20, mask=_dev_mask(mask))
         img = S.primal(o).cpu().numpy()
         ref = O.render(sc, seed=9, n_paths=n, max_depth=D, path_begin=off, n_norm=1 << 20, mask=mask)
-        assert primal_close(img, ref).all()
+        mass = O.render(sc, seed=9, n_paths=n, max_depth=D, path_begin=off, n_norm=1 << 20, mask=mask, estimator=2)
+        assert primal_close(img, ref, mass=mass, W=max(sc.W, sc.H)).all()
         gA, gL, _ = S.backward_lrb3(o, t32(dI_np))
         r = O.gradient(sc, dI_np, seed=9, n_paths=n, max_depth=D, path_begin=off, n_norm=1 << 20, mask=mask)
         assert rel_l2(gA.cpu().numpy(), r["d_albedo"]) < 1e-3
@@ -196,3 +202,53 @@ def test_film_l2_kernel():
     ref_loss = float(((I_.double() - T.double()) ** 2).sum() / n)
     assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
     assert torch.allclose(d, 2 * (I_ - T) / n, rtol=1e-6, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def slab():
+    sc = I.slab_scene(48, n=12)
+    return sc, lt.Scene(sc)
+
+
+@pytest.mark.parametrize("method,D", [("lrb3", 4), ("lrb3", 8), ("reslrb", 8), ("naive", 8), ("lrb3", 12)])
+def test_attached_caustic_slab_matches_oracle(slab, method, D):
+    """Dielectric height field: attached gradients through specular chains (first- and
+    later-generation chains, anchors that are themselves chain ends)."""
+    sc, S = slab
+    n, seed = 1 << 13, 11
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 61)
+    mask = agree_mask(S, sc, seed, n, D, max_divergent=2e-3)
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask))
+    dI = t32(dI_np)
+    if method == "lrb3":
+        gA, gL, gH = S.backward_lrb3(o, dI)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
+    elif method == "reslrb":
+        rec = torch.zeros((n, 8), device="cuda")
+        S.primal(o, estimator=lt.EST_RESLRB, aux=rec)
+        gA, gL, gH = S.backward_reslrb(o, dI, rec)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, method=O.RESLRB_AD, mask=mask)
+    else:
+        ws = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device="cuda")
+        S.primal(o, estimator=lt.EST_NAIVE, aux=ws)
+        gA, gL, gH = S.backward_naive(o, dI, ws)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
+    S.sync_status()
+    assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+
+
+def test_detached_caustic_slab_matches_oracle(slab):
+    sc, S = slab
+    n, seed, D = 1 << 13, 12, 8
+    mask = agree_mask(S, sc, seed, n, D, max_divergent=2e-3)
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask))
+    img = S.primal(o).cpu().numpy()
+    ref = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask)
+    mass = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, estimator=2)
+    assert primal_close(img, ref, mass=mass, W=max(sc.W, sc.H)).all()
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 62)
+    gA, gL, _ = S.backward_lrb3(o, t32(dI_np))
+    r = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, mask=mask)
+    assert rel_l2(gL.cpu().numpy(), r["d_Le"]) < 1e-3
+    assert rel_l2(gA.cpu().numpy(), r["d_albedo"]) < 1e-3
