@@ -246,7 +246,17 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.dbg = o->path_dbg;
   k.tape_offset = ((size_t)o->n_paths * sizeof(int) + 255) & ~(size_t)255;
   k.census = (unsigned long long*)o->census;
+  k.n_alb = k.n_h = k.priv_n = 0;
   return k;
+}
+
+// Gradients accumulate per block in shared memory when both parameter arrays fit in the
+// default 48 KB shared-memory limit (46 KB, leaving room for static shared memory).
+void set_privatization(const lt_scene* s, const lt_grads* g, KParams& kp) {
+  kp.n_alb = s->n_albedo;
+  kp.n_h = s->n_heights;
+  int n = (g && g->d_albedo ? s->n_albedo : 0) + (g && g->d_heights ? s->n_heights : 0);
+  kp.priv_n = (n > 0 && (size_t)(s->n_albedo + s->n_heights) * sizeof(float) <= 46 * 1024) ? s->n_albedo + s->n_heights : 0;
 }
 
 lt_status prep_grads(const lt_scene* s, const lt_grads* g, cudaStream_t st, GradPtrs& gp) {
@@ -477,7 +487,9 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   v = prep_grads(s, g, st, gp);
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_lrb3(s->dev, kparams(p, o), o->attached != 0, s->has_dielectric, dI, gp, cfg_for(s, o), st);
+  KParams kp = kparams(p, o);
+  set_privatization(s, g, kp);
+  cudaError_t e = launch_lrb3(s->dev, kp, o->attached != 0, s->has_dielectric, dI, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -492,7 +504,9 @@ lt_status lt_backward_reslrb(lt_scene* s, const lt_params* p, const lt_render_op
   v = prep_grads(s, g, st, gp);
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_reslrb(s->dev, kparams(p, o), o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
+  KParams kp = kparams(p, o);
+  set_privatization(s, g, kp);
+  cudaError_t e = launch_reslrb(s->dev, kp, o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_reslrb: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -509,7 +523,9 @@ lt_status lt_backward_naive(lt_scene* s, const lt_params* p, const lt_render_opt
   v = prep_grads(s, g, st, gp);
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_naive(s->dev, kparams(p, o), o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
+  KParams kp = kparams(p, o);
+  set_privatization(s, g, kp);
+  cudaError_t e = launch_naive(s->dev, kp, o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_naive: ") + cudaGetErrorString(e));
   return LT_OK;
 }

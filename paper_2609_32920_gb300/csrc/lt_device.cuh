@@ -158,7 +158,11 @@ struct Census {
 };
 
 // Closest hit: smallest t > kTMin, ties to the smaller original primitive id; `skip`
-// (leaf-order index) is the primitive the ray leaves.  Stackless threaded traversal.
+// (leaf-order index) is the primitive the ray leaves.  Stackless threaded traversal in
+// "while-while" form (Aila & Laine, "Understanding the efficiency of ray traversal on
+// GPUs", HPG 2009): each lane walks inner nodes until it has a leaf pending (or is done),
+// then the warp tests all pending leaves together, so leaf work is not serialised lane by
+// lane.
 template <bool ST = false>
 __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, float3 dir, int skip,
                                                 Census* cs = nullptr) {
@@ -166,71 +170,78 @@ __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, f
   HitRec h;
   h.prim = -1; h.t = 3.0e38f; h.b1 = 0; h.b2 = 0;
   int best_orig = 0x7fffffff;
-  float3 inv = safe_inv(dir);
+  const float3 inv = safe_inv(dir);
   int i = 0;
-  while (i < S.n_nodes) {
-    float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
-    int skipi = __float_as_int(lo.w);
-    if (ST) cs->nodes++;
-    if (hit_box(lo, hi, org, inv, h.t)) {
-      int leaf = __float_as_int(hi.w);
-      int cnt = leaf & 255;
-      if (cnt) {
-        int first = leaf >> 8;
-        for (int k = first; k < first + cnt; ++k) {
-          if (k == skip) continue;
-          if (ST) cs->prims++;
-          Prim p = load_prim(S, k);
-          float t, u, v;
-          if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
-              (t < h.t || (t == h.t && p.orig < best_orig))) {
-            h.prim = k; h.t = t; h.b1 = u; h.b2 = v; best_orig = p.orig;
-          }
+  while (true) {
+    int first = 0, cnt = 0;
+    while (i < S.n_nodes) {
+      const float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
+      const int skipi = __float_as_int(lo.w);
+      if (ST) cs->nodes++;
+      if (hit_box(lo, hi, org, inv, h.t)) {
+        const int leaf = __float_as_int(hi.w);
+        if (leaf & 255) {
+          first = leaf >> 8;
+          cnt = leaf & 255;
+          i = skipi;
+          break;
         }
-        i = skipi;
-      } else {
         i = i + 1;
+      } else {
+        i = skipi;
       }
-    } else {
-      i = skipi;
+    }
+    if (!cnt) break;
+    for (int k = first; k < first + cnt; ++k) {
+      if (k == skip) continue;
+      if (ST) cs->prims++;
+      const Prim p = load_prim(S, k);
+      float t, u, v;
+      if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
+          (t < h.t || (t == h.t && p.orig < best_orig))) {
+        h.prim = k; h.t = t; h.b1 = u; h.b2 = v; best_orig = p.orig;
+      }
     }
   }
   return h;
 }
 
-// Any hit in (kTMin, dist - kTMin) (sensor-connection visibility).
+// Any hit in (kTMin, dist - kTMin) (sensor-connection visibility), same traversal form.
 template <bool ST = false>
 __device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 dir, float dist, int skip,
                                          Census* cs = nullptr) {
   if (ST) cs->rays++;
-  float3 inv = safe_inv(dir);
-  float tmax = dist - kTMin;
+  const float3 inv = safe_inv(dir);
+  const float tmax = dist - kTMin;
   int i = 0;
-  while (i < S.n_nodes) {
-    float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
-    int skipi = __float_as_int(lo.w);
-    if (ST) cs->nodes++;
-    if (hit_box(lo, hi, org, inv, tmax)) {
-      int leaf = __float_as_int(hi.w);
-      int cnt = leaf & 255;
-      if (cnt) {
-        int first = leaf >> 8;
-        for (int k = first; k < first + cnt; ++k) {
-          if (k == skip) continue;
-          if (ST) cs->prims++;
-          Prim p = load_prim(S, k);
-          float t, u, v;
-          if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) return true;
+  while (true) {
+    int first = 0, cnt = 0;
+    while (i < S.n_nodes) {
+      const float4 lo = __ldg(S.node + 2 * i), hi = __ldg(S.node + 2 * i + 1);
+      const int skipi = __float_as_int(lo.w);
+      if (ST) cs->nodes++;
+      if (hit_box(lo, hi, org, inv, tmax)) {
+        const int leaf = __float_as_int(hi.w);
+        if (leaf & 255) {
+          first = leaf >> 8;
+          cnt = leaf & 255;
+          i = skipi;
+          break;
         }
-        i = skipi;
-      } else {
         i = i + 1;
+      } else {
+        i = skipi;
       }
-    } else {
-      i = skipi;
+    }
+    if (!cnt) return false;
+    for (int k = first; k < first + cnt; ++k) {
+      if (k == skip) continue;
+      if (ST) cs->prims++;
+      const Prim p = load_prim(S, k);
+      float t, u, v;
+      if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) return true;
     }
   }
-  return false;
 }
 
 // ------------------------------------------------------------------ camera / film
@@ -252,7 +263,28 @@ __device__ __forceinline__ bool project(const DevScene& S, float3 x, float& ux, 
 struct Conn {
   bool valid;
   float ux, uy, geo;
+  float3 wc;   // unit direction to the camera
+  float dist;  // distance to the camera
 };
+
+// The connection tests that need no ray: camera in the arrival hemisphere, in front of
+// the camera and on the film.  Fills geo, u, wc and dist; valid = candidate.
+__device__ __forceinline__ Conn connect_pre(const DevScene& S, float3 x, float3 ns) {
+  Conn c;
+  c.valid = false; c.ux = c.uy = c.geo = 0.0f;
+  float3 cv = S.cpos - x;
+  c.dist = length(cv);
+  c.wc = cv * (1.0f / c.dist);
+  float cosc = dot(ns, c.wc);
+  if (!(cosc > 0.0f)) return c;
+  float zc;
+  if (!project(S, x, c.ux, c.uy, zc)) return c;
+  if (!(c.ux >= 0.0f && c.ux < (float)S.W && c.uy >= 0.0f && c.uy < (float)S.H)) return c;
+  float cc = zc / c.dist;
+  c.geo = cosc * S.K0 / (c.dist * c.dist * cc * cc * cc);
+  c.valid = true;
+  return c;
+}
 template <bool ST = false>
 __device__ __forceinline__ Conn connect(const DevScene& S, float3 x, float3 ns, int prim, bool test_vis = true,
                                         Census* cs = nullptr) {

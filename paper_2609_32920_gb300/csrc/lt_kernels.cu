@@ -99,7 +99,23 @@ struct Vtx {
   bool diffuse;
 };
 
-// Returns false when the path ends (miss or emitter hit).
+// Complete a closest-hit record into a vertex; false when the path ends (miss or emitter).
+__device__ __forceinline__ bool walk_finish(const DevScene& S, const Walk& w, const HitRec& h, Vtx& v) {
+  if (h.prim < 0) return false;
+  v.prim = h.prim;
+  v.P = load_prim(S, h.prim);
+  v.m = __ldg(S.mat + v.P.mat);
+  if (v.m.x == MAT_EMITTER) return false;
+  v.b1 = h.b1; v.b2 = h.b2;
+  v.attached = w.prev_kind != K_SPECULAR;
+  v.x = v.attached ? v.P.o + v.P.e1 * h.b1 + v.P.e2 * h.b2 : w.org + w.dir * h.t;
+  v.nraw = cross(v.P.e1, v.P.e2);
+  v.n = normalize(v.nraw);
+  v.diffuse = v.m.x == MAT_DIFFUSE;
+  return true;
+}
+
+// Per-lane version (divergent callers): trace and complete the next vertex.
 template <bool ST = false>
 __device__ __forceinline__ bool walk_hit(const DevScene& S, const Walk& w, Vtx& v, Census* cs = nullptr) {
   HitRec h = trace_closest<ST>(S, w.org, w.dir, w.skip, cs);
@@ -161,6 +177,41 @@ __device__ __forceinline__ void block_add3(float* dst, float3 v) {
     a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
     if (lane == 0 && dst) { atomicAdd(dst, a); atomicAdd(dst + 1, b); atomicAdd(dst + 2, c); }
   }
+}
+
+// Gradient sink of a block: when the parameter arrays fit in shared memory each block
+// accumulates its gradients there (shared-memory atomics) and adds them to the global
+// arrays once at the end; the albedo and height arrays are small and every path touches
+// them, so global atomics on them contend heavily.
+struct Sink {
+  float* alb;
+  float* h;
+};
+__device__ __forceinline__ Sink sink_begin(const KParams& kp, const GradPtrs& g, float* sh) {
+  Sink s;
+  s.alb = g.d_albedo;
+  s.h = g.d_heights;
+  if (kp.priv_n > 0) {
+    for (int i = threadIdx.x; i < kp.priv_n; i += blockDim.x) sh[i] = 0.0f;
+    __syncthreads();
+    if (g.d_albedo) s.alb = sh;
+    if (g.d_heights) s.h = sh + kp.n_alb;
+  }
+  return s;
+}
+__device__ __forceinline__ void sink_end(const KParams& kp, const GradPtrs& g, const float* sh) {
+  if (kp.priv_n <= 0) return;
+  __syncthreads();
+  if (g.d_albedo)
+    for (int i = threadIdx.x; i < kp.n_alb; i += blockDim.x) {
+      const float v = sh[i];
+      if (v != 0.0f) atomicAdd(g.d_albedo + i, v);
+    }
+  if (g.d_heights)
+    for (int i = threadIdx.x; i < kp.n_h; i += blockDim.x) {
+      const float v = sh[kp.n_alb + i];
+      if (v != 0.0f) atomicAdd(g.d_heights + i, v);
+    }
 }
 
 // Albedo gradient at one diffuse vertex: weight (per channel) / rho times the bilinear
@@ -504,107 +555,227 @@ __device__ __forceinline__ void att_enter(const DevScene& S, const KParams& kp, 
   }
 }
 
+// ======================================================================= lane regeneration
+// Each warp owns a contiguous range of path indices and hands the next one to every lane
+// that has finished its path, so lanes never idle while a slower lane finishes (all 32
+// lanes call take() together at the top of the step loop).
+struct Dispenser {
+  int64_t next, end;
+  __device__ __forceinline__ void init(int64_t n_paths) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t per = (n_paths + warps - 1) / warps;
+    next = min(wid * per, n_paths);
+    end = min(next + per, n_paths);
+  }
+  // Lanes with `want` receive a path index, or -1 when the warp's range is exhausted.
+  __device__ __forceinline__ int64_t take(bool want) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    const unsigned lane = threadIdx.x & 31;
+    int64_t mine = -1;
+    if (want) {
+      int64_t cand = next + __popc(m & ((1u << lane) - 1u));
+      mine = cand < end ? cand : -1;
+    }
+    next += __popc(m);
+    return mine;
+  }
+};
+
 // ======================================================================= primal
+// One lane per path with lane regeneration (see Dispenser): each iteration of the step
+// loop performs one vertex of the lane's current path.
 template <int EST>
 __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
+  Dispenser disp;
+  disp.init(kp.n_paths);
+  bool busy = false, more = true, active = false;
+  int64_t p = 0;
+  int k = 0, nconn = 0;
+  uint32_t hash = 0;
+  Walk w;
+  // reservoir (capacity one)
+  float Om = 0.0f, wR = 0.0f, Rux = 0.0f, Ruy = 0.0f;
+  float3 LR = f3(0, 0, 0);
+  int R = -1;
+  while (true) {
+    const bool want = more && !busy;
+    const int64_t got = disp.take(want);
+    if (want) {
+      if (got < 0) {
+        more = false;
+      } else {
+        p = got;
+        active = !kp.mask || kp.mask[p];
+        float3 x0;
+        walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
+        hash = 2166136261u;
+        nconn = 0;
+        k = 0;
+        Om = wR = Rux = Ruy = 0.0f;
+        LR = f3(0, 0, 0);
+        R = -1;
+        busy = true;
+      }
+    }
+    if (!__any_sync(0xffffffffu, busy || more)) break;
+    const bool trav = busy && k < kp.max_depth;
+    HitRec h;
+    h.prim = -1;
+    if (trav) h = trace_closest(S, w.org, w.dir, w.skip);
+    Vtx v;
+    const bool alive = trav && walk_finish(S, w, h, v);
+    float3 ns = f3(0, 0, 0);
+    Conn c;
+    c.valid = false; c.ux = c.uy = 0.0f;
+    if (alive && v.diffuse) {
+      ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+      c = connect_pre(S, v.x, ns);
+    }
+    if (c.valid && occluded(S, v.x, c.wc, c.dist, v.prim)) c.valid = false;
+    if (!busy) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
-    const bool active = !kp.mask || kp.mask[p];
-    Walk w;
-    float3 x0;
-    walk_start(S, kp.seed, n, Le, w, x0);
-    uint32_t hash = 2166136261u;
-    int nconn = 0, depth = 0;
-    // reservoir (capacity one)
-    float Om = 0.0f, wR = 0.0f, Rux = 0.0f, Ruy = 0.0f;
-    float3 LR = f3(0, 0, 0);
-    int R = -1;
-    for (int k = 0; k < kp.max_depth; ++k) {
-      Vtx v;
-      if (!walk_hit(S, w, v)) break;
-      depth = k + 1;
-      float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
-      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
-      Conn c;
-      c.valid = false; c.ux = c.uy = 0.0f;
-      float3 L = f3(0, 0, 0);
-      if (v.diffuse) {
-        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
-        c = connect(S, v.x, ns, v.prim);
-        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
-        if (c.valid) {
-          ++nconn;
-          L = mul(w.beta, rho) * (c.geo * kp.inv_n);
-          if (active) {
-            if (EST == 1) {
-              float om = luminance(L);
-              if (om > 0.0f) {
-                Om += om;
-                if (r.w < om / Om) { R = k; wR = om; LR = L; Rux = c.ux; Ruy = c.uy; }
-              }
-            } else {
-              splat(image, S.W, S.H, c.ux, c.uy, L);
+    if (!alive) {
+      // end of the path: reservoir record / tape length / per-path outputs
+      if (EST == 1) {
+        float4* rec = (float4*)aux + 2 * p;
+        float wgt = R >= 0 ? Om / wR : 0.0f;
+        float3 Sh = LR * wgt;
+        if (active && R >= 0) splat(image, S.W, S.H, Rux, Ruy, Sh);
+        rec[0] = make_float4(__int_as_float(active ? R : -1), wgt, Rux, Ruy);
+        rec[1] = make_float4(Sh.x, Sh.y, Sh.z, 0.0f);
+      }
+      if (EST == 2) ((int*)aux)[p] = active ? k : 0;
+      if (kp.hash) kp.hash[p] = hash;
+      if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4((float)nconn, (float)k, 0.0f, 0.0f);
+      busy = false;
+      continue;
+    }
+    float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+    float3 rho = f3(0, 0, 0);
+    float3 L = f3(0, 0, 0);
+    if (v.diffuse) {
+      rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
+      if (c.valid) {
+        ++nconn;
+        L = mul(w.beta, rho) * (c.geo * kp.inv_n);
+        if (active) {
+          if (EST == 1) {
+            float om = luminance(L);
+            if (om > 0.0f) {
+              Om += om;
+              if (r.w < om / Om) { R = k; wR = om; LR = L; Rux = c.ux; Ruy = c.uy; }
             }
+          } else {
+            splat(image, S.W, S.H, c.ux, c.uy, L);
           }
         }
       }
-      bool refl = walk_scatter(S, w, v, ns, rho, r);
-      fnv(hash, (uint32_t)v.P.orig);
-      fnv(hash, vtx_flags(v, refl, c.valid));
-      if (EST == 2 && active) {
-        // naive-AD tape: [depth][path] records of two float4
-        float4* tape = (float4*)((char*)aux + kp.tape_offset) + 2 * ((size_t)k * kp.n_paths + p);
-        uint32_t fl = vtx_flags(v, refl, c.valid);
-        tape[0] = make_float4(__int_as_float(v.prim | (int)(fl << 24)), v.b1, v.b2, c.ux);
-        tape[1] = make_float4(L.x, L.y, L.z, c.uy);
-      }
     }
-    if (EST == 1) {
-      float4* rec = (float4*)aux + 2 * p;
-      float wgt = R >= 0 ? Om / wR : 0.0f;
-      float3 Sh = LR * wgt;
-      if (active && R >= 0) splat(image, S.W, S.H, Rux, Ruy, Sh);
-      rec[0] = make_float4(__int_as_float(active ? R : -1), wgt, Rux, Ruy);
-      rec[1] = make_float4(Sh.x, Sh.y, Sh.z, 0.0f);
+    bool refl = walk_scatter(S, w, v, ns, rho, r);
+    fnv(hash, (uint32_t)v.P.orig);
+    fnv(hash, vtx_flags(v, refl, c.valid));
+    if (EST == 2 && active) {
+      // naive-AD tape: [depth][path] records of two float4
+      float4* tape = (float4*)((char*)aux + kp.tape_offset) + 2 * ((size_t)k * kp.n_paths + p);
+      uint32_t fl = vtx_flags(v, refl, c.valid);
+      tape[0] = make_float4(__int_as_float(v.prim | (int)(fl << 24)), v.b1, v.b2, c.ux);
+      tape[1] = make_float4(L.x, L.y, L.z, c.uy);
     }
-    if (EST == 2) ((int*)aux)[p] = active ? depth : 0;
-    if (kp.hash) kp.hash[p] = hash;
-    if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4((float)nconn, (float)depth, 0.0f, 0.0f);
+    ++k;
   }
 }
 
 // ======================================================================= LRB-3-pass
-// Pass 2 (accumulate delta_total, Eq. 14) and pass 3 (backpropagate, Eq. 15-17) fused per
-// path: both replay the path from its counter; the connection-validity bits found in
-// pass 2 are kept in a register mask so pass 3 does not re-test visibility.
+// Pass 2 (accumulate delta_total, Eq. 14) and pass 3 (backpropagate, Eq. 15-17) per path,
+// run as a per-lane state machine: every iteration of the step loop performs one vertex
+// step (one closest-hit traversal) of whichever pass the lane is in, and a lane that
+// finishes a path takes the next one from its warp's range.  The connection-validity bits
+// found in pass 2 are kept in a register mask so pass 3 traces no visibility rays.
 template <bool ATT, bool ST, bool CH>
-__global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+__global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0) {
+  extern __shared__ float sgrad[];
+  const Sink sink = sink_begin(kp, g0, sgrad);
+  GradPtrs g = g0;
+  g.d_albedo = sink.alb;
+  g.d_heights = sink.h;
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
   float3 gLe = f3(0, 0, 0);
   Census cs = {0, 0, 0};
   uint32_t nverts = 0, nconns = 0;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
-    if (kp.mask && !kp.mask[p]) continue;
+  Dispenser disp;
+  disp.init(kp.n_paths);
+  enum { IDLE = 0, PASS2 = 1, PASS3 = 2 };
+  int phase = IDLE, k = 0, last = 0, nconn = 0;
+  bool more = true;
+  int64_t p = 0;
+  Walk w;
+  float3 dtot = f3(0, 0, 0), rem = f3(0, 0, 0);
+  uint64_t valid = 0;
+  PendAdj pv;
+  ChainInfo chain;
+  chain.ka = -1;
+  pv.prim = -1;
+  while (true) {
+    const bool want = more && phase == IDLE;
+    const int64_t got = disp.take(want);
+    if (want) {
+      if (got < 0) {
+        more = false;
+      } else if (!kp.mask || kp.mask[got]) {
+        p = got;
+        float3 x0;
+        walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
+        dtot = f3(0, 0, 0);
+        valid = 0;
+        nconn = 0;
+        k = 0;
+        phase = PASS2;
+      }
+    }
+    if (!__any_sync(0xffffffffu, phase != IDLE || more)) break;
+    const int kmax = phase == PASS2 ? kp.max_depth : last + 1;
+    const bool trav = phase != IDLE && k < kmax;
+    HitRec h;
+    h.prim = -1;
+    if (trav) h = trace_closest<ST>(S, w.org, w.dir, w.skip, &cs);
+    Vtx v;
+    const bool alive = trav && walk_finish(S, w, h, v);
+    float3 ns = f3(0, 0, 0);
+    Conn c;
+    c.valid = false; c.ux = c.uy = 0.0f;
+    if (alive && v.diffuse) {
+      ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+      if (phase == PASS2 || ((valid >> k) & 1ull)) c = connect_pre(S, v.x, ns);
+    }
+    // visibility only in pass 2; pass 3 reuses pass 2's validity bits
+    const bool vis = phase == PASS2 && c.valid;
+    if (vis && occluded<ST>(S, v.x, c.wc, c.dist, v.prim, &cs)) c.valid = false;
+    if (phase == IDLE) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
-    // ---------------- pass 2
-    Walk w;
-    float3 x0;
-    walk_start(S, kp.seed, n, Le, w, x0);
-    float3 dtot = f3(0, 0, 0);
-    uint64_t valid = 0;
-    int nconn = 0;
-    for (int k = 0; k < kp.max_depth; ++k) {
-      Vtx v;
-      if (!walk_hit<ST>(S, w, v, &cs)) break;
+    if (phase == PASS2) {
+      if (!alive) {
+        if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4(dtot.x, dtot.y, dtot.z, (float)nconn);
+        gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);  // emitted factor, weight delta_total
+        if (valid) {
+          float3 x0;
+          walk_start(S, kp.seed, n, Le, w, x0);
+          rem = dtot;
+          pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+          chain.ka = -1;
+          last = 63 - __clzll((long long)valid);
+          k = 0;
+          phase = PASS3;
+        } else {
+          phase = IDLE;
+        }
+        continue;
+      }
       if (ST) ++nverts;
       float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
-      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+      float3 rho = f3(0, 0, 0);
       if (v.diffuse) {
-        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
-        Conn c = connect<ST>(S, v.x, ns, v.prim, true, &cs);
         rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
         if (c.valid) {
           if (ST) ++nconns;
@@ -616,34 +787,24 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
         }
       }
       walk_scatter(S, w, v, ns, rho, r);
-    }
-    if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4(dtot.x, dtot.y, dtot.z, (float)nconn);
-    // ---------------- pass 3
-    gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);
-    if (valid == 0) continue;
-    float3 rem = dtot;
-    walk_start(S, kp.seed, n, Le, w, x0);
-    PendAdj pv;
-    pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
-    ChainInfo chain;
-    chain.ka = -1;
-    const int last = 63 - __clzll((long long)valid);
-    for (int k = 0; k <= last; ++k) {
-      Vtx v;
-      if (!walk_hit<ST>(S, w, v, &cs)) break;
+      ++k;
+    } else {
+      if (!alive) {
+        if (ATT) pend_flush<CH>(S, kp, n, pv, g.d_heights);
+        phase = IDLE;
+        continue;
+      }
       if (ST) ++nverts;
       float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
       // attached segment weight and chain bookkeeping: every connection from here on
       // carries this vertex's factors, so they weigh the remaining adjoint before Eq. 16
       if (ATT) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights);
-      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+      float3 rho = f3(0, 0, 0);
       if (v.diffuse) {
-        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
         TexFoot foot;
         rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
         float3 wsplat = f3(0, 0, 0);
         if ((valid >> k) & 1ull) {
-          Conn c = connect(S, v.x, ns, v.prim, false);
           float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
           float2 q;
           float3 Lb = adjoint_read(dI, S.W, S.H, c.ux, c.uy, L, ATT ? &q : nullptr);
@@ -657,8 +818,8 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
           pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
       }
       walk_scatter(S, w, v, ns, rho, r);
+      ++k;
     }
-    if (ATT) pend_flush<CH>(S, kp, n, pv, g.d_heights);
   }
   if (ST && kp.census) {
     atomicAdd(kp.census + 0, (unsigned long long)cs.rays);
@@ -667,6 +828,7 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
     atomicAdd(kp.census + 3, (unsigned long long)nverts);
     atomicAdd(kp.census + 4, (unsigned long long)nconns);
   }
+  sink_end(kp, g0, sgrad);
   block_add3(g.d_Le, gLe);
 }
 
@@ -675,7 +837,12 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
 // Lbar_R * S to every factor of L_R (Eq. 11); attached adds the positional channel.
 template <bool ATT, bool CH>
 __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const float* __restrict__ dI,
-                                                const float4* __restrict__ rec, GradPtrs g) {
+                                                const float4* __restrict__ rec, GradPtrs g0) {
+  extern __shared__ float sgrad[];
+  const Sink sink = sink_begin(kp, g0, sgrad);
+  GradPtrs g = g0;
+  g.d_albedo = sink.alb;
+  g.d_heights = sink.h;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
   float3 gLe = f3(0, 0, 0);
@@ -719,6 +886,7 @@ __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const fl
     }
     if (ATT) pend_flush<CH>(S, kp, n, pv, g.d_heights);
   }
+  sink_end(kp, g0, sgrad);
   block_add3(g.d_Le, gLe);
 }
 
@@ -726,7 +894,12 @@ __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const fl
 // Reverse sweep over the per-vertex tape: suffix sums of Lbar_i L_i replace the replay.
 template <bool ATT, bool CH>
 __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const float* __restrict__ dI,
-                                               const void* __restrict__ ws, GradPtrs g) {
+                                               const void* __restrict__ ws, GradPtrs g0) {
+  extern __shared__ float sgrad[];
+  const Sink sink = sink_begin(kp, g0, sgrad);
+  GradPtrs g = g0;
+  g.d_albedo = sink.alb;
+  g.d_heights = sink.h;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
   float3 gLe = f3(0, 0, 0);
@@ -811,6 +984,7 @@ __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const flo
     }
     gLe = gLe + f3(acc.x / Le.x, acc.y / Le.y, acc.z / Le.z);
   }
+  sink_end(kp, g0, sgrad);
   block_add3(g.d_Le, gLe);
 }
 
@@ -867,14 +1041,15 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
 cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                         const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
+  const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
   if (kp.census) {
-    if (att && chains) k_lrb3<true, true, true><<<grid, L.block, 0, st>>>(S, kp, dI, g);
-    else if (att) k_lrb3<true, true, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
-    else k_lrb3<false, true, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+    if (att && chains) k_lrb3<true, true, true><<<grid, L.block, smem, st>>>(S, kp, dI, g);
+    else if (att) k_lrb3<true, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
+    else k_lrb3<false, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
   } else {
-    if (att && chains) k_lrb3<true, false, true><<<grid, L.block, 0, st>>>(S, kp, dI, g);
-    else if (att) k_lrb3<true, false, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
-    else k_lrb3<false, false, false><<<grid, L.block, 0, st>>>(S, kp, dI, g);
+    if (att && chains) k_lrb3<true, false, true><<<grid, L.block, smem, st>>>(S, kp, dI, g);
+    else if (att) k_lrb3<true, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
+    else k_lrb3<false, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
   }
   return cudaGetLastError();
 }
@@ -882,18 +1057,20 @@ cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool cha
 cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                           const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
-  if (att && chains) k_reslrb<true, true><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
-  else if (att) k_reslrb<true, false><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
-  else k_reslrb<false, false><<<grid, L.block, 0, st>>>(S, kp, dI, (const float4*)rec, g);
+  const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
+  if (att && chains) k_reslrb<true, true><<<grid, L.block, smem, st>>>(S, kp, dI, (const float4*)rec, g);
+  else if (att) k_reslrb<true, false><<<grid, L.block, smem, st>>>(S, kp, dI, (const float4*)rec, g);
+  else k_reslrb<false, false><<<grid, L.block, smem, st>>>(S, kp, dI, (const float4*)rec, g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                          const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
-  if (att && chains) k_naive<true, true><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
-  else if (att) k_naive<true, false><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
-  else k_naive<false, false><<<grid, L.block, 0, st>>>(S, kp, dI, ws, g);
+  const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
+  if (att && chains) k_naive<true, true><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
+  else if (att) k_naive<true, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
+  else k_naive<false, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
   return cudaGetLastError();
 }
 

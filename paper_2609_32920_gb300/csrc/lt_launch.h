@@ -21,6 +21,8 @@ struct KParams {
   float* dbg;                // DEVICE [n_paths][4] or null
   size_t tape_offset;        // naive tape: bytes before the first record
   unsigned long long* census;  // DEVICE [5] or null: rays, box tests, primitive tests, vertices, connections
+  int n_alb, n_h;              // parameter counts
+  int priv_n;                  // > 0: gradients accumulate in n_alb + n_h floats of shared memory per block
 };
 
 struct GradPtrs {
