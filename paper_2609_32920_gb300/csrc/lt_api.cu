@@ -307,14 +307,19 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
                        {o.x + e1.x + e2.x, o.y + e1.y + e2.y, o.z + e1.z + e2.z}};
     for (int k = 0; k < (i < nq ? 4 : 3); ++k) boxes[i].grow(pts[k]);
   }
-  Builder B(boxes);
-  B.build(0, np, 0);
+  // Up to kDirect analytic quads (walls, emitters: few and large) are tested directly by
+  // every ray; the BVH covers the remaining primitives.
+  const int kDirect = 32;
+  const int nd = nq <= kDirect ? nq : 0;
+  std::vector<Box> bvh_boxes(boxes.begin() + nd, boxes.end());
+  Builder B(bvh_boxes);
+  if (np > nd) B.build(0, np - nd, 0);
   // flatten in depth-first preorder; leaves take consecutive slots of the leaf order
   std::vector<float4> node;
   std::vector<int2> range;
   std::vector<int> order;  // leaf order -> original primitive
   std::vector<int> pre;  // preorder of builder nodes
-  {
+  if (!B.nodes.empty()) {
     std::vector<int> stk = {0};
     while (!stk.empty()) {
       int b = stk.back();
@@ -339,8 +344,8 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
     int skip = i + size[pre[i]];
     int leafinfo = 0;
     if (bn.left < 0) {
-      int first = (int)order.size();
-      for (int k = bn.begin; k < bn.end; ++k) order.push_back(B.idx[k]);
+      int first = nd + (int)order.size();
+      for (int k = bn.begin; k < bn.end; ++k) order.push_back(nd + B.idx[k]);
       leafinfo = (first << 8) | (bn.end - bn.begin);
     }
     node[2 * i] = make_float4(bn.box.lo[0], bn.box.lo[1], bn.box.lo[2], 0.0f);
@@ -350,9 +355,15 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
   }
   // prim ranges: the builder kept each subtree contiguous in B.idx and leaves were
   // emitted in preorder, so build-order positions equal leaf-order positions
-  for (int i = 0; i < nn; ++i) range[i] = make_int2(B.nodes[pre[i]].begin, B.nodes[pre[i]].end);
-  for (int i = 0; i < np; ++i)
-    if (order[i] != B.idx[i]) return fail(LT_ERR_INVALID_ARG, "internal: BVH leaf order mismatch");
+  for (int i = 0; i < nn; ++i) range[i] = make_int2(nd + B.nodes[pre[i]].begin, nd + B.nodes[pre[i]].end);
+  for (int i = 0; i < np - nd; ++i)
+    if (order[i] != nd + B.idx[i]) return fail(LT_ERR_INVALID_ARG, "internal: BVH leaf order mismatch");
+  {
+    std::vector<int> full(np);
+    for (int i = 0; i < nd; ++i) full[i] = i;
+    for (int i = nd; i < np; ++i) full[i] = order[i - nd];
+    order.swap(full);
+  }
   // leaf-order primitive arrays
   std::vector<float4> prim(3 * np), tri_base(3 * np, make_float4(0, 0, 0, 0));
   std::vector<int4> prim_h(np, make_int4(-1, -1, -1, -1));
@@ -412,6 +423,7 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
   }
   DevScene& S = s->dev;
   S.prim = s->d_prim; S.prim_h = s->d_prim_h; S.node = s->d_node; S.n_nodes = nn; S.n_prims = np;
+  S.n_direct = nd;
   S.mat = s->d_mat; S.mat_ior = s->d_ior; S.emitter_prim = emitter_leaf; S.err = s->d_err;
   const float* q = d->quads + 9 * d->emitter_quad;
   HV lo = hv(q[0], q[1], q[2]), le1 = hv(q[3], q[4], q[5]), le2 = hv(q[6], q[7], q[8]);
@@ -433,6 +445,7 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
   S.W = d->width; S.H = d->height;
   // initial bounds
   RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, nullptr, np, s->d_node, s->d_range, nn};
+  if (nn == 0) ra.n_nodes = 0;
   e = launch_refit(ra, st);
   if (e) { free_scene(s); return fail(LT_ERR_CUDA, std::string("refit: ") + cudaGetErrorString(e)); }
   *out = s;

@@ -23,13 +23,15 @@ enum ErrBits : int { ERR_BOUNDS = 1, ERR_TIMEOUT = 2, ERR_NAN = 4 };
 //   prim[3i+2] = (e2.xyz, 1 if triangle else 0 as int bits)
 //   prim_h[i]  = height-parameter indices of the three triangle vertices (or -1)
 //   node[2j+0] = (lo.xyz, skip index)  node[2j+1] = (hi.xyz, leaf first*256 + count)
-// Threaded BVH in depth-first preorder: the first child of an inner node j is j+1, and
-// `skip` is the next node after j's subtree; leaves have count > 0.
+// Threaded BVH in depth-first preorder over primitives [n_direct, n_prims): the first child
+// of an inner node j is j+1, and `skip` is the next node after j's subtree; leaves have
+// count > 0.  The few large analytic quads [0, n_direct) are tested directly by every ray.
 struct DevScene {
   const float4* prim;
   const int4* prim_h;
   const float4* node;
   int n_nodes, n_prims;
+  int n_direct;           // primitives [0, n_direct) are tested directly by every ray (large quads)
   const int4* mat;        // (type, tex_off, tex_w, tex_h)
   const float* mat_ior;
   int emitter_prim;       // index in leaf order
@@ -170,6 +172,16 @@ __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, f
   HitRec h;
   h.prim = -1; h.t = 3.0e38f; h.b1 = 0; h.b2 = 0;
   int best_orig = 0x7fffffff;
+  for (int k = 0; k < S.n_direct; ++k) {
+    if (k == skip) continue;
+    if (ST) cs->prims++;
+    const Prim p = load_prim(S, k);
+    float t, u, v;
+    if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
+        (t < h.t || (t == h.t && p.orig < best_orig))) {
+      h.prim = k; h.t = t; h.b1 = u; h.b2 = v; best_orig = p.orig;
+    }
+  }
   const float3 inv = safe_inv(dir);
   int i = 0;
   while (true) {
@@ -211,8 +223,15 @@ template <bool ST = false>
 __device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 dir, float dist, int skip,
                                          Census* cs = nullptr) {
   if (ST) cs->rays++;
-  const float3 inv = safe_inv(dir);
   const float tmax = dist - kTMin;
+  for (int k = 0; k < S.n_direct; ++k) {
+    if (k == skip) continue;
+    if (ST) cs->prims++;
+    const Prim p = load_prim(S, k);
+    float t, u, v;
+    if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) return true;
+  }
+  const float3 inv = safe_inv(dir);
   int i = 0;
   while (true) {
     int first = 0, cnt = 0;

@@ -1022,8 +1022,10 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
   if (a.n_prims > 0 && a.heights) {
     k_update_tris<<<(a.n_prims + 255) / 256, 256, 0, st>>>(a.prim, a.prim_h, a.tri_base, a.heights, a.n_prims);
   }
-  int threads = a.n_nodes * 32;
-  k_refit_nodes<<<(threads + 255) / 256, 256, 0, st>>>(a.node, a.range, a.prim, a.n_nodes);
+  if (a.n_nodes > 0) {
+    int threads = a.n_nodes * 32;
+    k_refit_nodes<<<(threads + 255) / 256, 256, 0, st>>>(a.node, a.range, a.prim, a.n_nodes);
+  }
   return cudaGetLastError();
 }
 
