@@ -173,6 +173,47 @@ lt_status lt_backward_naive(lt_scene* scene, const lt_params* params, const lt_r
 lt_status lt_film_l2(const float* image, const float* target, int64_t n, float* d_image, float* loss,
                      void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Learned reservoir target.  A 16 -> 64 -> 64 -> 1 ReLU network (BF16 weights, FP32
+ * accumulation on tensor cores) predicts, from a sensor connection's features, the log of
+ * the adjoint weight |Lbar_i * L_i|_1 / lum(L_i) the connection will see; ResLRB then uses
+ * omega_i = lum(L_i) (exp(sigma * y_i) + 1e-3) (sigma = target scale) in place of the
+ * luminance of Eq. 8.  Because Eq. 10 holds for any positive weights the estimator stays
+ * unbiased; only its variance changes.  Parameter block: LT_MLP_PARAMS floats (DEVICE,
+ * FP32): W1[16][64] b1[64] W2[64][64] b2[64] W3[64] b3 | feature mean[16] | feature
+ * 1/std[16] | target scale | target mean | padding.  Pass it as opts->mlp with
+ * opts->target = LT_TARGET_MLP to lt_primal(LT_EST_RESLRB).
+ * Features (16): vertex position (3), arrival-side normal (3), arrival direction (3),
+ * log throughput (3), (depth index + 1) / max_depth, film u / width, film v / height,
+ * log of the connection weight. */
+#define LT_MLP_PARAMS 5352
+#define LT_MLP_WEIGHTS 5313
+
+/* Training pairs from an LRB-3 pass-2 replay (Eq. 14): for every valid connection, its 16
+ * features into feats [capacity][16] and its target log(|Lbar*L|_1 / lum(L) + floor) into
+ * targets [capacity] (DEVICE).  *count (DEVICE int64, zeroed by this call) receives the
+ * number of connections found; only the first `capacity` are written. */
+lt_status lt_mlp_collect(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                         const float* d_image, float target_floor, float* feats, float* targets,
+                         int64_t capacity, int64_t* count, void* stream);
+
+/* Set the standardisation statistics of the parameter block from n training pairs. */
+lt_status lt_mlp_init_stats(float* mlp, const float* feats, const float* targets, int64_t n, void* stream);
+
+/* Gradient of the mean squared error of the standardized target over samples [0, n) of a
+ * batch of size `batch` (added into grad [LT_MLP_WEIGHTS], DEVICE; the mean loss is added
+ * into *loss, DEVICE).  Forward and backward GEMM tiles run on tensor cores. */
+lt_status lt_mlp_grad(const float* mlp, const float* feats, const float* targets, int64_t n, int64_t batch,
+                      float* grad, float* loss, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; `step` counts from 1) on the trainable
+ * block, with moment buffers m, v [LT_MLP_WEIGHTS] (DEVICE). */
+lt_status lt_mlp_adam(float* mlp, float* m, float* v, const float* grad, int step, float learning_rate,
+                      void* stream);
+
+/* Network outputs (standardized target units) for n feature rows (DEVICE). */
+lt_status lt_mlp_forward(const float* mlp, const float* feats, int64_t n, float* out, void* stream);
+
 /* Bytes of one ResLRB record (constant per path). */
 size_t lt_record_size(const lt_render_opts* opts);
 /* Bytes of the naive-AD tape for opts (n_paths * max_depth * record). */

@@ -1023,3 +1023,98 @@ int or_render_pt(const or_scene* s, const or_params* p, uint64_t seed, int spp, 
 }
 
 }  // extern "C"
+
+// =============================================================== learned reservoir target
+// FP64 reference of the 16 -> 64 -> 64 -> 1 ReLU network (parameter block layout as the
+// library's: W1[16][64] b1[64] W2[64][64] b2[64] W3[64] b3 | mean[16] 1/std[16] | target
+// scale, target mean).  With `round` set it applies the same BFloat16 roundings as the
+// tensor-core path (standardized inputs, weights W1 W2 W3, hidden activations after ReLU);
+// the backward treats those roundings as identity (straight-through).
+namespace {
+double bf16_round(double x) {
+  float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even on the upper 16 bits
+  u &= 0xFFFF0000u;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+struct MlpRef {
+  const double* P;
+  bool round;
+  double W1(int k, int o) const { double w = P[k * 64 + o]; return round ? bf16_round(w) : w; }
+  double W2(int k, int o) const { double w = P[1088 + k * 64 + o]; return round ? bf16_round(w) : w; }
+  double W3(int k) const { double w = P[5248 + k]; return round ? bf16_round(w) : w; }
+  void forward(const double* f, double x[16], double z1[64], double h1[64], double z2[64], double h2[64], double& y) const {
+    for (int i = 0; i < 16; ++i) {
+      x[i] = (double)(float)(((float)f[i] - (float)P[5313 + i]) * (float)P[5329 + i]);
+      if (round) x[i] = bf16_round(x[i]);
+    }
+    for (int o = 0; o < 64; ++o) {
+      double a = P[1024 + o];
+      for (int k = 0; k < 16; ++k) a += x[k] * W1(k, o);
+      z1[o] = a;
+      h1[o] = a > 0 ? a : 0.0;
+      if (round) h1[o] = bf16_round(h1[o]);
+    }
+    for (int o = 0; o < 64; ++o) {
+      double a = P[5184 + o];
+      for (int k = 0; k < 64; ++k) a += h1[k] * W2(k, o);
+      z2[o] = a;
+      h2[o] = a > 0 ? a : 0.0;
+      if (round) h2[o] = bf16_round(h2[o]);
+    }
+    y = P[5312];
+    for (int k = 0; k < 64; ++k) y += h2[k] * W3(k);
+  }
+};
+}  // namespace
+
+extern "C" {
+void or_mlp_forward(const double* P, const double* X, int64_t n, int round, double* out) {
+  MlpRef M{P, round != 0};
+  for (int64_t s = 0; s < n; ++s) {
+    double x[16], z1[64], h1[64], z2[64], h2[64], y;
+    M.forward(X + 16 * s, x, z1, h1, z2, h2, y);
+    out[s] = y;
+  }
+}
+
+// Gradient of L = (1/n) sum_s (y_s - t_s)^2 with t_s = (T_s - target mean) / target scale,
+// by hand-written reverse mode (chain rule through the three layers).
+double or_mlp_grad(const double* P, const double* X, const double* T, int64_t n, int round, double* grad) {
+  MlpRef M{P, round != 0};
+  for (int i = 0; i < 5313; ++i) grad[i] = 0.0;
+  double loss = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    double x[16], z1[64], h1[64], z2[64], h2[64], y;
+    M.forward(X + 16 * s, x, z1, h1, z2, h2, y);
+    const double t = (T[s] - P[5346]) / P[5345];
+    const double e = y - t;
+    loss += e * e / (double)n;
+    const double dy = 2.0 * e / (double)n;
+    grad[5312] += dy;
+    double dz2[64], dh1[64];
+    for (int k = 0; k < 64; ++k) {
+      grad[5248 + k] += dy * h2[k];
+      dz2[k] = z2[k] > 0 ? dy * M.W3(k) : 0.0;
+      grad[5184 + k] += dz2[k];
+    }
+    for (int i = 0; i < 64; ++i) {
+      double a = 0.0;
+      for (int j = 0; j < 64; ++j) {
+        grad[1088 + i * 64 + j] += h1[i] * dz2[j];
+        a += dz2[j] * M.W2(i, j);
+      }
+      dh1[i] = a;
+    }
+    for (int i = 0; i < 64; ++i) {
+      const double dz1 = z1[i] > 0 ? dh1[i] : 0.0;
+      grad[1024 + i] += dz1;
+      for (int k = 0; k < 16; ++k) grad[k * 64 + i] += x[k] * dz1;
+    }
+  }
+  return loss;
+}
+}  // extern "C"

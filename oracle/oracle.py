@@ -86,6 +86,9 @@ def lib():
             L.or_reservoir.restype = C.c_int
             L.or_intersect.argtypes = [P(or_scene), P(or_params), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
             L.or_intersect.restype = C.c_int
+            L.or_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]
+            L.or_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]
+            L.or_mlp_grad.restype = C.c_double
             _lib = L
     return _lib
 
@@ -246,3 +249,20 @@ def intersect(scene, org, dir, skip=-1):
     out = np.zeros(3)
     prim = lib().or_intersect(C.byref(b.sc), C.byref(b.params), o.ctypes.data, d.ctypes.data, skip, out.ctypes.data)
     return prim, out
+
+
+def mlp_forward(P, X, round_bf16=True):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 16)
+    out = np.zeros(X.shape[0])
+    lib().or_mlp_forward(P.ctypes.data, X.ctypes.data, X.shape[0], int(round_bf16), out.ctypes.data)
+    return out
+
+
+def mlp_grad(P, X, T, round_bf16=True):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 16)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    g = np.zeros(5313)
+    loss = lib().or_mlp_grad(P.ctypes.data, X.ctypes.data, T.ctypes.data, X.shape[0], int(round_bf16), g.ctypes.data)
+    return g, float(loss)

@@ -14,7 +14,7 @@ OUT = os.path.join(PKG, "liblt.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
-SOURCES = ["lt_api.cu", "lt_kernels.cu"]
+SOURCES = ["lt_api.cu", "lt_kernels.cu", "lt_mlp.cu"]
 
 
 def _nvcc():

@@ -227,8 +227,8 @@ lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 1024 || o->block_size % 32))
     return fail(LT_ERR_INVALID_ARG, "block_size must be a multiple of 32 in 32..1024 (or 0)");
   if (o->block_size > 128) return fail(LT_ERR_INVALID_ARG, "kernels are compiled for at most 128 threads per block");
-  if (o->target == LT_TARGET_MLP) return fail(LT_ERR_UNSUPPORTED, "learned reservoir target not available in this call");
-  if (o->target != LT_TARGET_LUMINANCE) return fail(LT_ERR_INVALID_ARG, "unknown reservoir target");
+  if (o->target != LT_TARGET_LUMINANCE && o->target != LT_TARGET_MLP) return fail(LT_ERR_INVALID_ARG, "unknown reservoir target");
+  if (o->target == LT_TARGET_MLP && !o->mlp) return fail(LT_ERR_INVALID_ARG, "LT_TARGET_MLP needs opts->mlp");
   return LT_OK;
 }
 
@@ -247,6 +247,7 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.tape_offset = ((size_t)o->n_paths * sizeof(int) + 255) & ~(size_t)255;
   k.census = (unsigned long long*)o->census;
   k.n_alb = k.n_h = k.priv_n = 0;
+  k.mlp = o->target == LT_TARGET_MLP ? (const float*)o->mlp : nullptr;
   return k;
 }
 
@@ -552,6 +553,62 @@ lt_status lt_film_l2(const float* I, const float* T, int64_t n, float* dI, float
   LT_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
   cudaError_t e = launch_film_l2(I, T, n, dI, loss, sms, st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_film_l2: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_mlp_collect(lt_scene* s, const lt_params* p, const lt_render_opts* o, const float* dI, float tfloor,
+                         float* feats, float* targets, int64_t cap, int64_t* count, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!dI || !count || (cap > 0 && (!feats || !targets)) || cap < 0)
+    return fail(LT_ERR_INVALID_ARG, "lt_mlp_collect: bad buffers");
+  if (!(tfloor >= 0)) return fail(LT_ERR_INVALID_ARG, "lt_mlp_collect: target_floor must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  LT_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), st));
+  if (o->n_paths == 0) return LT_OK;
+  cudaError_t e = launch_collect(s->dev, kparams(p, o), dI, tfloor, feats, targets, cap, (unsigned long long*)count,
+                                 cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_mlp_collect: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_mlp_init_stats(float* mlp, const float* feats, const float* targets, int64_t n, void* stream) {
+  if (!mlp || !feats || !targets || n <= 1) return fail(LT_ERR_INVALID_ARG, "lt_mlp_init_stats: bad arguments");
+  cudaError_t e = launch_mlp_moments(feats, targets, n, mlp, (cudaStream_t)stream);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_mlp_init_stats: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+static int device_sms() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+lt_status lt_mlp_grad(const float* mlp, const float* feats, const float* targets, int64_t n, int64_t batch,
+                      float* grad, float* loss, void* stream) {
+  if (!mlp || !grad || n < 0 || batch <= 0 || n > batch || (n > 0 && (!feats || !targets)))
+    return fail(LT_ERR_INVALID_ARG, "lt_mlp_grad: bad arguments");
+  if (n == 0) return LT_OK;
+  cudaError_t e = launch_mlp_grad(mlp, feats, targets, n, 1.0f / (float)batch, grad, loss, device_sms(),
+                                  (cudaStream_t)stream);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_mlp_grad: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_mlp_adam(float* mlp, float* m, float* v, const float* grad, int step, float lr, void* stream) {
+  if (!mlp || !m || !v || !grad || step < 1 || !(lr > 0)) return fail(LT_ERR_INVALID_ARG, "lt_mlp_adam: bad arguments");
+  cudaError_t e = launch_mlp_adam(mlp, m, v, grad, step, lr, (cudaStream_t)stream);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_mlp_adam: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_mlp_forward(const float* mlp, const float* feats, int64_t n, float* out, void* stream) {
+  if (!mlp || n < 0 || (n > 0 && (!feats || !out))) return fail(LT_ERR_INVALID_ARG, "lt_mlp_forward: bad arguments");
+  if (n == 0) return LT_OK;
+  cudaError_t e = launch_mlp_forward(mlp, feats, n, out, device_sms(), (cudaStream_t)stream);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_mlp_forward: ") + cudaGetErrorString(e));
   return LT_OK;
 }
 

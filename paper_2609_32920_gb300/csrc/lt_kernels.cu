@@ -7,6 +7,7 @@
 
 #include "lt_device.cuh"
 #include "lt_launch.h"
+#include "lt_mlp.cuh"
 
 namespace lt {
 
@@ -555,6 +556,64 @@ __device__ __forceinline__ void att_enter(const DevScene& S, const KParams& kp, 
   }
 }
 
+// ======================================================================= learned target
+// Features of a sensor connection for the learned reservoir target: position, arrival-side
+// normal, arrival direction, log throughput, relative depth, film position, log
+// connection weight (16 values; standardized inside the network).
+__device__ __forceinline__ void conn_features(const DevScene& S, float3 x, float3 ns, float3 din, float3 beta, int k,
+                                              int D, const Conn& c, float inv_n, float f[16]) {
+  f[0] = x.x; f[1] = x.y; f[2] = x.z;
+  f[3] = ns.x; f[4] = ns.y; f[5] = ns.z;
+  f[6] = din.x; f[7] = din.y; f[8] = din.z;
+  f[9] = logf(beta.x + 1e-30f); f[10] = logf(beta.y + 1e-30f); f[11] = logf(beta.z + 1e-30f);
+  f[12] = (float)(k + 1) / (float)D;
+  f[13] = c.ux / (float)S.W; f[14] = c.uy / (float)S.H;
+  f[15] = logf(c.geo * inv_n + 1e-30f);
+}
+
+// Training pairs from LRB-3 pass 2: for every valid connection its features and the target
+// log(|Lbar_i * L_i|_1 / lum(L_i) + floor), i.e. the adjoint weight the connection sees per
+// unit of its luminance.
+__global__ void __launch_bounds__(128) k_collect(DevScene S, KParams kp, const float* __restrict__ dI, float tfloor,
+                                                 float* __restrict__ feats, float* __restrict__ targets, int64_t cap,
+                                                 unsigned long long* __restrict__ count) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
+    const uint64_t n = (uint64_t)(kp.path_offset + p);
+    Walk w;
+    float3 x0;
+    walk_start(S, kp.seed, n, Le, w, x0);
+    for (int k = 0; k < kp.max_depth; ++k) {
+      Vtx v;
+      if (!walk_hit(S, w, v)) break;
+      float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+      if (v.diffuse) {
+        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+        Conn c = connect(S, v.x, ns, v.prim);
+        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
+        if (c.valid) {
+          float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
+          float3 Lb = adjoint_read(dI, S.W, S.H, c.ux, c.uy, L, nullptr);
+          float3 P = mul(Lb, L);
+          float lum = luminance(L);
+          if (lum > 0.0f) {
+            unsigned long long slot = atomicAdd(count, 1ull);
+            if ((int64_t)slot < cap) {
+              float f[16];
+              conn_features(S, v.x, ns, w.dir, w.beta, k, kp.max_depth, c, kp.inv_n, f);
+              for (int i = 0; i < 16; ++i) feats[slot * 16 + i] = f[i];
+              targets[slot] = logf((fabsf(P.x) + fabsf(P.y) + fabsf(P.z)) / lum + tfloor);
+            }
+          }
+        }
+      }
+      walk_scatter(S, w, v, ns, rho, r);
+    }
+  }
+}
+
 // ======================================================================= lane regeneration
 // Each warp owns a contiguous range of path indices and hands the next one to every lane
 // that has finished its path, so lanes never idle while a slower lane finishes (all 32
@@ -587,6 +646,16 @@ struct Dispenser {
 // loop performs one vertex of the lane's current path.
 template <int EST>
 __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
+  // learned reservoir target: network image and one 32x16 feature tile per warp
+  extern __shared__ __align__(16) unsigned char psmem[];
+  MlpSmem& mlp = *reinterpret_cast<MlpSmem*>(psmem);
+  __nv_bfloat16* ftile = reinterpret_cast<__nv_bfloat16*>(psmem + ((sizeof(MlpSmem) + 15) & ~size_t(15))) +
+                         (threadIdx.x >> 5) * 32 * kMlpIn;
+  const bool learned = EST == 1 && kp.mlp != nullptr;
+  if (learned) {
+    mlp_load_smem(mlp, kp.mlp);
+    __syncthreads();
+  }
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
   Dispenser disp;
   disp.init(kp.n_paths);
@@ -634,6 +703,22 @@ __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* _
       c = connect_pre(S, v.x, ns);
     }
     if (c.valid && occluded(S, v.x, c.wc, c.dist, v.prim)) c.valid = false;
+    // learned reservoir target: one warp-wide tensor-core evaluation for the lanes that
+    // have a connection at this step (all 32 lanes take part)
+    float yhat = 0.0f;
+    if (learned) {
+      const bool need = busy && alive && c.valid && active;
+      if (__any_sync(0xffffffffu, need)) {
+        float f[16];
+        if (need) {
+          conn_features(S, v.x, ns, w.dir, w.beta, k, kp.max_depth, c, kp.inv_n, f);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) f[i] = mlp.mean[i];
+        }
+        yhat = mlp_warp_infer(mlp, f, ftile);
+      }
+    }
     if (!busy) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
     if (!alive) {
@@ -663,6 +748,9 @@ __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* _
         if (active) {
           if (EST == 1) {
             float om = luminance(L);
+            // learned target: lum(L) (exp(sigma * yhat) + eps); any positive weight keeps the
+            // estimator unbiased (Eq. 10)
+            if (learned) om *= __expf(fminf(fmaxf(mlp.tscale * yhat, -30.0f), 30.0f)) + 1e-3f;
             if (om > 0.0f) {
               Om += om;
               if (r.w < om / Om) { R = k; wR = om; LR = L; Rux = c.ux; Ruy = c.uy; }
@@ -1032,9 +1120,12 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
 cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux, const LaunchCfg& L,
                           cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
+  const size_t smem = (est == 1 && kp.mlp)
+                          ? ((sizeof(MlpSmem) + 15) & ~size_t(15)) + sizeof(__nv_bfloat16) * 32 * kMlpIn * (L.block / 32)
+                          : 0;
   switch (est) {
     case 0: k_primal<0><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
-    case 1: k_primal<1><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
+    case 1: k_primal<1><<<grid, L.block, smem, st>>>(S, kp, image, aux); break;
     default: k_primal<2><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
   }
   return cudaGetLastError();
@@ -1073,6 +1164,13 @@ cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool ch
   if (att && chains) k_naive<true, true><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
   else if (att) k_naive<true, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
   else k_naive<false, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI, float tfloor, float* feats,
+                           float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L, cudaStream_t st) {
+  int grid = grid_for(L, kp.n_paths);
+  k_collect<<<grid, L.block, 0, st>>>(S, kp, dI, tfloor, feats, targets, cap, count);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ struct KParams {
   unsigned long long* census;  // DEVICE [5] or null: rays, box tests, primitive tests, vertices, connections
   int n_alb, n_h;              // parameter counts
   int priv_n;                  // > 0: gradients accumulate in n_alb + n_h floats of shared memory per block
+  const float* mlp;            // learned reservoir target parameters (DEVICE) or null (luminance)
 };
 
 struct GradPtrs {
@@ -58,6 +59,14 @@ cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool c
                           const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
 cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                          const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI, float tfloor, float* feats,
+                           float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L, cudaStream_t st);
+size_t mlp_grad_smem_bytes();
+cudaError_t launch_mlp_grad(const float* P, const float* X, const float* T, int64_t n, float inv_batch, float* g,
+                            float* loss, int sms, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* P, float* M, float* V, const float* g, int step, float lr, cudaStream_t st);
+cudaError_t launch_mlp_moments(const float* X, const float* T, int64_t n, float* P, cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* P, const float* X, int64_t n, float* out, int sms, cudaStream_t st);
 cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,
                            cudaStream_t st);
 

@@ -349,6 +349,20 @@ def smooth_adjoint(W: int, H: int, seed: int, scale: float = 1.0) -> np.ndarray:
     return scale * a / (W * H)
 
 
+def blob_adjoint(W: int, H: int, seed: int, sigma: float = 0.12, scale: float = 1.0) -> np.ndarray:
+    """A spatially concentrated signed adjoint [H, W, 3]: a Gaussian blob at a seeded film
+    position (the image difference of an inverse problem that is wrong in one region) plus
+    10% smooth background."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    cx, cy = (0.25 + 0.5 * torch.rand(2, generator=g, dtype=torch.float64)).tolist()
+    sgn = (torch.rand(3, generator=g, dtype=torch.float64) * 0.5 + 0.75).numpy()
+    ys, xs = np.meshgrid((np.arange(H) + 0.5) / H, (np.arange(W) + 0.5) / W, indexing="ij")
+    blob = np.exp(-((xs - cx) ** 2 + (ys - cy) ** 2) / (2 * sigma * sigma))
+    a = blob[..., None] * sgn[None, None, :] + 0.1 * smooth_adjoint(W, H, seed + 1) * (W * H)
+    return scale * a / (W * H)
+
+
 def perturbed_albedo(scene: Scene, std: float = 0.05, seed: int = 1) -> np.ndarray:
     """Target albedo: albedo + N(0, std), clamped to [0.05, 0.95]."""
     n = _torch_normal(scene.albedo.shape, std, seed)

@@ -65,7 +65,9 @@ _lock = threading.Lock()
 # Every symbol include/lt.h declares (checked by the CPU test-suite against the .so).
 EXPORTS = ["lt_scene_create", "lt_scene_refit", "lt_scene_destroy", "lt_primal", "lt_backward_lrb3",
            "lt_backward_reslrb", "lt_backward_naive", "lt_film_l2", "lt_record_size", "lt_naive_workspace_bytes",
-           "lt_sync_status", "lt_last_error", "lt_version"]
+           "lt_sync_status", "lt_last_error", "lt_version", "lt_mlp_collect", "lt_mlp_init_stats", "lt_mlp_grad",
+           "lt_mlp_adam", "lt_mlp_forward"]
+MLP_PARAMS, MLP_WEIGHTS = 5352, 5313
 
 
 def lib():
@@ -93,6 +95,11 @@ def lib():
             L.lt_sync_status.argtypes = [V, V]
             L.lt_last_error.restype = C.c_char_p
             L.lt_version.restype = C.c_char_p
+            L.lt_mlp_collect.argtypes = [V, P(lt_params), P(lt_render_opts), V, C.c_float, V, V, C.c_int64, V, V]
+            L.lt_mlp_init_stats.argtypes = [V, V, V, C.c_int64, V]
+            L.lt_mlp_grad.argtypes = [V, V, V, C.c_int64, C.c_int64, V, V, V]
+            L.lt_mlp_adam.argtypes = [V, V, V, V, C.c_int, C.c_float, V]
+            L.lt_mlp_forward.argtypes = [V, V, C.c_int64, V, V]
             _lib = L
     return _lib
 
@@ -252,6 +259,17 @@ class Scene:
                                        nbytes, C.byref(gr), _stream(stream)))
         return g
 
+    def mlp_collect(self, o, d_image, capacity, target_floor=0.0, stream=None):
+        """Training pairs (features [n,16], targets [n]) from an LRB-3 pass-2 replay."""
+        f = torch.empty((capacity, 16), device=self.device, dtype=torch.float32)
+        t = torch.empty(capacity, device=self.device, dtype=torch.float32)
+        cnt = torch.zeros(1, device=self.device, dtype=torch.int64)
+        p = self.params()
+        _check(lib().lt_mlp_collect(self._h, C.byref(p), C.byref(o), _ptr(d_image.contiguous()), float(target_floor),
+                                    _ptr(f), _ptr(t), int(capacity), _ptr(cnt), _stream(stream)))
+        n = min(int(cnt.item()), capacity)
+        return f[:n], t[:n], int(cnt.item())
+
     def sync_status(self, stream=None):
         _check(lib().lt_sync_status(self._h, _stream(stream)))
 
@@ -267,3 +285,64 @@ def film_l2(image, target, d_image=None, loss=None, stream=None):
 
 def version() -> str:
     return lib().lt_version().decode()
+
+
+# ------------------------------------------------------------------ learned reservoir target
+def mlp_init(seed=0, device="cuda"):
+    """Fresh parameter block (He-initialised weights, zero biases, identity statistics)."""
+    g = torch.Generator().manual_seed(seed)
+    P = torch.zeros(MLP_PARAMS, dtype=torch.float32)
+    P[0:1024] = torch.randn(1024, generator=g) * (2.0 / 16) ** 0.5
+    P[1088:5184] = torch.randn(4096, generator=g) * (2.0 / 64) ** 0.5
+    P[5248:5312] = torch.randn(64, generator=g) * (1.0 / 64) ** 0.5
+    P[5329:5345] = 1.0  # 1/std
+    P[5345] = 1.0       # target scale
+    return P.to(device)
+
+
+def mlp_init_stats(P, feats, targets, stream=None):
+    _check(lib().lt_mlp_init_stats(_ptr(P), _ptr(feats.contiguous()), _ptr(targets.contiguous()), feats.shape[0],
+                                   _stream(stream)))
+
+
+def mlp_grad(P, feats, targets, grad, loss, batch=None, stream=None):
+    n = feats.shape[0]
+    _check(lib().lt_mlp_grad(_ptr(P), _ptr(feats.contiguous()), _ptr(targets.contiguous()), n, int(batch or n),
+                             _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def mlp_adam(P, m, v, grad, step, lr, stream=None):
+    _check(lib().lt_mlp_adam(_ptr(P), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr), _stream(stream)))
+
+
+def mlp_forward(P, feats, out=None, stream=None):
+    o = out if out is not None else torch.empty(feats.shape[0], device=feats.device, dtype=torch.float32)
+    _check(lib().lt_mlp_forward(_ptr(P), _ptr(feats.contiguous()), feats.shape[0], _ptr(o), _stream(stream)))
+    return o
+
+
+def mlp_train(P, feats, targets, epochs=20, batch=4096, lr=1e-3, seed=0, stream=None):
+    """Adam on the standardized-target MSE with the project's tensor-core kernels; returns
+    the per-epoch mean losses.  (Mini-batches are contiguous slices of a seeded permutation.)"""
+    n = feats.shape[0]
+    mlp_init_stats(P, feats, targets, stream)
+    m = torch.zeros(MLP_WEIGHTS, device=P.device)
+    v = torch.zeros(MLP_WEIGHTS, device=P.device)
+    grad = torch.zeros(MLP_WEIGHTS, device=P.device)
+    loss = torch.zeros(1, device=P.device)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    losses, step = [], 0
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=g).to(P.device)
+        fx, tx = feats[perm].contiguous(), targets[perm].contiguous()
+        loss.zero_()
+        nb = 0
+        for b0 in range(0, n, batch):
+            b1 = min(n, b0 + batch)
+            grad.zero_()
+            mlp_grad(P, fx[b0:b1], tx[b0:b1], grad, loss, batch=b1 - b0, stream=stream)
+            step += 1
+            mlp_adam(P, m, v, grad, step, lr, stream=stream)
+            nb += 1
+        losses.append(float(loss.item()) / nb)
+    return losses

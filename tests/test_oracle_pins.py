@@ -320,3 +320,56 @@ def test_reslrb_gradient_unbiased_paired(oracle):
     assert np.mean(np.abs(zp) > 3) < 0.02
     # and it is a different per-seed estimator (variance strictly positive)
     assert np.all(dd.std(0) > 0)
+
+
+# ------------------------------------------------------------------ learned target MLP
+def _mlp_params(seed=0):
+    rng = np.random.default_rng(seed)
+    P = np.zeros(5352)
+    P[0:1024] = rng.normal(size=1024) * np.sqrt(2 / 16)
+    P[1024:1088] = rng.normal(size=64) * 0.1
+    P[1088:5184] = rng.normal(size=4096) * np.sqrt(2 / 64)
+    P[5184:5248] = rng.normal(size=64) * 0.1
+    P[5248:5312] = rng.normal(size=64) * np.sqrt(1 / 64)
+    P[5312] = 0.3
+    P[5313:5329] = rng.normal(size=16) * 0.1
+    P[5329:5345] = rng.uniform(0.5, 2.0, size=16)
+    P[5345], P[5346] = 1.7, -0.4
+    return P
+
+
+def test_mlp_oracle_gradient_vs_central_differences(oracle):
+    """The oracle network's reverse mode (FP64, no rounding) against central differences of
+    its loss, on every parameter group."""
+    rng = np.random.default_rng(1)
+    P = _mlp_params(0)
+    X = rng.normal(size=(40, 16))
+    T = rng.normal(size=40)
+    g, loss = oracle.mlp_grad(P, X, T, round_bf16=False)
+    for k in [3, 500, 1030, 1088 + 7 * 64 + 9, 4000, 5190, 5250, 5312]:
+        h = 1e-6
+        Pp, Pm = P.copy(), P.copy()
+        Pp[k] += h
+        Pm[k] -= h
+        fd = (oracle.mlp_grad(Pp, X, T, round_bf16=False)[1] - oracle.mlp_grad(Pm, X, T, round_bf16=False)[1]) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    # the forward is the plain network: one sample by hand
+    x = ((X[0].astype(np.float32) - P[5313:5329].astype(np.float32)) * P[5329:5345].astype(np.float32)).astype(np.float64)
+    h1 = np.maximum(P[1024:1088] + x @ P[0:1024].reshape(16, 64), 0)
+    h2 = np.maximum(P[5184:5248] + h1 @ P[1088:5184].reshape(64, 64), 0)
+    y = P[5312] + h2 @ P[5248:5312]
+    assert oracle.mlp_forward(P, X[:1], round_bf16=False)[0] == pytest.approx(y, rel=1e-12)
+
+
+def test_mlp_oracle_bf16_rounding():
+    """BFloat16 emulation: each rounding keeps 8 significant bits (relative error <= 2^-9),
+    so over 64-term sums the network output moves by well under a few percent of its
+    typical magnitude, and it does move."""
+    from oracle import oracle as O
+    P = _mlp_params(2)
+    X = np.random.default_rng(3).normal(size=(64, 16))
+    a = O.mlp_forward(P, X, round_bf16=True)
+    b = O.mlp_forward(P, X, round_bf16=False)
+    rel = np.abs(a - b) / np.abs(b).mean()
+    assert np.median(rel) < 1e-2 and np.max(rel) < 5e-2
+    assert not np.allclose(a, b, rtol=1e-6)
