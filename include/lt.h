@@ -214,6 +214,30 @@ lt_status lt_mlp_adam(float* mlp, float* m, float* v, const float* grad, int ste
 /* Network outputs (standardized target units) for n feature rows (DEVICE). */
 lt_status lt_mlp_forward(const float* mlp, const float* feats, int64_t n, float* out, void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Naive-AD gradient without any allocation (no counterpart in the paper).
+ * Some callers cannot hand the library a workspace or let it allocate one: an application
+ * that owns a fixed GPU memory budget and forbids allocations once it is running, or a
+ * render loop for which cudaMalloc/cudaFree are off limits because they can synchronise
+ * the whole device and stall every other stream.  For them this call runs the same two
+ * kernels as lt_primal(LT_EST_NAIVE) followed by lt_backward_naive, but keeps the
+ * per-vertex tape in one fixed scratch array of LT_NAIVE_STATIC_BYTES that is compiled
+ * into the library: every GPU that loads liblt holds that memory until the process exits.
+ * The caller still passes the fixed adjoint d_image (DEVICE [H][W][3]), the image to
+ * overwrite (DEVICE [H][W][3]) and the gradient outputs.
+ *  - Requests whose tape (lt_naive_workspace_bytes(opts)) exceeds LT_NAIVE_STATIC_BYTES are
+ *    rejected with LT_ERR_INVALID_ARG; nothing is launched.
+ *  - The scene's device must be the current device.  The first call on a device looks up
+ *    the scratch array's device address for that device (once, cached afterwards); make
+ *    that first call before any stream capture on that device begins.
+ *  - All calls on a device share the one array and it keeps whatever the last call left;
+ *    each call writes every tape entry it later reads, so nothing needs clearing, but two
+ *    calls whose work overlaps on the GPU (for example on two streams) race on the array
+ *    and must be serialised by the caller. */
+#define LT_NAIVE_STATIC_BYTES (32u << 20)
+lt_status lt_naive_gradient_static(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                                   const float* d_image, float* image, const lt_grads* grads, void* stream);
+
 /* Bytes of one ResLRB record (constant per path). */
 size_t lt_record_size(const lt_render_opts* opts);
 /* Bytes of the naive-AD tape for opts (n_paths * max_depth * record). */

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -275,9 +276,67 @@ lt_status prep_grads(const lt_scene* s, const lt_grads* g, cudaStream_t st, Grad
 
 }  // namespace
 
+// Fixed tape for lt_naive_gradient_static: file-scope device memory, so that call never
+// allocates.  Host code must not use this name as an address; it looks the device
+// address up per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_naive_static_tape[LT_NAIVE_STATIC_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+void* g_static_tape[kMaxDevices] = {};
+
+// Device address of the fixed tape on the current device (looked up on first use).
+lt_status static_tape(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(LT_ERR_UNSUPPORTED, "device index beyond the static tape table");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_tape[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_naive_static_tape);
+    if (e != cudaSuccess || !p)
+      return fail(LT_ERR_CUDA, std::string("lt_naive_gradient_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_static_tape[dev] = p;
+  }
+  *out = g_static_tape[dev];
+  return LT_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* lt_last_error(void) { return g_last_error.c_str(); }
+
+lt_status lt_naive_gradient_static(lt_scene* s, const lt_params* p, const lt_render_opts* o, const float* dI,
+                                   float* image, const lt_grads* g, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!dI || !image) return fail(LT_ERR_INVALID_ARG, "lt_naive_gradient_static: d_image or image is NULL");
+  const size_t need = lt_naive_workspace_bytes(o);
+  if (need > (size_t)LT_NAIVE_STATIC_BYTES)
+    return fail(LT_ERR_INVALID_ARG, "lt_naive_gradient_static: the tape needs " + std::to_string(need) +
+                                        " bytes, more than the fixed scratch of " +
+                                        std::to_string((size_t)LT_NAIVE_STATIC_BYTES) + " bytes (fewer paths or depth)");
+  int dev = -1;
+  LT_CUDA(cudaGetDevice(&dev));
+  if (dev != s->device) return fail(LT_ERR_INVALID_ARG, "lt_naive_gradient_static: the scene's device is not current");
+  void* tape = nullptr;
+  v = static_tape(dev, &tape);
+  if (v != LT_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+  LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
+  GradPtrs gp;
+  v = prep_grads(s, g, st, gp);
+  if (v != LT_OK) return v;
+  if (o->n_paths == 0) return LT_OK;
+  const LaunchCfg L = cfg_for(s, o);
+  cudaError_t e = launch_primal(s->dev, kparams(p, o), LT_EST_NAIVE, image, tape, L, st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_naive_gradient_static: ") + cudaGetErrorString(e));
+  KParams kb = kparams(p, o);
+  set_privatization(s, g, kb);
+  e = launch_naive(s->dev, kb, o->attached != 0, s->has_dielectric, dI, tape, gp, L, st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_naive_gradient_static: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
 
 const char* lt_version(void) { return "liblt 0.1 (sm_103a)"; }
 

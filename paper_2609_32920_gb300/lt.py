@@ -66,7 +66,7 @@ _lock = threading.Lock()
 EXPORTS = ["lt_scene_create", "lt_scene_refit", "lt_scene_destroy", "lt_primal", "lt_backward_lrb3",
            "lt_backward_reslrb", "lt_backward_naive", "lt_film_l2", "lt_record_size", "lt_naive_workspace_bytes",
            "lt_sync_status", "lt_last_error", "lt_version", "lt_mlp_collect", "lt_mlp_init_stats", "lt_mlp_grad",
-           "lt_mlp_adam", "lt_mlp_forward"]
+           "lt_mlp_adam", "lt_mlp_forward", "lt_naive_gradient_static"]
 MLP_PARAMS, MLP_WEIGHTS = 5352, 5313
 
 
