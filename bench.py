@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-method and memory-vs-depth sweep")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
     ap.add_argument("--paths-log2", type=int, default=22, help="paths per GPU per step (profiling uses fewer)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-target study")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: only warm-up and timed steps (no e2e, census, sweep or CPU baseline)")
     return ap.parse_args()
@@ -312,6 +313,9 @@ def run_ours(args):
     methods, memory = {}, {}
     if not args.no_sweep:
         methods, memory = method_sweep(S, sc, target, heights, dev, path_offset, ws, flush)
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = learned_target_study(dev)
     clk = clocks.stop()
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N=1 only)
@@ -333,6 +337,7 @@ def run_ours(args):
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
                 "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory,
+                "learned_target": learned,
                 "lib": lt.version()}
         print(json.dumps(line))
     if ws > 1:
@@ -405,6 +410,73 @@ def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
             ms, peak = run(m, D, timed_reps=1)
             memory[str(D)][m] = {"extra_bytes": peak, "ms": ms}
     return methods, memory
+
+
+def _learned_one(dev, kind, seeds, paths_log2, depth):
+    """Time x gradient variance of ResLRB with the learned reservoir target against ResLRB
+    with the luminance target on one workload.  kind "caustic": dielectric 64x64 height
+    field over a receiver, 256x256, attached height gradients, image adjoint from an L2 loss
+    against the caustic of a different height field.  kind "interior": the box with the
+    32x32 height field, image adjoint concentrated in one film region.  Both estimators use
+    the same seeds; variance = mean over parameters of the per-parameter variance across
+    seeds."""
+    import torch
+
+    from paper_2609_32920_gb300 import inputs as I
+    from paper_2609_32920_gb300 import lt
+    n = 1 << paths_log2
+    if kind == "caustic":
+        sc = I.slab_scene(256, n=64, seed=0)
+        S = lt.Scene(sc)
+        T_S = lt.Scene(I.slab_scene(256, n=64, seed=1))
+        target = T_S.primal(T_S.opts(seed=7, n_paths=4 * n, max_depth=depth))
+        del T_S
+        img = S.primal(S.opts(seed=8, n_paths=4 * n, max_depth=depth))
+        _, dI = lt.film_l2(img, target)
+        gi = 2
+    else:
+        sc = I.box_scene(256, heightmap=32)
+        S = lt.Scene(sc)
+        dI = torch.tensor(I.blob_adjoint(sc.W, sc.H, 81), dtype=torch.float32, device=dev)
+        gi = 0
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    (f, t, cnt), ms_collect = timed(lambda: S.mlp_collect(S.opts(seed=9, n_paths=n, max_depth=depth, attached=1), dI,
+                                                          capacity=1 << 20,
+                                                          target_floor=0.01 * float(dI.abs().max())))
+    P = lt.mlp_init(0)
+    losses, ms_train = timed(lambda: lt.mlp_train(P, f, t, epochs=20, batch=4096, lr=1e-3))
+    rec = torch.empty((n, 8), device=dev)
+    res = {}
+    for name, extra in (("plain", {}), ("learned", {"target": lt.TARGET_MLP, "mlp": P})):
+        grads, ms = [], []
+        for s_ in range(seeds):
+            o = S.opts(seed=100 + s_, n_paths=n, max_depth=depth, attached=1, **extra)
+            g, m_ = timed(lambda: (S.primal(o, estimator=lt.EST_RESLRB, aux=rec), S.backward_reslrb(o, dI, rec))[1])
+            grads.append(g[gi].cpu().clone())
+            ms.append(m_)
+        G = torch.stack(grads).double()
+        var = float(G.var(dim=0, unbiased=True).mean())
+        res[name] = {"ms_per_gradient": statistics.median(ms), "variance": var,
+                     "time_x_variance": statistics.median(ms) * var, "mean_grad_norm": float(G.mean(0).norm())}
+    conns = cnt / n
+    wl = "slab256_hm64 (caustic)" if kind == "caustic" else "box256_hm32 (interior, localized adjoint)"
+    return {"workload": "%s depth %d, 2^%d paths per gradient, %d seeds" % (wl, depth, paths_log2, seeds),
+            "pairs": int(f.shape[0]), "connections_per_path": conns, "collect_ms": ms_collect, "train_ms": ms_train,
+            "train_loss_first_last": [losses[0], losses[-1]], "plain": res["plain"], "learned": res["learned"],
+            "efficiency_gain": res["plain"]["time_x_variance"] / res["learned"]["time_x_variance"]}
+
+
+def learned_target_study(dev):
+    return {"caustic": _learned_one(dev, "caustic", 16, 20, 32), "interior": _learned_one(dev, "interior", 16, 20, 16)}
 
 
 def main():
