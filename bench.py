@@ -177,19 +177,20 @@ def run_ours(args):
     from paper_2609_32920_gb300 import inputs as I
     from paper_2609_32920_gb300 import lt
 
+    from paper_2609_32920_gb300.shard import max_over_ranks, path_shard
     sc = I.box_scene(256, heightmap=32)
     S = lt.Scene(sc)
     W, H = sc.W, sc.H
-    path_offset = rank * N_PATHS  # weak scaling: each rank traces its own 2^22 paths
+    # weak scaling: each rank traces its own 2^22 paths, no data-path collective
+    path_offset, _, n_norm = path_shard(rank, ws, N_PATHS)
     # target image: the same scene with perturbed albedo and heights (rendered by liblt)
     tgt_sc = sc.with_params(albedo=I.perturbed_albedo(sc, 0.05, 1), heights=sc.heights * 0.5)
     T_S = lt.Scene(tgt_sc)
     target = T_S.primal(T_S.opts(seed=12345, n_paths=N_PATHS, max_depth=DEPTH))
     del T_S
     heights = S.heights.clone()
-    o_plain = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, path_offset=path_offset, n_norm=N_PATHS * ws)
-    o_att = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset,
-                   n_norm=N_PATHS * ws)
+    o_plain = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, path_offset=path_offset, n_norm=n_norm)
+    o_att = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset, n_norm=n_norm)
     img = S.new_image()
     dI = torch.empty_like(img)
     loss = torch.empty(1, device=dev)
@@ -230,17 +231,13 @@ def run_ours(args):
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     bwd_ms = [a.elapsed_time(b) for a, b in bev]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dev)
     if args.profile:
         clocks.stop()
         if rank == 0:
             print(json.dumps({"profile": True, "paths": N_PATHS, "ms_per_step": total_ms / args.steps,
                               "backward_ms": statistics.median(bwd_ms)}))
         return 0
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t)
     ms_per_step = total_ms / args.steps
     value = ws * N_PATHS / (ms_per_step * 1e-3)
     S.sync_status()
@@ -276,11 +273,7 @@ def run_ours(args):
         e2e_step()
         b.record(stream)
     barrier()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e_ev) / len(e_ev)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e_ev) / len(e_ev), dev)
     e2e_value = ws * N_PATHS / (e2e_ms * 1e-3)
 
     # ---------------- algorithmic work of the dominant kernel (counting variant, untimed)
