@@ -238,6 +238,75 @@ lt_status lt_mlp_forward(const float* mlp, const float* feats, int64_t n, float*
 lt_status lt_naive_gradient_static(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
                                    const float* d_image, float* image, const lt_grads* grads, void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Batched passes (no counterpart in the paper, which renders one scene at a time):
+ * many scenes with uneven path budgets, depths and geometry run their paths in ONE
+ * persistent launch per pass.  Each item's path range is cut into chunks of
+ * 32 * paths_per_thread paths; a warp takes the next chunk of the whole batch with one
+ * atomic, so items of any size share the GPU without a launch per item.  Each pass
+ * (its clears, height refits and the kernel) is captured once into a CUDA graph and
+ * replayed by lt_batch_run.  Per path the work is the same as the single-scene call
+ * with the item's opts, so results match those calls up to floating-point summation
+ * order (atomics).
+ *
+ * An item fixes every buffer the passes use (all DEVICE, caller-owned, alive and unmoved
+ * until lt_batch_destroy; the scene too).  Buffer contents are read at each run, so
+ * parameters, heights and d_image may change between runs. */
+typedef struct {
+  lt_scene* scene;
+  lt_params params;
+  const float* heights;    /* [n_heights] or NULL: primal passes refit the scene first;
+                              two items with heights must not share a scene          */
+  lt_render_opts opts;     /* seed, path_offset, n_paths, n_norm, max_depth, attached,
+                              path_mask and path_dbg are used (path_dbg by LT_PASS_LRB3:
+                              (delta_total rgb, valid connections) as lt_backward_lrb3);
+                              the launch shape comes from the batch configuration    */
+  float* image;            /* [H][W][3] primal passes: overwritten                   */
+  void* records;           /* [n_paths][lt_record_size] ResLRB records, or NULL when the
+                              ResLRB passes are not run                              */
+  const float* d_image;    /* [H][W][3] adjoint read by the backward passes           */
+  lt_grads grads;          /* overwritten by the backward passes unless accumulate    */
+} lt_batch_item;
+
+/* Passes.  PRIMAL = lt_primal(LT_EST_PLAIN) of every item; PRIMAL_RESLRB =
+ * lt_primal(LT_EST_RESLRB) (luminance target) writing `records`; LRB3 =
+ * lt_backward_lrb3; RESLRB = lt_backward_reslrb reading `records`. */
+enum { LT_PASS_PRIMAL = 0, LT_PASS_PRIMAL_RESLRB = 1, LT_PASS_LRB3 = 2, LT_PASS_RESLRB = 3 };
+
+/* Launch shape of the persistent kernels.  blocks_per_sm = 0: as many blocks as fit on an
+ * SM at once (occupancy of the pass's kernel), so the grid is resident. */
+typedef struct {
+  int block_size;        /* 64, 128 or 256                                             */
+  int paths_per_thread;  /* 1, 2, 4 or 8: chunk = 32 * paths_per_thread paths          */
+  int blocks_per_sm;     /* 0 = occupancy, else 1..32                                  */
+} lt_batch_config;
+
+typedef struct lt_batch lt_batch; /* opaque: item table on the device, captured graphs */
+
+/* Copy the items (n >= 1) and build the device item table.  All scenes must be on the
+ * current device.  Default configuration: block 128, 4 paths per thread, occupancy.
+ * Synchronises `stream` once (table upload). */
+lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_batch** out);
+
+/* Run one pass for every item on `stream`: launches the pass's CUDA graph (captured on
+ * first use on a stream the batch owns, and again after lt_batch_set_config).  Passes of
+ * one batch share state and must not overlap on the GPU (serialise them on one stream).
+ * LT_ERR_INVALID_ARG: unknown pass, or a ResLRB pass with an item without records. */
+lt_status lt_batch_run(lt_batch* batch, int pass, void* stream);
+
+lt_status lt_batch_set_config(lt_batch* batch, const lt_batch_config* cfg);
+lt_status lt_batch_get_config(const lt_batch* batch, lt_batch_config* cfg);
+
+/* Autotuner: time the pass (graph replay, CUDA events on `stream`, best of `reps` after
+ * one warm-up) for every block_size in {64, 128, 256} x paths_per_thread in {1, 2, 4, 8}
+ * at occupancy, keep the fastest as the batch configuration and return it in *best (and
+ * its time per pass in *best_ms, either may be NULL).  Blocking: synchronises `stream`.
+ * The pass runs many times; outputs hold one complete run of the pass afterwards (a
+ * backward pass with accumulate set accumulates every run). */
+lt_status lt_batch_tune(lt_batch* batch, int pass, int reps, void* stream, lt_batch_config* best, float* best_ms);
+
+void lt_batch_destroy(lt_batch* batch);
+
 /* Bytes of one ResLRB record (constant per path). */
 size_t lt_record_size(const lt_render_opts* opts);
 /* Bytes of the naive-AD tape for opts (n_paths * max_depth * record). */

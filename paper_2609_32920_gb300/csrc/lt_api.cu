@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 #include <vector>
 
 #include "../../include/lt.h"
+#include "lt_batch.h"
 #include "lt_device.cuh"
 #include "lt_launch.h"
 
@@ -682,5 +684,268 @@ lt_status lt_sync_status(lt_scene* s, void* stream) {
   if (h) return fail(LT_ERR_DEVICE_CHECK, "device-side check failed (bits " + std::to_string(h) + ")");
   return LT_OK;
 }
+
+// ------------------------------------------------------------------ batched passes
+}  // extern "C"
+
+struct lt_batch {
+  int device = 0, sms = 1;
+  std::vector<lt_batch_item> items;
+  bool any_att = false, chains = false, all_rec = true;
+  // one item table per chunk size (32 * paths_per_thread, paths_per_thread = 1, 2, 4, 8):
+  // only the first-chunk indices differ, and a configuration change must not rewrite a
+  // table that a running pass may still read
+  BatchJob* d_jobs[4] = {};
+  int64_t n_chunks[4] = {};
+  unsigned long long* d_ticket = nullptr;  // [4], one per pass
+  cudaStream_t cap = nullptr;              // capture stream
+  lt_batch_config cfg{128, 4, 0};
+  cudaGraphExec_t exec[4] = {};
+};
+
+namespace {
+
+int ppt_slot(int ppt) { return ppt == 1 ? 0 : ppt == 2 ? 1 : ppt == 4 ? 2 : ppt == 8 ? 3 : -1; }
+
+void drop_graphs(lt_batch* b) {
+  for (auto& e : b->exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+}
+
+void free_batch(lt_batch* b) {
+  if (!b) return;
+  drop_graphs(b);
+  for (auto* j : b->d_jobs) cudaFree(j);
+  cudaFree(b->d_ticket);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+lt_status check_batch_cfg(const lt_batch_config* c) {
+  if (!c) return fail(LT_ERR_INVALID_ARG, "config is NULL");
+  if (c->block_size != 64 && c->block_size != 128 && c->block_size != 256)
+    return fail(LT_ERR_INVALID_ARG, "block_size must be 64, 128 or 256");
+  if (ppt_slot(c->paths_per_thread) < 0) return fail(LT_ERR_INVALID_ARG, "paths_per_thread must be 1, 2, 4 or 8");
+  if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return fail(LT_ERR_INVALID_ARG, "blocks_per_sm must be in 0..32");
+  return LT_OK;
+}
+
+int kernel_pass(int pass) {
+  return pass == LT_PASS_PRIMAL ? BPASS_PRIMAL
+         : pass == LT_PASS_PRIMAL_RESLRB ? BPASS_PRIMAL_RES
+         : pass == LT_PASS_LRB3 ? BPASS_LRB3 : BPASS_RESLRB;
+}
+
+// Enqueue one pass on `st`: clears and refits of every item, the queue reset, the kernel
+// with `per_sm` resident blocks per SM.
+lt_status enqueue_pass(lt_batch* b, int pass, int per_sm, cudaStream_t st) {
+  const bool primal = pass == LT_PASS_PRIMAL || pass == LT_PASS_PRIMAL_RESLRB;
+  for (const lt_batch_item& it : b->items) {
+    const lt_scene* s = it.scene;
+    if (primal) {
+      if (it.heights && s->n_heights > 0) {
+        RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, it.heights, s->n_prims, s->d_node, s->d_range, s->n_nodes};
+        cudaError_t e = launch_refit(ra, st);
+        if (e) return fail(LT_ERR_CUDA, std::string("batch refit: ") + cudaGetErrorString(e));
+      }
+      LT_CUDA(cudaMemsetAsync(it.image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
+    } else {
+      GradPtrs gp;
+      lt_status v = prep_grads(s, &it.grads, st, gp);
+      if (v != LT_OK) return v;
+    }
+  }
+  const int slot = ppt_slot(b->cfg.paths_per_thread);
+  const int64_t nch = b->n_chunks[slot];
+  if (nch == 0) return LT_OK;
+  LT_CUDA(cudaMemsetAsync(b->d_ticket + pass, 0, sizeof(unsigned long long), st));
+  const int kpass = kernel_pass(pass);
+  const int block = b->cfg.block_size;
+  // a resident grid, but no more warps than chunks
+  const int64_t warps_per_block = block / 32;
+  int64_t grid = (int64_t)b->sms * per_sm;
+  grid = std::min<int64_t>(grid, (nch + warps_per_block - 1) / warps_per_block);
+  BatchArgs a{b->d_jobs[slot], (int)b->items.size(), 32 * b->cfg.paths_per_thread, nch, b->d_ticket + pass};
+  cudaError_t e = launch_batch(kpass, b->any_att, b->chains, a, block, (int)std::max<int64_t>(grid, 1), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("batched pass: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+// Capture the pass on the batch's own stream and instantiate it.
+lt_status capture_pass(lt_batch* b, int pass) {
+  int per_sm = b->cfg.blocks_per_sm;
+  if (per_sm == 0) per_sm = batch_occupancy(kernel_pass(pass), b->any_att, b->chains, b->cfg.block_size);
+  if (per_sm < 1) return fail(LT_ERR_CUDA, "batched kernel cannot be resident at this block size");
+  LT_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  lt_status v = enqueue_pass(b, pass, per_sm, b->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (v != LT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return v;
+  }
+  if (e != cudaSuccess) return fail(LT_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec[pass], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->exec[pass] = nullptr;
+    return fail(LT_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return LT_OK;
+}
+
+lt_status check_pass(const lt_batch* b, int pass) {
+  if (!b) return fail(LT_ERR_INVALID_ARG, "batch is NULL");
+  if (pass < LT_PASS_PRIMAL || pass > LT_PASS_RESLRB) return fail(LT_ERR_INVALID_ARG, "unknown pass");
+  if ((pass == LT_PASS_PRIMAL_RESLRB || pass == LT_PASS_RESLRB) && !b->all_rec)
+    return fail(LT_ERR_INVALID_ARG, "a ResLRB pass needs records for every item");
+  return LT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_batch** out) {
+  if (!out) return fail(LT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!items || n < 1) return fail(LT_ERR_INVALID_ARG, "need at least one item");
+  int dev = 0;
+  LT_CUDA(cudaGetDevice(&dev));
+  std::unique_ptr<lt_batch, void (*)(lt_batch*)> b(new lt_batch, free_batch);
+  b->device = dev;
+  std::vector<BatchJob> jobs(n);
+  for (int i = 0; i < n; ++i) {
+    lt_batch_item it = items[i];
+    const std::string at = "item " + std::to_string(i) + ": ";
+    if (!it.scene) return fail(LT_ERR_INVALID_ARG, at + "scene is NULL");
+    if (it.scene->device != dev) return fail(LT_ERR_INVALID_ARG, at + "scene is on another device");
+    // launch shape and the learned target are batch-wide; the census is single-scene only
+    it.opts.block_size = 0;
+    it.opts.blocks_per_sm = 0;
+    it.opts.target = LT_TARGET_LUMINANCE;
+    it.opts.mlp = nullptr;
+    it.opts.census = nullptr;
+    lt_status v = check_opts(it.scene, &it.params, &it.opts);
+    if (v != LT_OK) return fail(v, at + g_last_error);
+    if (!it.image || !it.d_image) return fail(LT_ERR_INVALID_ARG, at + "image or d_image is NULL");
+    if (it.heights && it.scene->n_heights > 0)
+      for (int j = 0; j < i; ++j)
+        if (b->items[j].scene == it.scene && b->items[j].heights)
+          return fail(LT_ERR_INVALID_ARG, at + "two items with heights share a scene");
+    b->items.push_back(it);
+    b->sms = it.scene->sms;
+    b->any_att |= it.opts.attached != 0;
+    b->chains |= it.opts.attached != 0 && it.scene->has_dielectric;
+    b->all_rec &= it.records != nullptr || it.opts.n_paths == 0;
+    BatchJob& J = jobs[i];
+    J.S = it.scene->dev;
+    J.kp = kparams(&it.params, &b->items[i].opts);
+    J.dI = it.d_image;
+    J.g = GradPtrs{it.grads.d_albedo, it.grads.d_Le, it.grads.d_heights};
+    J.image = it.image;
+    J.rec = it.records;
+    J.att = it.opts.attached != 0;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int slot = 0; slot < 4; ++slot) {
+    const int64_t chunk = 32ll << slot;
+    int64_t c = 0;
+    for (int i = 0; i < n; ++i) {
+      jobs[i].chunk0 = c;
+      c += (jobs[i].kp.n_paths + chunk - 1) / chunk;
+    }
+    b->n_chunks[slot] = c;
+    LT_CUDA(cudaMalloc(&b->d_jobs[slot], sizeof(BatchJob) * n));
+    LT_CUDA(cudaMemcpyAsync(b->d_jobs[slot], jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, st));
+  }
+  LT_CUDA(cudaMalloc(&b->d_ticket, 4 * sizeof(unsigned long long)));
+  LT_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  LT_CUDA(cudaStreamSynchronize(st));  // the host copy of the table goes out of scope
+  *out = b.release();
+  return LT_OK;
+}
+
+lt_status lt_batch_run(lt_batch* b, int pass, void* stream) {
+  lt_status v = check_pass(b, pass);
+  if (v != LT_OK) return v;
+  if (!b->exec[pass]) {
+    v = capture_pass(b, pass);
+    if (v != LT_OK) return v;
+  }
+  LT_CUDA(cudaGraphLaunch(b->exec[pass], (cudaStream_t)stream));
+  return LT_OK;
+}
+
+lt_status lt_batch_set_config(lt_batch* b, const lt_batch_config* cfg) {
+  if (!b) return fail(LT_ERR_INVALID_ARG, "batch is NULL");
+  lt_status v = check_batch_cfg(cfg);
+  if (v != LT_OK) return v;
+  b->cfg = *cfg;
+  drop_graphs(b);
+  return LT_OK;
+}
+
+lt_status lt_batch_get_config(const lt_batch* b, lt_batch_config* cfg) {
+  if (!b || !cfg) return fail(LT_ERR_INVALID_ARG, "batch or cfg is NULL");
+  *cfg = b->cfg;
+  return LT_OK;
+}
+
+lt_status lt_batch_tune(lt_batch* b, int pass, int reps, void* stream, lt_batch_config* best, float* best_ms) {
+  lt_status v = check_pass(b, pass);
+  if (v != LT_OK) return v;
+  if (reps < 1) return fail(LT_ERR_INVALID_ARG, "reps must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  LT_CUDA(cudaEventCreate(&e0));
+  LT_CUDA(cudaEventCreate(&e1));
+  const lt_batch_config keep = b->cfg;
+  lt_batch_config win = keep;
+  float win_ms = 3e38f;
+  lt_status res = LT_OK;
+  for (int block : {64, 128, 256}) {
+    for (int ppt : {1, 2, 4, 8}) {
+      lt_batch_config c{block, ppt, 0};
+      lt_batch_set_config(b, &c);
+      res = lt_batch_run(b, pass, stream);  // capture + warm-up
+      if (res != LT_OK) break;
+      float t_min = 3e38f;
+      for (int r = 0; r < reps && res == LT_OK; ++r) {
+        cudaError_t e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[pass], st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) res = fail(LT_ERR_CUDA, std::string("lt_batch_tune: ") + cudaGetErrorString(e));
+        t_min = std::min(t_min, ms);
+      }
+      if (res != LT_OK) break;
+      if (t_min < win_ms) {
+        win_ms = t_min;
+        win = c;
+      }
+    }
+    if (res != LT_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (res != LT_OK) {
+    lt_batch_set_config(b, &keep);
+    return res;
+  }
+  lt_batch_set_config(b, &win);
+  v = lt_batch_run(b, pass, stream);  // outputs: one complete run of the chosen shape
+  if (v != LT_OK) return v;
+  LT_CUDA(cudaStreamSynchronize(st));
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return LT_OK;
+}
+
+void lt_batch_destroy(lt_batch* b) { free_batch(b); }
 
 }  // extern "C"

@@ -1,0 +1,42 @@
+// lt_batch.h -- internal interface of the batched passes: one persistent launch runs the
+// paths of many scenes, each with its own parameters, path budget, depth and outputs.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lt_device.cuh"
+#include "lt_launch.h"
+
+namespace lt {
+
+// One item of a batch as the kernels see it (device memory, read per lane).
+struct BatchJob {
+  DevScene S;
+  KParams kp;        // priv_n = 0 (gradients go to global memory), census = null
+  const float* dI;   // adjoint image
+  GradPtrs g;
+  float* image;      // primal image
+  void* rec;         // ResLRB records (32 B per path) or null
+  int att;           // attached formulation
+  int64_t chunk0;    // index of this item's first chunk in the batch's chunk sequence
+};
+
+// Work queue: the items' path ranges are cut into chunks of `chunk` paths (an item's last
+// chunk may be shorter); a warp takes the next chunk with one atomic on `ticket`, which
+// the pass resets to zero before the launch.
+struct BatchArgs {
+  const BatchJob* jobs;
+  int n_jobs;
+  int chunk;
+  int64_t n_chunks;
+  unsigned long long* ticket;
+};
+
+enum BatchPass { BPASS_PRIMAL = 0, BPASS_PRIMAL_RES = 1, BPASS_LRB3 = 2, BPASS_RESLRB = 3 };
+
+// `chains`: some attached item's scene has dielectrics (compiles the specular-chain variant).
+cudaError_t launch_batch(int pass, bool att, bool chains, const BatchArgs& a, int block, int grid, cudaStream_t st);
+// Resident blocks per SM of the pass's kernel at `block` threads (0 on error).
+int batch_occupancy(int pass, bool att, bool chains, int block);
+
+}  // namespace lt

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "lt_device.cuh"
+#include "lt_batch.h"
 #include "lt_launch.h"
 #include "lt_mlp.cuh"
 
@@ -641,24 +642,87 @@ struct Dispenser {
   }
 };
 
+// Batched launches: a warp serves its lanes from its current chunk and takes the next
+// chunk (one atomic on the ticket) when that is used up, so lanes of one warp may hold
+// paths of different items for a while.  All 32 lanes call take() together; every
+// iteration of its loop serves at least one lane or consumes a ticket, so it ends.
+struct BatchDispenser {
+  int job;
+  int64_t next, end;
+  bool done;
+  __device__ __forceinline__ void init() {
+    job = 0;
+    next = end = 0;
+    done = false;
+  }
+  // Lanes with `want` receive a path index of item `my_job`, or -1 once the queue is empty.
+  __device__ __forceinline__ int64_t take(const BatchArgs& a, bool want, int& my_job) {
+    const unsigned lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    int64_t mine = -1;
+    while (m != 0u && !done) {
+      if (next >= end) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.ticket, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int64_t)t >= a.n_chunks) {
+          done = true;
+          break;
+        }
+        int lo = 0, hi = a.n_jobs - 1;  // the last item whose first chunk is <= t
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.jobs[mid].chunk0 <= (int64_t)t) lo = mid; else hi = mid - 1;
+        }
+        job = lo;
+        next = ((int64_t)t - a.jobs[lo].chunk0) * a.chunk;
+        end = min(next + (int64_t)a.chunk, a.jobs[lo].kp.n_paths);
+      }
+      const bool in = (m >> lane) & 1u;
+      const int rank = __popc(m & ((1u << lane) - 1u));
+      const int64_t avail = end - next;
+      const int n = (int64_t)__popc(m) < avail ? __popc(m) : (int)avail;
+      if (in && rank < n) {
+        mine = next + rank;
+        my_job = job;
+      }
+      next += n;
+      m = __ballot_sync(0xffffffffu, in && rank >= n);
+    }
+    return mine;
+  }
+};
+
+__device__ __forceinline__ void add3(float* d, float3 v) {
+  if (!d || (v.x == 0.0f && v.y == 0.0f && v.z == 0.0f)) return;
+  atomicAdd(d, v.x);
+  atomicAdd(d + 1, v.y);
+  atomicAdd(d + 2, v.z);
+}
+
 // ======================================================================= primal
 // One lane per path with lane regeneration (see Dispenser): each iteration of the step
 // loop performs one vertex of the lane's current path.
-template <int EST>
-__global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
+// BATCH: the lane's scene, parameters and outputs are those of the batch item its path
+// belongs to (BatchDispenser); S0, kp0, image0 and aux0 are not used.
+template <int EST, bool BATCH>
+__device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& kp0, float* __restrict__ image0,
+                                            void* aux0, const BatchArgs& ba) {
   // learned reservoir target: network image and one 32x16 feature tile per warp
   extern __shared__ __align__(16) unsigned char psmem[];
   MlpSmem& mlp = *reinterpret_cast<MlpSmem*>(psmem);
   __nv_bfloat16* ftile = reinterpret_cast<__nv_bfloat16*>(psmem + ((sizeof(MlpSmem) + 15) & ~size_t(15))) +
                          (threadIdx.x >> 5) * 32 * kMlpIn;
-  const bool learned = EST == 1 && kp.mlp != nullptr;
+  const bool learned = !BATCH && EST == 1 && kp0.mlp != nullptr;
   if (learned) {
-    mlp_load_smem(mlp, kp.mlp);
+    mlp_load_smem(mlp, kp0.mlp);
     __syncthreads();
   }
-  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  float3 Le = BATCH ? f3(0, 0, 0) : f3(kp0.Le[0], kp0.Le[1], kp0.Le[2]);
   Dispenser disp;
-  disp.init(kp.n_paths);
+  BatchDispenser bdisp;
+  if (BATCH) bdisp.init(); else disp.init(kp0.n_paths);
+  int jb = 0;
   bool busy = false, more = true, active = false;
   int64_t p = 0;
   int k = 0, nconn = 0;
@@ -670,12 +734,19 @@ __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* _
   int R = -1;
   while (true) {
     const bool want = more && !busy;
-    const int64_t got = disp.take(want);
+    int jnew = jb;
+    const int64_t got = BATCH ? bdisp.take(ba, want, jnew) : disp.take(want);
+    if (BATCH) jb = jnew;
+    const DevScene& S = BATCH ? ba.jobs[jb].S : S0;
+    const KParams& kp = BATCH ? ba.jobs[jb].kp : kp0;
+    float* image = BATCH ? ba.jobs[jb].image : image0;
+    void* aux = BATCH ? ba.jobs[jb].rec : aux0;
     if (want) {
       if (got < 0) {
         more = false;
       } else {
         p = got;
+        if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
         active = !kp.mask || kp.mask[p];
         float3 x0;
         walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
@@ -775,25 +846,42 @@ __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* _
   }
 }
 
+template <int EST>
+__global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
+  primal_body<EST, false>(S, kp, image, aux, BatchArgs{});
+}
+
+template <int EST>
+__global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
+  primal_body<EST, true>(ba.jobs[0].S, ba.jobs[0].kp, nullptr, nullptr, ba);
+}
+
 // ======================================================================= LRB-3-pass
 // Pass 2 (accumulate delta_total, Eq. 14) and pass 3 (backpropagate, Eq. 15-17) per path,
 // run as a per-lane state machine: every iteration of the step loop performs one vertex
 // step (one closest-hit traversal) of whichever pass the lane is in, and a lane that
 // finishes a path takes the next one from its warp's range.  The connection-validity bits
 // found in pass 2 are kept in a register mask so pass 3 traces no visibility rays.
-template <bool ATT, bool ST, bool CH>
-__global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0) {
+// BATCH: per-lane item (BatchDispenser), global gradient atomics, per-item attached flag;
+// S0, kp0, dI0 and g0 are not used.
+template <bool ATT, bool ST, bool CH, bool BATCH>
+__device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0, const float* __restrict__ dI0,
+                                          const GradPtrs& g0, const BatchArgs& ba) {
   extern __shared__ float sgrad[];
-  const Sink sink = sink_begin(kp, g0, sgrad);
-  GradPtrs g = g0;
-  g.d_albedo = sink.alb;
-  g.d_heights = sink.h;
-  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  GradPtrs gs = g0;
+  if (!BATCH) {
+    const Sink sink = sink_begin(kp0, g0, sgrad);
+    gs.d_albedo = sink.alb;
+    gs.d_heights = sink.h;
+  }
+  float3 Le = BATCH ? f3(0, 0, 0) : f3(kp0.Le[0], kp0.Le[1], kp0.Le[2]);
   float3 gLe = f3(0, 0, 0);
   Census cs = {0, 0, 0};
   uint32_t nverts = 0, nconns = 0;
   Dispenser disp;
-  disp.init(kp.n_paths);
+  BatchDispenser bdisp;
+  if (BATCH) bdisp.init(); else disp.init(kp0.n_paths);
+  int jb = 0;
   enum { IDLE = 0, PASS2 = 1, PASS3 = 2 };
   int phase = IDLE, k = 0, last = 0, nconn = 0;
   bool more = true;
@@ -807,12 +895,24 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
   pv.prim = -1;
   while (true) {
     const bool want = more && phase == IDLE;
-    const int64_t got = disp.take(want);
+    int jnew = jb;
+    const int64_t got = BATCH ? bdisp.take(ba, want, jnew) : disp.take(want);
+    if (BATCH && jnew != jb) {
+      add3(ba.jobs[jb].g.d_Le, gLe);  // emitted-radiance gradient of the lane's previous item
+      gLe = f3(0, 0, 0);
+      jb = jnew;
+    }
+    const DevScene& S = BATCH ? ba.jobs[jb].S : S0;
+    const KParams& kp = BATCH ? ba.jobs[jb].kp : kp0;
+    const float* dI = BATCH ? ba.jobs[jb].dI : dI0;
+    const GradPtrs& g = BATCH ? ba.jobs[jb].g : gs;
+    const bool att = ATT && (!BATCH || ba.jobs[jb].att);
     if (want) {
       if (got < 0) {
         more = false;
       } else if (!kp.mask || kp.mask[got]) {
         p = got;
+        if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
         float3 x0;
         walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
         dtot = f3(0, 0, 0);
@@ -878,7 +978,7 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
       ++k;
     } else {
       if (!alive) {
-        if (ATT) pend_flush<CH>(S, kp, n, pv, g.d_heights);
+        if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights);
         phase = IDLE;
         continue;
       }
@@ -886,7 +986,7 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
       float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
       // attached segment weight and chain bookkeeping: every connection from here on
       // carries this vertex's factors, so they weigh the remaining adjoint before Eq. 16
-      if (ATT) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights);
+      if (att) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights);
       float3 rho = f3(0, 0, 0);
       if (v.diffuse) {
         TexFoot foot;
@@ -895,34 +995,94 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
         if ((valid >> k) & 1ull) {
           float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
           float2 q;
-          float3 Lb = adjoint_read(dI, S.W, S.H, c.ux, c.uy, L, ATT ? &q : nullptr);
+          float3 Lb = adjoint_read(dI, S.W, S.H, c.ux, c.uy, L, att ? &q : nullptr);
           float3 P = mul(Lb, L);
           wsplat = P;           // splat factor rho_k / pi (Eq. 15)
           rem = rem - P;        // Eq. 16
-          if (ATT) conn_adjoint(S, v.x, v.nraw, hsum(P), q, pv.gx, pv.gn);
+          if (att) conn_adjoint(S, v.x, v.nraw, hsum(P), q, pv.gx, pv.gn);
         }
         scatter_albedo(g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor rho_k (Eq. 17)
-        if (ATT && CH && !v.attached)
+        if (att && CH && !v.attached)
           pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
       }
       walk_scatter(S, w, v, ns, rho, r);
       ++k;
     }
   }
-  if (ST && kp.census) {
-    atomicAdd(kp.census + 0, (unsigned long long)cs.rays);
-    atomicAdd(kp.census + 1, (unsigned long long)cs.nodes);
-    atomicAdd(kp.census + 2, (unsigned long long)cs.prims);
-    atomicAdd(kp.census + 3, (unsigned long long)nverts);
-    atomicAdd(kp.census + 4, (unsigned long long)nconns);
+  if (BATCH) {
+    add3(ba.jobs[jb].g.d_Le, gLe);
+    return;
   }
-  sink_end(kp, g0, sgrad);
-  block_add3(g.d_Le, gLe);
+  if (ST && kp0.census) {
+    atomicAdd(kp0.census + 0, (unsigned long long)cs.rays);
+    atomicAdd(kp0.census + 1, (unsigned long long)cs.nodes);
+    atomicAdd(kp0.census + 2, (unsigned long long)cs.prims);
+    atomicAdd(kp0.census + 3, (unsigned long long)nverts);
+    atomicAdd(kp0.census + 4, (unsigned long long)nconns);
+  }
+  sink_end(kp0, g0, sgrad);
+  block_add3(g0.d_Le, gLe);
+}
+
+template <bool ATT, bool ST, bool CH>
+__global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0) {
+  lrb3_body<ATT, ST, CH, false>(S, kp, dI, g0, BatchArgs{});
+}
+
+template <bool ATT, bool CH>
+__global__ void __launch_bounds__(256) k_lrb3_batch(BatchArgs ba) {
+  lrb3_body<ATT, false, CH, true>(ba.jobs[0].S, ba.jobs[0].kp, nullptr, ba.jobs[0].g, ba);
 }
 
 // ======================================================================= ResLRB backward
 // Replay to the selected vertex R and apply the log-derivative identity with weight
 // Lbar_R * S to every factor of L_R (Eq. 11); attached adds the positional channel.
+// One path of the ResLRB backward pass; `att` selects the attached formulation (ATT gates
+// its code at compile time).  gLe accumulates the emitted-radiance gradient.
+template <bool ATT, bool CH>
+__device__ __forceinline__ void reslrb_path(const DevScene& S, const KParams& kp, const float* __restrict__ dI,
+                                            const float4* __restrict__ rec, const GradPtrs& g, int64_t p, bool att,
+                                            float3 Le, float3& gLe) {
+  if (kp.mask && !kp.mask[p]) return;
+  float4 r0 = rec[2 * p], r1 = rec[2 * p + 1];
+  int R = __float_as_int(r0.x);
+  if (R < 0) return;
+  if (R >= kp.max_depth) { set_err(S, ERR_BOUNDS); return; }
+  const uint64_t n = (uint64_t)(kp.path_offset + p);
+  float3 Sh = f3(r1.x, r1.y, r1.z);
+  float2 q;
+  float3 Lb = adjoint_read(dI, S.W, S.H, r0.z, r0.w, Sh, att ? &q : nullptr);
+  float3 P = mul(Lb, Sh);
+  float lam = hsum(P);
+  gLe = gLe + f3(P.x / Le.x, P.y / Le.y, P.z / Le.z);
+  Walk w;
+  float3 x0;
+  walk_start(S, kp.seed, n, Le, w, x0);
+  PendAdj pv;
+  pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+  ChainInfo chain;
+  chain.ka = -1;
+  for (int k = 0; k <= R; ++k) {
+    Vtx v;
+    if (!walk_hit(S, w, v)) { set_err(S, ERR_BOUNDS); break; }
+    float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+    if (att) att_enter<CH>(S, kp, n, k, v, lam, lam, pv, chain, g.d_heights);
+    float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+    if (v.diffuse) {
+      ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+      TexFoot foot;
+      rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
+      scatter_albedo(g.d_albedo, foot, P, rho);  // scattering factor (k < R) or splat factor (k = R)
+      if (att) {
+        if (k == R) conn_adjoint(S, v.x, v.nraw, lam, q, pv.gx, pv.gn);
+        if (CH && !v.attached) pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, P, rho);
+      }
+    }
+    walk_scatter(S, w, v, ns, rho, r);
+  }
+  if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights);
+}
+
 template <bool ATT, bool CH>
 __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const float* __restrict__ dI,
                                                 const float4* __restrict__ rec, GradPtrs g0) {
@@ -934,48 +1094,34 @@ __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const fl
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
   float3 gLe = f3(0, 0, 0);
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
-    if (kp.mask && !kp.mask[p]) continue;
-    float4 r0 = rec[2 * p], r1 = rec[2 * p + 1];
-    int R = __float_as_int(r0.x);
-    if (R < 0) continue;
-    if (R >= kp.max_depth) { set_err(S, ERR_BOUNDS); continue; }
-    const uint64_t n = (uint64_t)(kp.path_offset + p);
-    float3 Sh = f3(r1.x, r1.y, r1.z);
-    float2 q;
-    float3 Lb = adjoint_read(dI, S.W, S.H, r0.z, r0.w, Sh, ATT ? &q : nullptr);
-    float3 P = mul(Lb, Sh);
-    float lam = hsum(P);
-    gLe = gLe + f3(P.x / Le.x, P.y / Le.y, P.z / Le.z);
-    Walk w;
-    float3 x0;
-    walk_start(S, kp.seed, n, Le, w, x0);
-    PendAdj pv;
-    pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
-    ChainInfo chain;
-    chain.ka = -1;
-    for (int k = 0; k <= R; ++k) {
-      Vtx v;
-      if (!walk_hit(S, w, v)) { set_err(S, ERR_BOUNDS); break; }
-      float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
-      if (ATT) att_enter<CH>(S, kp, n, k, v, lam, lam, pv, chain, g.d_heights);
-      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
-      if (v.diffuse) {
-        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
-        TexFoot foot;
-        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
-        scatter_albedo(g.d_albedo, foot, P, rho);  // scattering factor (k < R) or splat factor (k = R)
-        if (ATT) {
-          if (k == R) conn_adjoint(S, v.x, v.nraw, lam, q, pv.gx, pv.gn);
-          if (CH && !v.attached) pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, P, rho);
-        }
-      }
-      walk_scatter(S, w, v, ns, rho, r);
-    }
-    if (ATT) pend_flush<CH>(S, kp, n, pv, g.d_heights);
-  }
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride)
+    reslrb_path<ATT, CH>(S, kp, dI, rec, g, p, ATT, Le, gLe);
   sink_end(kp, g0, sgrad);
   block_add3(g.d_Le, gLe);
+}
+
+// Batched ResLRB backward: lanes take paths from the batch queue (one path each per turn).
+template <bool ATT, bool CH>
+__global__ void __launch_bounds__(256) k_reslrb_batch(BatchArgs ba) {
+  BatchDispenser bdisp;
+  bdisp.init();
+  int jb = 0;
+  float3 gLe = f3(0, 0, 0);
+  while (true) {
+    int jnew = jb;
+    const int64_t p = bdisp.take(ba, true, jnew);
+    if (jnew != jb) {
+      add3(ba.jobs[jb].g.d_Le, gLe);
+      gLe = f3(0, 0, 0);
+      jb = jnew;
+    }
+    if (!__any_sync(0xffffffffu, p >= 0)) break;
+    if (p < 0) continue;
+    const BatchJob& J = ba.jobs[jb];
+    const float3 Le = f3(J.kp.Le[0], J.kp.Le[1], J.kp.Le[2]);
+    reslrb_path<ATT, CH>(J.S, J.kp, J.dI, (const float4*)J.rec, J.g, p, ATT && J.att, Le, gLe);
+  }
+  add3(ba.jobs[jb].g.d_Le, gLe);
 }
 
 // ======================================================================= naive reverse
@@ -1173,6 +1319,46 @@ cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI
   k_collect<<<grid, L.block, 0, st>>>(S, kp, dI, tfloor, feats, targets, cap, count);
   return cudaGetLastError();
 }
+
+template <class K>
+static int occupancy_of(K kern, int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, 0) != cudaSuccess) return 0;
+  return n;
+}
+
+// Kernel of a batched pass (the same selection as launch_batch).
+#define LT_BATCH_DISPATCH(CALL)                                                  \
+  switch (pass) {                                                                \
+    case BPASS_PRIMAL: CALL(k_primal_batch<0>); break;                           \
+    case BPASS_PRIMAL_RES: CALL(k_primal_batch<1>); break;                       \
+    case BPASS_LRB3:                                                             \
+      if (att && chains) CALL((k_lrb3_batch<true, true>));                       \
+      else if (att) CALL((k_lrb3_batch<true, false>));                           \
+      else CALL((k_lrb3_batch<false, false>));                                   \
+      break;                                                                     \
+    default:                                                                     \
+      if (att && chains) CALL((k_reslrb_batch<true, true>));                     \
+      else if (att) CALL((k_reslrb_batch<true, false>));                         \
+      else CALL((k_reslrb_batch<false, false>));                                 \
+      break;                                                                     \
+  }
+
+cudaError_t launch_batch(int pass, bool att, bool chains, const BatchArgs& a, int block, int grid, cudaStream_t st) {
+#define LT_LAUNCH_ONE(K) K<<<grid, block, 0, st>>>(a)
+  LT_BATCH_DISPATCH(LT_LAUNCH_ONE)
+#undef LT_LAUNCH_ONE
+  return cudaGetLastError();
+}
+
+int batch_occupancy(int pass, bool att, bool chains, int block) {
+  int n = 0;
+#define LT_OCC_ONE(K) n = occupancy_of(K, block)
+  LT_BATCH_DISPATCH(LT_OCC_ONE)
+#undef LT_OCC_ONE
+  return n;
+}
+#undef LT_BATCH_DISPATCH
 
 cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,
                            cudaStream_t st) {

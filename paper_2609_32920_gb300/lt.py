@@ -59,6 +59,17 @@ class lt_grads(C.Structure):
     _fields_ = [("d_albedo", C.c_void_p), ("d_Le", C.c_void_p), ("d_heights", C.c_void_p), ("accumulate", C.c_int)]
 
 
+class lt_batch_item(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("params", lt_params), ("heights", C.c_void_p), ("opts", lt_render_opts),
+                ("image", C.c_void_p), ("records", C.c_void_p), ("d_image", C.c_void_p), ("grads", lt_grads)]
+
+
+class lt_batch_config(C.Structure):
+    _fields_ = [("block_size", C.c_int), ("paths_per_thread", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
+PASS_PRIMAL, PASS_PRIMAL_RESLRB, PASS_LRB3, PASS_RESLRB = 0, 1, 2, 3
+
 _lib = None
 _lock = threading.Lock()
 
@@ -66,7 +77,8 @@ _lock = threading.Lock()
 EXPORTS = ["lt_scene_create", "lt_scene_refit", "lt_scene_destroy", "lt_primal", "lt_backward_lrb3",
            "lt_backward_reslrb", "lt_backward_naive", "lt_film_l2", "lt_record_size", "lt_naive_workspace_bytes",
            "lt_sync_status", "lt_last_error", "lt_version", "lt_mlp_collect", "lt_mlp_init_stats", "lt_mlp_grad",
-           "lt_mlp_adam", "lt_mlp_forward", "lt_naive_gradient_static"]
+           "lt_mlp_adam", "lt_mlp_forward", "lt_naive_gradient_static", "lt_batch_create", "lt_batch_run",
+           "lt_batch_set_config", "lt_batch_get_config", "lt_batch_tune", "lt_batch_destroy"]
 MLP_PARAMS, MLP_WEIGHTS = 5352, 5313
 
 
@@ -100,6 +112,13 @@ def lib():
             L.lt_mlp_grad.argtypes = [V, V, V, C.c_int64, C.c_int64, V, V, V]
             L.lt_mlp_adam.argtypes = [V, V, V, V, C.c_int, C.c_float, V]
             L.lt_mlp_forward.argtypes = [V, V, C.c_int64, V, V]
+            L.lt_batch_create.argtypes = [P(lt_batch_item), C.c_int, V, P(V)]
+            L.lt_batch_run.argtypes = [V, C.c_int, V]
+            L.lt_batch_set_config.argtypes = [V, P(lt_batch_config)]
+            L.lt_batch_get_config.argtypes = [V, P(lt_batch_config)]
+            L.lt_batch_tune.argtypes = [V, C.c_int, C.c_int, V, P(lt_batch_config), P(C.c_float)]
+            L.lt_batch_destroy.argtypes = [V]
+            L.lt_batch_destroy.restype = None
             _lib = L
     return _lib
 
@@ -272,6 +291,76 @@ class Scene:
 
     def sync_status(self, stream=None):
         _check(lib().lt_sync_status(self._h, _stream(stream)))
+
+
+class Batch:
+    """Many scenes in one persistent launch per pass (lt_batch_*).
+
+    `items`: list of dicts with keys scene (Scene), n_paths, max_depth and optionally seed,
+    path_offset, n_norm, attached, albedo, Le, heights (refit by the primal passes),
+    d_image, reslrb (allocate ResLRB records), accumulate.  The batch allocates each item's
+    image, records and gradients (attributes of the item dicts: image, records, grads) and
+    keeps every tensor alive; change parameter values in place (copy_) between runs."""
+
+    def __init__(self, items, stream=None):
+        self.items = items
+        arr = (lt_batch_item * len(items))()
+        for k, it in enumerate(items):
+            S = it["scene"]
+            o = Scene.opts(seed=it.get("seed", 0), n_paths=it["n_paths"], max_depth=it["max_depth"],
+                           attached=it.get("attached", 0), path_offset=it.get("path_offset", 0),
+                           n_norm=it.get("n_norm", 0), dbg_out=it.get("dbg_out"))
+            it.setdefault("albedo", S.albedo)
+            it.setdefault("Le", S.Le)
+            it.setdefault("d_image", torch.zeros((S.H, S.W, 3), device=S.device))
+            it["image"] = S.new_image()
+            it["grads"] = S.new_grads()
+            it["records"] = (torch.empty((max(1, it["n_paths"]), 8), device=S.device)
+                             if it.get("reslrb") else None)
+            it["_opts"] = o
+            e = arr[k]
+            e.scene = S._h.value
+            e.params = lt_params(it["albedo"].data_ptr(), it["Le"].data_ptr())
+            h = it.get("heights")
+            e.heights = None if h is None else h.data_ptr()
+            e.opts = o
+            e.image = it["image"].data_ptr()
+            e.records = None if it["records"] is None else it["records"].data_ptr()
+            e.d_image = it["d_image"].data_ptr()
+            e.grads = S._grads(*it["grads"], it.get("accumulate", False))
+        h = C.c_void_p()
+        _check(lib().lt_batch_create(arr, len(items), _stream(stream), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            try:
+                torch.cuda.synchronize()
+            except Exception:
+                pass
+            _lib.lt_batch_destroy(h)
+            self._h = None
+
+    def run(self, pass_id, stream=None):
+        _check(lib().lt_batch_run(self._h, int(pass_id), _stream(stream)))
+
+    def config(self):
+        c = lt_batch_config()
+        _check(lib().lt_batch_get_config(self._h, C.byref(c)))
+        return dict(block_size=c.block_size, paths_per_thread=c.paths_per_thread, blocks_per_sm=c.blocks_per_sm)
+
+    def set_config(self, block_size=128, paths_per_thread=4, blocks_per_sm=0):
+        c = lt_batch_config(int(block_size), int(paths_per_thread), int(blocks_per_sm))
+        _check(lib().lt_batch_set_config(self._h, C.byref(c)))
+
+    def tune(self, pass_id, reps=2, stream=None):
+        """Autotune block size x paths per thread for `pass_id`; returns (config, ms)."""
+        c = lt_batch_config()
+        ms = C.c_float()
+        _check(lib().lt_batch_tune(self._h, int(pass_id), int(reps), _stream(stream), C.byref(c), C.byref(ms)))
+        return dict(block_size=c.block_size, paths_per_thread=c.paths_per_thread, blocks_per_sm=c.blocks_per_sm), \
+            float(ms.value)
 
 
 def film_l2(image, target, d_image=None, loss=None, stream=None):
