@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
     ap.add_argument("--paths-log2", type=int, default=22, help="paths per GPU per step (profiling uses fewer)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-target study")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched many-scene study")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: only warm-up and timed steps (no e2e, census, sweep or CPU baseline)")
     return ap.parse_args()
@@ -309,6 +310,9 @@ def run_ours(args):
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_target_study(dev)
+    batched = None
+    if not args.no_batch and rank == 0:
+        batched = batched_study(dev)
     clk = clocks.stop()
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N=1 only)
@@ -330,7 +334,7 @@ def run_ours(args):
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
                 "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory,
-                "learned_target": learned,
+                "learned_target": learned, "batched": batched,
                 "lib": lt.version()}
         print(json.dumps(line))
     if ws > 1:
@@ -470,6 +474,76 @@ def _learned_one(dev, kind, seeds, paths_log2, depth):
 
 def learned_target_study(dev):
     return {"caustic": _learned_one(dev, "caustic", 16, 20, 32), "interior": _learned_one(dev, "interior", 16, 20, 16)}
+
+
+def batched_study(dev, n_scenes=64, reps=3):
+    """Many scenes of uneven size (caustic slabs and boxes, height fields 32^2..256^2,
+    depth 4..32, 2^16..2^22 paths, attached) in one persistent launch per pass, against the
+    same work issued scene by scene.  One iteration = refit + primal + LRB-3 backward of
+    every scene.  The batch's launch shape comes from its autotuner (LRB-3 pass)."""
+    import torch
+
+    from paper_2609_32920_gb300 import inputs as I
+    from paper_2609_32920_gb300 import lt
+    t0 = time.time()
+    items = []
+    for k, spec in enumerate(I.batched_set(n_scenes, seed=0, max_paths_log2=22)):
+        S = lt.Scene(spec["scene"])
+        it = dict(scene=S, n_paths=spec["n_paths"], max_depth=spec["max_depth"], attached=spec["attached"], seed=k)
+        if S.n_heights:
+            it["heights"] = S.heights.clone()
+        it["d_image"] = torch.tensor(I.smooth_adjoint(S.W, S.H, 500 + k), dtype=torch.float32, device=dev)
+        items.append(it)
+    build_s = time.time() - t0
+    B = lt.Batch(items)
+    B.run(lt.PASS_PRIMAL)
+    t1 = time.time()
+    cfg, tuned_ms = B.tune(lt.PASS_LRB3, reps=1)
+    tune_s = time.time() - t1
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        ms = []
+        fn()
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    def batched():
+        B.run(lt.PASS_PRIMAL)
+        B.run(lt.PASS_LRB3)
+
+    opts = [it["scene"].opts(seed=it["seed"], n_paths=it["n_paths"], max_depth=it["max_depth"],
+                             attached=it["attached"]) for it in items]
+    grads = [it["scene"].new_grads() for it in items]
+    imgs = [it["scene"].new_image() for it in items]
+
+    def sequential():
+        for it, o, g, im in zip(items, opts, grads, imgs):
+            S = it["scene"]
+            if S.n_heights:
+                S.refit(it["heights"])
+            S.primal(o, image=im)
+            S.backward_lrb3(o, it["d_image"], grads=g)
+
+    ms_b = timed(batched)
+    ms_s = timed(sequential)
+    total = sum(it["n_paths"] for it in items)
+    for it in items:
+        it["scene"].sync_status()
+    return {"workload": "%d scenes: slab/box alternating, height fields 32^2..256^2, depth 4..32, "
+                        "2^16..2^22 paths, attached, 128x128 film" % n_scenes,
+            "total_paths": total, "tris": sum(it["scene"].src.n_tris for it in items),
+            "batched": {"ms_per_iteration": ms_b, "paths_per_s": total / (ms_b * 1e-3), "config": cfg,
+                        "tuned_lrb3_pass_ms": tuned_ms, "tune_s": tune_s},
+            "per_scene_calls": {"ms_per_iteration": ms_s, "paths_per_s": total / (ms_s * 1e-3)},
+            "speedup": ms_s / ms_b, "scene_build_s": build_s}
 
 
 def main():

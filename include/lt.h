@@ -241,11 +241,13 @@ lt_status lt_naive_gradient_static(lt_scene* scene, const lt_params* params, con
 /* ---------------------------------------------------------------------------------
  * Batched passes (no counterpart in the paper, which renders one scene at a time):
  * many scenes with uneven path budgets, depths and geometry run their paths in ONE
- * persistent launch per pass.  Each item's path range is cut into chunks of
- * 32 * paths_per_thread paths; a warp takes the next chunk of the whole batch with one
- * atomic, so items of any size share the GPU without a launch per item.  Each pass
- * (its clears, height refits and the kernel) is captured once into a CUDA graph and
- * replayed by lt_batch_run.  Per path the work is the same as the single-scene call
+ * persistent launch per pass and kernel variant.  Each item's path range is cut into
+ * chunks of 32 * paths_per_thread paths; a warp takes the next chunk of its launch with
+ * one atomic, so items of any size share the GPU without a launch per item.  Backward
+ * passes run attached items on scenes with dielectrics (specular chains) in a second
+ * persistent kernel, a parallel branch of the same graph, because that kernel variant
+ * needs about twice the registers.  Each pass (its clears, height refits and kernels) is
+ * captured once into a CUDA graph and replayed by lt_batch_run.  Per path the work is the same as the single-scene call
  * with the item's opts, so results match those calls up to floating-point summation
  * order (atomics).
  *

@@ -688,17 +688,25 @@ lt_status lt_sync_status(lt_scene* s, void* stream) {
 // ------------------------------------------------------------------ batched passes
 }  // extern "C"
 
+// Kernel groups of a batch: the specular-chain variant of the attached backward kernels
+// needs about twice the registers of the lean variant (half the resident warps), so only
+// items that can form chains (attached, scene with dielectrics) run it.  The item table
+// holds the lean group first, then the chain group; the backward passes launch one
+// persistent kernel per non-empty group, as two parallel branches of the pass's graph.
 struct lt_batch {
   int device = 0, sms = 1;
-  std::vector<lt_batch_item> items;
-  bool any_att = false, chains = false, all_rec = true;
+  std::vector<lt_batch_item> items;  // table order (lean group, then chain group)
+  int n_lean = 0;                    // items [0, n_lean) form the lean group
+  bool att_lean = false, all_rec = true;
   // one item table per chunk size (32 * paths_per_thread, paths_per_thread = 1, 2, 4, 8):
   // only the first-chunk indices differ, and a configuration change must not rewrite a
   // table that a running pass may still read
   BatchJob* d_jobs[4] = {};
-  int64_t n_chunks[4] = {};
-  unsigned long long* d_ticket = nullptr;  // [4], one per pass
-  cudaStream_t cap = nullptr;              // capture stream
+  int64_t n_chunks[4] = {};   // whole batch
+  int64_t split[4] = {};      // first chunk of the chain group
+  unsigned long long* d_ticket = nullptr;  // [4 passes][2 groups]
+  cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams (main, second branch)
+  cudaEvent_t fork = nullptr, join = nullptr;
   lt_batch_config cfg{128, 4, 0};
   cudaGraphExec_t exec[4] = {};
 };
@@ -720,6 +728,9 @@ void free_batch(lt_batch* b) {
   for (auto* j : b->d_jobs) cudaFree(j);
   cudaFree(b->d_ticket);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap2) cudaStreamDestroy(b->cap2);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   delete b;
 }
 
@@ -738,9 +749,54 @@ int kernel_pass(int pass) {
          : pass == LT_PASS_LRB3 ? BPASS_LRB3 : BPASS_RESLRB;
 }
 
-// Enqueue one pass on `st`: clears and refits of every item, the queue reset, the kernel
-// with `per_sm` resident blocks per SM.
-lt_status enqueue_pass(lt_batch* b, int pass, int per_sm, cudaStream_t st) {
+// One persistent launch of the pass over the items [j0, j1) of the table.
+struct GroupLaunch {
+  int j0 = 0, j1 = 0;
+  int64_t c0 = 0, c1 = 0;  // chunk range
+  bool att = false, chains = false;
+  int per_sm = 0;
+};
+
+std::vector<GroupLaunch> plan_pass(const lt_batch* b, int pass) {
+  const int slot = ppt_slot(b->cfg.paths_per_thread);
+  const int n = (int)b->items.size();
+  std::vector<GroupLaunch> out;
+  const bool primal = pass == LT_PASS_PRIMAL || pass == LT_PASS_PRIMAL_RESLRB;
+  if (primal) {
+    out.push_back(GroupLaunch{0, n, 0, b->n_chunks[slot], false, false, 0});
+  } else {
+    out.push_back(GroupLaunch{0, b->n_lean, 0, b->split[slot], b->att_lean, false, 0});
+    out.push_back(GroupLaunch{b->n_lean, n, b->split[slot], b->n_chunks[slot], true, true, 0});
+  }
+  std::vector<GroupLaunch> keep;
+  for (GroupLaunch& g : out) {
+    if (g.c1 <= g.c0) continue;
+    g.per_sm = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm
+                                        : batch_occupancy(kernel_pass(pass), g.att, g.chains, b->cfg.block_size);
+    keep.push_back(g);
+  }
+  return keep;
+}
+
+lt_status launch_group(lt_batch* b, int pass, int gi, const GroupLaunch& g, cudaStream_t st) {
+  const int slot = ppt_slot(b->cfg.paths_per_thread);
+  unsigned long long* ticket = b->d_ticket + 2 * pass + gi;
+  LT_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st));
+  const int block = b->cfg.block_size;
+  // a resident grid, but no more warps than chunks
+  const int64_t nch = g.c1 - g.c0;
+  const int64_t warps_per_block = block / 32;
+  int64_t grid = std::min<int64_t>((int64_t)b->sms * g.per_sm, (nch + warps_per_block - 1) / warps_per_block);
+  BatchArgs a{b->d_jobs[slot] + g.j0, g.j1 - g.j0, 32 * b->cfg.paths_per_thread, g.c0, nch, ticket};
+  cudaError_t e = launch_batch(kernel_pass(pass), g.att, g.chains, a, block, (int)std::max<int64_t>(grid, 1), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("batched pass: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+// Enqueue one pass on `st`: clears and refits of every item, then the group launches
+// (a second group runs on a forked branch `st2`, joined back into `st`).
+lt_status enqueue_pass(lt_batch* b, int pass, const std::vector<GroupLaunch>& plan, cudaStream_t st,
+                       cudaStream_t st2) {
   const bool primal = pass == LT_PASS_PRIMAL || pass == LT_PASS_PRIMAL_RESLRB;
   for (const lt_batch_item& it : b->items) {
     const lt_scene* s = it.scene;
@@ -757,29 +813,28 @@ lt_status enqueue_pass(lt_batch* b, int pass, int per_sm, cudaStream_t st) {
       if (v != LT_OK) return v;
     }
   }
-  const int slot = ppt_slot(b->cfg.paths_per_thread);
-  const int64_t nch = b->n_chunks[slot];
-  if (nch == 0) return LT_OK;
-  LT_CUDA(cudaMemsetAsync(b->d_ticket + pass, 0, sizeof(unsigned long long), st));
-  const int kpass = kernel_pass(pass);
-  const int block = b->cfg.block_size;
-  // a resident grid, but no more warps than chunks
-  const int64_t warps_per_block = block / 32;
-  int64_t grid = (int64_t)b->sms * per_sm;
-  grid = std::min<int64_t>(grid, (nch + warps_per_block - 1) / warps_per_block);
-  BatchArgs a{b->d_jobs[slot], (int)b->items.size(), 32 * b->cfg.paths_per_thread, nch, b->d_ticket + pass};
-  cudaError_t e = launch_batch(kpass, b->any_att, b->chains, a, block, (int)std::max<int64_t>(grid, 1), st);
-  if (e) return fail(LT_ERR_CUDA, std::string("batched pass: ") + cudaGetErrorString(e));
+  if (plan.size() == 2) {
+    LT_CUDA(cudaEventRecord(b->fork, st));
+    LT_CUDA(cudaStreamWaitEvent(st2, b->fork, 0));
+    lt_status v = launch_group(b, pass, 1, plan[1], st2);
+    if (v != LT_OK) return v;
+    LT_CUDA(cudaEventRecord(b->join, st2));
+  }
+  if (!plan.empty()) {
+    lt_status v = launch_group(b, pass, 0, plan[0], st);
+    if (v != LT_OK) return v;
+  }
+  if (plan.size() == 2) LT_CUDA(cudaStreamWaitEvent(st, b->join, 0));
   return LT_OK;
 }
 
-// Capture the pass on the batch's own stream and instantiate it.
+// Capture the pass on the batch's own streams and instantiate it.
 lt_status capture_pass(lt_batch* b, int pass) {
-  int per_sm = b->cfg.blocks_per_sm;
-  if (per_sm == 0) per_sm = batch_occupancy(kernel_pass(pass), b->any_att, b->chains, b->cfg.block_size);
-  if (per_sm < 1) return fail(LT_ERR_CUDA, "batched kernel cannot be resident at this block size");
+  const std::vector<GroupLaunch> plan = plan_pass(b, pass);
+  for (const GroupLaunch& g : plan)
+    if (g.per_sm < 1) return fail(LT_ERR_CUDA, "batched kernel cannot be resident at this block size");
   LT_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  lt_status v = enqueue_pass(b, pass, per_sm, b->cap);
+  lt_status v = enqueue_pass(b, pass, plan, b->cap, b->cap2);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   if (v != LT_OK) {
@@ -816,7 +871,7 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
   LT_CUDA(cudaGetDevice(&dev));
   std::unique_ptr<lt_batch, void (*)(lt_batch*)> b(new lt_batch, free_batch);
   b->device = dev;
-  std::vector<BatchJob> jobs(n);
+  std::vector<lt_batch_item> lean, chain;
   for (int i = 0; i < n; ++i) {
     lt_batch_item it = items[i];
     const std::string at = "item " + std::to_string(i) + ": ";
@@ -833,16 +888,26 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     if (!it.image || !it.d_image) return fail(LT_ERR_INVALID_ARG, at + "image or d_image is NULL");
     if (it.heights && it.scene->n_heights > 0)
       for (int j = 0; j < i; ++j)
-        if (b->items[j].scene == it.scene && b->items[j].heights)
+        if (items[j].scene == it.scene && items[j].heights)
           return fail(LT_ERR_INVALID_ARG, at + "two items with heights share a scene");
-    b->items.push_back(it);
     b->sms = it.scene->sms;
-    b->any_att |= it.opts.attached != 0;
-    b->chains |= it.opts.attached != 0 && it.scene->has_dielectric;
     b->all_rec &= it.records != nullptr || it.opts.n_paths == 0;
+    if (it.opts.attached != 0 && it.scene->has_dielectric) {
+      chain.push_back(it);
+    } else {
+      b->att_lean |= it.opts.attached != 0;
+      lean.push_back(it);
+    }
+  }
+  b->n_lean = (int)lean.size();
+  b->items = lean;
+  b->items.insert(b->items.end(), chain.begin(), chain.end());
+  std::vector<BatchJob> jobs(n);
+  for (int i = 0; i < n; ++i) {
+    const lt_batch_item& it = b->items[i];
     BatchJob& J = jobs[i];
     J.S = it.scene->dev;
-    J.kp = kparams(&it.params, &b->items[i].opts);
+    J.kp = kparams(&it.params, &it.opts);
     J.dI = it.d_image;
     J.g = GradPtrs{it.grads.d_albedo, it.grads.d_Le, it.grads.d_heights};
     J.image = it.image;
@@ -854,15 +919,20 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     const int64_t chunk = 32ll << slot;
     int64_t c = 0;
     for (int i = 0; i < n; ++i) {
+      if (i == b->n_lean) b->split[slot] = c;
       jobs[i].chunk0 = c;
       c += (jobs[i].kp.n_paths + chunk - 1) / chunk;
     }
+    if (b->n_lean == n) b->split[slot] = c;
     b->n_chunks[slot] = c;
     LT_CUDA(cudaMalloc(&b->d_jobs[slot], sizeof(BatchJob) * n));
     LT_CUDA(cudaMemcpyAsync(b->d_jobs[slot], jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, st));
   }
-  LT_CUDA(cudaMalloc(&b->d_ticket, 4 * sizeof(unsigned long long)));
+  LT_CUDA(cudaMalloc(&b->d_ticket, 8 * sizeof(unsigned long long)));
   LT_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  LT_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
+  LT_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  LT_CUDA(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
   LT_CUDA(cudaStreamSynchronize(st));  // the host copy of the table goes out of scope
   *out = b.release();
   return LT_OK;

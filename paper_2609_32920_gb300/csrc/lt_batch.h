@@ -24,10 +24,13 @@ struct BatchJob {
 // Work queue: the items' path ranges are cut into chunks of `chunk` paths (an item's last
 // chunk may be shorter); a warp takes the next chunk with one atomic on `ticket`, which
 // the pass resets to zero before the launch.
+// A launch serves the items jobs[0, n_jobs): ticket t (0 <= t < n_chunks) is chunk
+// chunk_base + t of the batch.
 struct BatchArgs {
   const BatchJob* jobs;
   int n_jobs;
   int chunk;
+  int64_t chunk_base;
   int64_t n_chunks;
   unsigned long long* ticket;
 };

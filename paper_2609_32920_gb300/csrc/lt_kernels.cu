@@ -669,13 +669,14 @@ struct BatchDispenser {
           done = true;
           break;
         }
-        int lo = 0, hi = a.n_jobs - 1;  // the last item whose first chunk is <= t
+        const int64_t c = a.chunk_base + (int64_t)t;
+        int lo = 0, hi = a.n_jobs - 1;  // the last item whose first chunk is <= c
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
-          if (a.jobs[mid].chunk0 <= (int64_t)t) lo = mid; else hi = mid - 1;
+          if (a.jobs[mid].chunk0 <= c) lo = mid; else hi = mid - 1;
         }
         job = lo;
-        next = ((int64_t)t - a.jobs[lo].chunk0) * a.chunk;
+        next = (c - a.jobs[lo].chunk0) * a.chunk;
         end = min(next + (int64_t)a.chunk, a.jobs[lo].kp.n_paths);
       }
       const bool in = (m >> lane) & 1u;
