@@ -6,9 +6,10 @@ One step = one pass of the hot path over one batch of 2^22 light paths at depth 
   refit the height field's triangles and BVH bounds (2 kernels)
   -> primal light tracing with sensor connection and splat at every vertex (1 kernel)
   -> film L2 loss and image adjoint (1 kernel)
-  -> LRB-3-pass backward, passes 2 and 3 fused, attached gradients w.r.t. the emitted
-     radiance and every height-field vertex height including the splat-position
-     derivative (1 kernel).
+  -> LRB-3-pass backward, attached gradients w.r.t. the emitted radiance and every
+     height-field vertex height including the splat-position derivative (2 kernels:
+     pass 2 stores delta_total and the connection-validity mask per path, pass 3
+     backpropagates).
 Inputs are seeded and synthetic (see paper_2609_32920_gb300.inputs).  `value` is
 device-timed with inputs resident in HBM; `e2e` adds the host->device copy of the step's
 inputs and the device->host copy of loss and gradients.  The ResLRB and naive-AD
@@ -191,14 +192,18 @@ def run_ours(args):
     del T_S
     heights = S.heights.clone()
     o_plain = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, path_offset=path_offset, n_norm=n_norm)
-    o_att = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset, n_norm=n_norm)
+    # LRB-3 in the paper's three-pass form: passes 2 and 3 are two kernels that hand over
+    # delta_total and the connection-validity mask per path (20 B per path, flat in depth)
+    lrb3_state = S.new_lrb3_state(N_PATHS)
+    o_att = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset, n_norm=n_norm,
+                   lrb3_state=lrb3_state)
     img = S.new_image()
     dI = torch.empty_like(img)
     loss = torch.empty(1, device=dev)
     grads = S.new_grads()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
-    launches_per_step = 5  # update_tris, refit_nodes, primal, film_l2, lrb3
+    launches_per_step = 6  # update_tris, refit_nodes, primal, film_l2, lrb3 pass 2, lrb3 pass 3
 
     def step(bwd_events=None):
         S.refit(heights)
@@ -280,7 +285,7 @@ def run_ours(args):
     # ---------------- algorithmic work of the dominant kernel (counting variant, untimed)
     census = torch.zeros(5, dtype=torch.int64, device=dev)
     o_cnt = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset,
-                   n_norm=N_PATHS * ws, census=census)
+                   n_norm=N_PATHS * ws, census=census, lrb3_state=lrb3_state)
     S.backward_lrb3(o_cnt, dI, grads=S.new_grads())
     torch.cuda.synchronize()
     c = [int(x) for x in census.cpu()]
@@ -296,7 +301,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 x max SM clock
     achieved = flops / bwd_mean_s / 1e12
-    roofline = {"bound": "alu", "kernel": "k_lrb3<attached> (LRB-3-pass passes 2+3 fused)",
+    roofline = {"bound": "alu", "kernel": "LRB-3-pass backward, attached: k_lrb3_p2 + k_lrb3_p3 (passes 2 and 3)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "traffic": None, "kernel_ms": 1e3 * bwd_mean_s,
@@ -304,9 +309,11 @@ def run_ours(args):
                            "connections": c[4], "flops_per": FLOPS_PER}}
 
     # ---------------- other estimators + memory vs depth (outside the headline timing)
-    methods, memory = {}, {}
+    methods, memory, caustic = {}, {}, None
     if not args.no_sweep:
         methods, memory = method_sweep(S, sc, target, heights, dev, path_offset, ws, flush)
+        if rank == 0:
+            caustic = caustic_sweep(dev, flush)
     learned = None
     if not args.no_learned and rank == 0:
         learned = learned_target_study(dev)
@@ -333,7 +340,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory,
+                "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory, "caustic_memory_vs_depth": caustic,
                 "learned_target": learned, "batched": batched,
                 "lib": lt.version()}
         print(json.dumps(line))
@@ -343,9 +350,13 @@ def run_ours(args):
     return 0
 
 
-def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
-    """Paths/s of each estimator (primal + backward, attached) at depth 16 and the peak
-    extra device memory of each estimator at depths 4..64."""
+METHODS = ("lrb3", "lrb3_fused", "reslrb", "naive")
+
+
+def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
+    """run(method, D, reps) -> (median ms, peak extra device bytes) of one attached
+    gradient: primal + film L2 + backward.  lrb3 = two-kernel form with its per-path
+    state; lrb3_fused = one fused backward kernel without per-path state."""
     import torch
 
     from paper_2609_32920_gb300 import lt
@@ -356,19 +367,20 @@ def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
     grads = S.new_grads()
 
     def run(method, D, timed_reps=3):
-        o = S.opts(seed=3, n_paths=N_PATHS, max_depth=D, attached=1, path_offset=path_offset,
-                   n_norm=N_PATHS * ws)
         torch.cuda.synchronize()
         base = torch.cuda.memory_allocated()
         torch.cuda.reset_peak_memory_stats()
         aux = None
+        state = S.new_lrb3_state(n_paths) if method == "lrb3" else None
+        o = S.opts(seed=3, n_paths=n_paths, max_depth=D, attached=1, path_offset=path_offset, n_norm=n_norm,
+                   lrb3_state=state)
         if method == "reslrb":
-            aux = torch.empty((N_PATHS, 8), dtype=torch.float32, device=dev)
+            aux = torch.empty((n_paths, 8), dtype=torch.float32, device=dev)
         elif method == "naive":
             aux = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device=dev)
 
         def once():
-            if method == "lrb3":
+            if method.startswith("lrb3"):
                 S.primal(o, image=img)
                 lt.film_l2(img, target, d_image=dI, loss=loss)
                 S.backward_lrb3(o, dI, grads=grads)
@@ -392,21 +404,53 @@ def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
-        del aux
+        del aux, state
         torch.cuda.empty_cache()
         return statistics.median(ms), peak
 
+    return run
+
+
+def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
+    """Paths/s of each estimator (primal + backward, attached) at depth 16 and the peak
+    extra device memory of each estimator at depths 4..64 (box with the 32x32 height field)."""
+    run = _pipeline_runner(S, target, dev, N_PATHS, path_offset, N_PATHS * ws, flush)
     methods = {}
-    for m in ("lrb3", "reslrb", "naive"):
+    for m in METHODS:
         ms, peak = run(m, DEPTH)
         methods[m] = {"paths_per_s": N_PATHS / (ms * 1e-3), "ms": ms, "extra_bytes": peak}
     memory = {}
     for D in (4, 8, 16, 32, 64):
         memory[str(D)] = {}
-        for m in ("lrb3", "reslrb", "naive"):
+        for m in METHODS:
             ms, peak = run(m, D, timed_reps=1)
             memory[str(D)][m] = {"extra_bytes": peak, "ms": ms}
     return methods, memory
+
+
+def caustic_sweep(dev, flush, paths_log2=24):
+    """The caustic workload: a 512x512 camera over a dielectric slab with a 128x128 height
+    field (32k triangles) above a diffuse receiver, 2^24 paths per gradient, attached
+    height gradients of an L2 loss against the caustic of another height field.  Time and
+    peak extra device memory of every estimator at depths 4..64."""
+    import torch
+
+    from paper_2609_32920_gb300 import inputs as I
+    from paper_2609_32920_gb300 import lt
+    n = 1 << paths_log2
+    S = lt.Scene(I.slab_scene(512, n=128, seed=0))
+    T_S = lt.Scene(I.slab_scene(512, n=128, seed=1))
+    target = T_S.primal(T_S.opts(seed=7, n_paths=n, max_depth=8))
+    del T_S
+    run = _pipeline_runner(S, target, dev, n, 0, n, flush)
+    out = {"workload": "slab512_hm128 (caustic), 2^%d paths, attached heights" % paths_log2}
+    for D in (4, 8, 16, 32, 64):
+        out[str(D)] = {}
+        for m in METHODS:
+            ms, peak = run(m, D, timed_reps=1)
+            out[str(D)][m] = {"extra_bytes": peak, "ms": ms, "paths_per_s": n / (ms * 1e-3)}
+    S.sync_status()
+    return out
 
 
 def _learned_one(dev, kind, seeds, paths_log2, depth):

@@ -108,6 +108,13 @@ typedef struct {
                            work done (rays traced, BVH box tests, primitive tests,
                            path vertices, valid connections) using a counting kernel
                            variant; for measurement, not for timed runs           */
+  void* lrb3_state;     /* DEVICE optional, lt_backward_lrb3 only: per-path state of
+                           lt_lrb3_state_bytes(opts) bytes.  Given, passes 2 and 3 run
+                           as two kernels and pass 2 stores each path's delta_total
+                           and connection-validity mask there (20 B per path, the
+                           paper's three-pass form); NULL, one fused kernel keeps
+                           them in registers.  Same result either way.            */
+  size_t lrb3_state_bytes; /* size of lrb3_state                                    */
 } lt_render_opts;
 
 /* Gradient outputs (DEVICE, FP32, caller-owned).  NULL skips a parameter group.
@@ -147,8 +154,11 @@ lt_status lt_primal(lt_scene* scene, const lt_params* params, const lt_render_op
 /* LRB-3-pass backward (Sec. 4.3, Eq. 14-19): pass 2 accumulates
  * delta_total = sum_i Lbar_i * L_i (and in the attached case the positional adjoint),
  * pass 3 replays again, backpropagates each splat with Lbar_i (Eq. 15), subtracts
- * (Eq. 16) and backpropagates the scattering factors with delta_rem (Eq. 17).  Both
- * passes run fused per path; no per-path state reaches global memory.
+ * (Eq. 16) and backpropagates the scattering factors with delta_rem (Eq. 17).  Without
+ * opts->lrb3_state both passes run fused per path and no per-path state reaches global
+ * memory; with it, pass 2 and pass 3 are two kernels that hand delta_total and the
+ * connection-validity mask over through that buffer (memory flat in depth either way).
+ * LT_ERR_INVALID_ARG if lrb3_state_bytes < lt_lrb3_state_bytes(opts).
  * d_image: DEVICE [H][W][3] adjoint dI.  path_dbg (optional) [n_paths][4] =
  * (delta_total rgb, n valid connections). */
 lt_status lt_backward_lrb3(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
@@ -308,6 +318,10 @@ lt_status lt_batch_get_config(const lt_batch* batch, lt_batch_config* cfg);
 lt_status lt_batch_tune(lt_batch* batch, int pass, int reps, void* stream, lt_batch_config* best, float* best_ms);
 
 void lt_batch_destroy(lt_batch* batch);
+
+/* Bytes of the optional LRB-3 per-path state (opts->lrb3_state): 16 B (delta_total rgb,
+ * validity bits 0-31) then 4 B (validity bits 32-63) per path, each array 256-B aligned. */
+size_t lt_lrb3_state_bytes(const lt_render_opts* opts);
 
 /* Bytes of one ResLRB record (constant per path). */
 size_t lt_record_size(const lt_render_opts* opts);

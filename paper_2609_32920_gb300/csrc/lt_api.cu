@@ -527,6 +527,11 @@ void lt_scene_destroy(lt_scene* s) { free_scene(s); }
 
 size_t lt_record_size(const lt_render_opts*) { return 32; }
 
+size_t lt_lrb3_state_bytes(const lt_render_opts* o) {
+  if (!o || o->n_paths < 0) return 0;
+  return lrb3_state_bytes(o->n_paths);
+}
+
 size_t lt_naive_workspace_bytes(const lt_render_opts* o) {
   if (!o || o->n_paths < 0 || o->max_depth < 1) return 0;
   size_t head = ((size_t)o->n_paths * sizeof(int) + 255) & ~(size_t)255;
@@ -557,6 +562,8 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   lt_status v = check_opts(s, p, o);
   if (v != LT_OK) return v;
   if (!dI) return fail(LT_ERR_INVALID_ARG, "d_image is NULL");
+  if (o->lrb3_state && o->lrb3_state_bytes < lt_lrb3_state_bytes(o))
+    return fail(LT_ERR_INVALID_ARG, "lrb3_state smaller than lt_lrb3_state_bytes()");
   cudaStream_t st = (cudaStream_t)stream;
   GradPtrs gp;
   v = prep_grads(s, g, st, gp);
@@ -564,7 +571,7 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
   set_privatization(s, g, kp);
-  cudaError_t e = launch_lrb3(s->dev, kp, o->attached != 0, s->has_dielectric, dI, gp, cfg_for(s, o), st);
+  cudaError_t e = launch_lrb3(s->dev, kp, o->attached != 0, s->has_dielectric, dI, gp, o->lrb3_state, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
   return LT_OK;
 }

@@ -865,9 +865,13 @@ __global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
 // found in pass 2 are kept in a register mask so pass 3 traces no visibility rays.
 // BATCH: per-lane item (BatchDispenser), global gradient atomics, per-item attached flag;
 // S0, kp0, dI0 and g0 are not used.
-template <bool ATT, bool ST, bool CH, bool BATCH>
+// MODE 0: passes 2 and 3 fused per lane.  MODE 1: pass 2 only, storing delta_total and the
+// validity mask of path p in xrec[p] (rgb, bits 0-31) and xhi[p] (bits 32-63).  MODE 2:
+// pass 3 only, starting from that state (paths without a valid connection are skipped).
+template <bool ATT, bool ST, bool CH, bool BATCH, int MODE = 0>
 __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0, const float* __restrict__ dI0,
-                                          const GradPtrs& g0, const BatchArgs& ba) {
+                                          const GradPtrs& g0, const BatchArgs& ba, float4* xrec = nullptr,
+                                          uint32_t* xhi = nullptr) {
   extern __shared__ float sgrad[];
   GradPtrs gs = g0;
   if (!BATCH) {
@@ -911,6 +915,21 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     if (want) {
       if (got < 0) {
         more = false;
+      } else if (MODE == 2) {
+        const float4 a = xrec[got];
+        const uint64_t vm = (uint64_t)__float_as_uint(a.w) | ((uint64_t)xhi[got] << 32);
+        if (vm && (!kp.mask || kp.mask[got])) {
+          p = got;
+          float3 x0;
+          walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
+          rem = f3(a.x, a.y, a.z);
+          valid = vm;
+          pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+          chain.ka = -1;
+          last = 63 - __clzll((long long)valid);
+          k = 0;
+          phase = PASS3;
+        }
       } else if (!kp.mask || kp.mask[got]) {
         p = got;
         if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
@@ -943,11 +962,15 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     if (vis && occluded<ST>(S, v.x, c.wc, c.dist, v.prim, &cs)) c.valid = false;
     if (phase == IDLE) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
-    if (phase == PASS2) {
+    if (MODE != 2 && phase == PASS2) {
       if (!alive) {
         if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4(dtot.x, dtot.y, dtot.z, (float)nconn);
         gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);  // emitted factor, weight delta_total
-        if (valid) {
+        if (MODE == 1) {
+          xrec[p] = make_float4(dtot.x, dtot.y, dtot.z, __uint_as_float((uint32_t)valid));
+          xhi[p] = (uint32_t)(valid >> 32);
+          phase = IDLE;
+        } else if (valid) {
           float3 x0;
           walk_start(S, kp.seed, n, Le, w, x0);
           rem = dtot;
@@ -977,7 +1000,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       }
       walk_scatter(S, w, v, ns, rho, r);
       ++k;
-    } else {
+    } else if (MODE != 1) {
       if (!alive) {
         if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights);
         phase = IDLE;
@@ -1028,6 +1051,20 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
 template <bool ATT, bool ST, bool CH>
 __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0) {
   lrb3_body<ATT, ST, CH, false>(S, kp, dI, g0, BatchArgs{});
+}
+
+// Two-kernel form: pass 2 (per-path state out, emitted-radiance gradient) ...
+template <bool ST>
+__global__ void __launch_bounds__(128) k_lrb3_p2(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
+                                                 float4* xrec, uint32_t* xhi) {
+  lrb3_body<false, ST, false, false, 1>(S, kp, dI, g0, BatchArgs{}, xrec, xhi);
+}
+// ... then pass 3 (albedo and height gradients) from that state.
+template <bool ATT, bool ST, bool CH>
+__global__ void __launch_bounds__(128) k_lrb3_p3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
+                                                 const float4* xrec, const uint32_t* xhi) {
+  lrb3_body<ATT, ST, CH, false, 2>(S, kp, dI, g0, BatchArgs{}, const_cast<float4*>(xrec),
+                                   const_cast<uint32_t*>(xhi));
 }
 
 template <bool ATT, bool CH>
@@ -1279,9 +1316,29 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
 }
 
 cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
-                        const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
+                        const GradPtrs& g, void* state, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
   const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
+  if (state) {
+    float4* xrec = (float4*)state;
+    uint32_t* xhi = (uint32_t*)((char*)state + lrb3_state_split(kp.n_paths));
+    KParams k2 = kp;
+    k2.priv_n = 0;  // pass 2 writes no albedo or height gradients
+    GradPtrs g3 = g;
+    g3.d_Le = nullptr;  // pass 3 writes no emitted-radiance gradient
+    if (kp.census) k_lrb3_p2<true><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+    else k_lrb3_p2<false><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+    if (kp.census) {
+      if (att && chains) k_lrb3_p3<true, true, true><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+      else if (att) k_lrb3_p3<true, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+      else k_lrb3_p3<false, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+    } else {
+      if (att && chains) k_lrb3_p3<true, false, true><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+      else if (att) k_lrb3_p3<true, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+      else k_lrb3_p3<false, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+    }
+    return cudaGetLastError();
+  }
   if (kp.census) {
     if (att && chains) k_lrb3<true, true, true><<<grid, L.block, smem, st>>>(S, kp, dI, g);
     else if (att) k_lrb3<true, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);

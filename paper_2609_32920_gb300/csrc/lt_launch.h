@@ -53,8 +53,12 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
 cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux,
                           const LaunchCfg& L, cudaStream_t st);
 // `chains`: the scene has dielectrics, so attached passes need the specular-chain variant.
+// `state` (or null: fused kernel): per-path state of the two-kernel form, layout
+// float4[n_paths] then, at byte lrb3_state_split(n_paths), uint32[n_paths].
 cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
-                        const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+                        const GradPtrs& g, void* state, const LaunchCfg& L, cudaStream_t st);
+inline size_t lrb3_state_split(int64_t n) { return ((size_t)n * 16 + 255) & ~(size_t)255; }
+inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_split(n) + (((size_t)n * 4 + 255) & ~(size_t)255); }
 cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                           const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
 cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,

@@ -52,7 +52,8 @@ class lt_render_opts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("path_offset", C.c_int64), ("n_paths", C.c_int64), ("n_norm", C.c_int64),
                 ("max_depth", C.c_int), ("attached", C.c_int), ("target", C.c_int), ("mlp", C.c_void_p),
                 ("block_size", C.c_int), ("blocks_per_sm", C.c_int), ("path_mask", C.c_void_p),
-                ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p), ("census", C.c_void_p)]
+                ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p), ("census", C.c_void_p),
+                ("lrb3_state", C.c_void_p), ("lrb3_state_bytes", C.c_size_t)]
 
 
 class lt_grads(C.Structure):
@@ -78,7 +79,7 @@ EXPORTS = ["lt_scene_create", "lt_scene_refit", "lt_scene_destroy", "lt_primal",
            "lt_backward_reslrb", "lt_backward_naive", "lt_film_l2", "lt_record_size", "lt_naive_workspace_bytes",
            "lt_sync_status", "lt_last_error", "lt_version", "lt_mlp_collect", "lt_mlp_init_stats", "lt_mlp_grad",
            "lt_mlp_adam", "lt_mlp_forward", "lt_naive_gradient_static", "lt_batch_create", "lt_batch_run",
-           "lt_batch_set_config", "lt_batch_get_config", "lt_batch_tune", "lt_batch_destroy"]
+           "lt_batch_set_config", "lt_batch_get_config", "lt_batch_tune", "lt_batch_destroy", "lt_lrb3_state_bytes"]
 MLP_PARAMS, MLP_WEIGHTS = 5352, 5313
 
 
@@ -104,6 +105,8 @@ def lib():
             L.lt_record_size.restype = C.c_size_t
             L.lt_naive_workspace_bytes.argtypes = [P(lt_render_opts)]
             L.lt_naive_workspace_bytes.restype = C.c_size_t
+            L.lt_lrb3_state_bytes.argtypes = [P(lt_render_opts)]
+            L.lt_lrb3_state_bytes.restype = C.c_size_t
             L.lt_sync_status.argtypes = [V, V]
             L.lt_last_error.restype = C.c_char_p
             L.lt_version.restype = C.c_char_p
@@ -213,7 +216,9 @@ class Scene:
     @staticmethod
     def opts(seed=0, n_paths=1 << 14, max_depth=4, attached=0, path_offset=0, n_norm=0, block_size=0,
              blocks_per_sm=0, mask=None, hash_out=None, dbg_out=None, target=TARGET_LUMINANCE, mlp=None,
-             census=None):
+             census=None, lrb3_state=None):
+        """Render options.  `lrb3_state`: a device buffer of lrb3_state_bytes(opts) bytes
+        selects the two-kernel form of lt_backward_lrb3 (see include/lt.h)."""
         o = lt_render_opts()
         o.seed, o.path_offset, o.n_paths, o.n_norm = int(seed), int(path_offset), int(n_paths), int(n_norm)
         o.max_depth, o.attached, o.target = int(max_depth), int(attached), int(target)
@@ -223,9 +228,20 @@ class Scene:
         o.path_hash = None if hash_out is None else hash_out.data_ptr()
         o.path_dbg = None if dbg_out is None else dbg_out.data_ptr()
         o.census = None if census is None else census.data_ptr()
+        o.lrb3_state = None if lrb3_state is None else lrb3_state.data_ptr()
+        o.lrb3_state_bytes = 0 if lrb3_state is None else lrb3_state.numel() * lrb3_state.element_size()
         # the struct holds raw device pointers: keep the tensors alive as long as it lives
-        o._keep = (mask, hash_out, dbg_out, census, mlp)
+        o._keep = (mask, hash_out, dbg_out, census, mlp, lrb3_state)
         return o
+
+    @staticmethod
+    def lrb3_state_bytes(n_paths) -> int:
+        o = lt_render_opts()
+        o.n_paths = int(n_paths)
+        return int(lib().lt_lrb3_state_bytes(C.byref(o)))
+
+    def new_lrb3_state(self, n_paths):
+        return torch.empty(self.lrb3_state_bytes(n_paths), dtype=torch.uint8, device=self.device)
 
     def record_size(self, o) -> int:
         return int(lib().lt_record_size(C.byref(o)))

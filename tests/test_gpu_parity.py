@@ -55,15 +55,17 @@ def test_primal_connection_counts_exact(box64):
     assert np.array_equal(dbg.cpu().numpy()[mask, 0], ref["dbg"][mask, 3])
 
 
-@pytest.mark.parametrize("seed,D", [(0, 4), (1, 12)])
-def test_lrb3_detached_matches_naive_ad(box64, seed, D):
+@pytest.mark.parametrize("seed,D,split", [(0, 4, False), (1, 12, False), (1, 12, True)])
+def test_lrb3_detached_matches_naive_ad(box64, seed, D, split):
+    """split: passes 2 and 3 as two kernels with the per-path state in global memory."""
     sc, S = box64
     n = 1 << 14
     dI_np = I.smooth_adjoint(sc.W, sc.H, 10 + seed)
     mask = agree_mask(S, sc, seed, n, D)
     dbg = torch.zeros((n, 4), device="cuda")
-    gA, gL, _ = S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask), dbg_out=dbg),
-                                t32(dI_np))
+    state = S.new_lrb3_state(n) if split else None
+    gA, gL, _ = S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask), dbg_out=dbg,
+                                       lrb3_state=state), t32(dI_np))
     ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, mask=mask, want_dbg=True)
     assert rel_l2(gA.cpu().numpy(), ref["d_albedo"]) < 1e-3
     assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
@@ -114,15 +116,16 @@ def test_naive_detached_matches_oracle(box64):
     assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
 
 
-@pytest.mark.parametrize("method", ["lrb3", "reslrb", "naive"])
+@pytest.mark.parametrize("method", ["lrb3", "lrb3_split", "reslrb", "naive"])
 def test_attached_height_field_matches_oracle(boxhm, method):
     sc, S = boxhm
     n, D, seed = 1 << 14, 6, 6
     dI_np = I.smooth_adjoint(sc.W, sc.H, 41)
     mask = agree_mask(S, sc, seed, n, D)
-    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask))
+    state = S.new_lrb3_state(n) if method == "lrb3_split" else None
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask), lrb3_state=state)
     dI = t32(dI_np)
-    if method == "lrb3":
+    if method.startswith("lrb3"):
         gA, gL, gH = S.backward_lrb3(o, dI)
         ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
     elif method == "reslrb":
@@ -190,6 +193,10 @@ def test_invalid_arguments_raise(box64):
     with pytest.raises(lt.LTError) as e:
         S.primal(o, estimator=lt.EST_RESLRB, aux=None)
     assert e.value.status == lt.LT_ERR_INVALID_ARG
+    short = torch.empty(S.lrb3_state_bytes(1024) - 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lt.LTError) as e:
+        S.backward_lrb3(S.opts(n_paths=1024, max_depth=8, lrb3_state=short), torch.zeros((sc.H, sc.W, 3), device="cuda"))
+    assert e.value.status == lt.LT_ERR_INVALID_ARG
     S.sync_status()
 
 
@@ -210,7 +217,8 @@ def slab():
     return sc, lt.Scene(sc)
 
 
-@pytest.mark.parametrize("method,D", [("lrb3", 4), ("lrb3", 8), ("reslrb", 8), ("naive", 8), ("lrb3", 12)])
+@pytest.mark.parametrize("method,D", [("lrb3", 4), ("lrb3", 8), ("reslrb", 8), ("naive", 8), ("lrb3", 12),
+                                      ("lrb3_split", 12)])
 def test_attached_caustic_slab_matches_oracle(slab, method, D):
     """Dielectric height field: attached gradients through specular chains (first- and
     later-generation chains, anchors that are themselves chain ends)."""
@@ -218,9 +226,10 @@ def test_attached_caustic_slab_matches_oracle(slab, method, D):
     n, seed = 1 << 13, 11
     dI_np = I.smooth_adjoint(sc.W, sc.H, 61)
     mask = agree_mask(S, sc, seed, n, D, max_divergent=2e-3)
-    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask))
+    state = S.new_lrb3_state(n) if method == "lrb3_split" else None
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask), lrb3_state=state)
     dI = t32(dI_np)
-    if method == "lrb3":
+    if method.startswith("lrb3"):
         gA, gL, gH = S.backward_lrb3(o, dI)
         ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
     elif method == "reslrb":
