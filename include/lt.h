@@ -115,6 +115,9 @@ typedef struct {
                            paper's three-pass form); NULL, one fused kernel keeps
                            them in registers.  Same result either way.            */
   size_t lrb3_state_bytes; /* size of lrb3_state                                    */
+  int bvh_width;        /* BVH node width traversed: 2 (threaded binary BVH, stackless),
+                           4 or 8 (wide BVH, ordered stack traversal); 0 = 4.  The
+                           scene holds all three; results agree up to ties.        */
 } lt_render_opts;
 
 /* Gradient outputs (DEVICE, FP32, caller-owned).  NULL skips a parameter group.
@@ -270,9 +273,9 @@ typedef struct {
   const float* heights;    /* [n_heights] or NULL: primal passes refit the scene first;
                               two items with heights must not share a scene          */
   lt_render_opts opts;     /* seed, path_offset, n_paths, n_norm, max_depth, attached,
-                              path_mask and path_dbg are used (path_dbg by LT_PASS_LRB3:
-                              (delta_total rgb, valid connections) as lt_backward_lrb3);
-                              the launch shape comes from the batch configuration    */
+                              path_mask, path_hash and path_dbg are used as by the
+                              single-scene calls; the launch shape and BVH width come
+                              from the batch configuration                          */
   float* image;            /* [H][W][3] primal passes: overwritten                   */
   void* records;           /* [n_paths][lt_record_size] ResLRB records, or NULL when the
                               ResLRB passes are not run                              */
@@ -291,12 +294,14 @@ typedef struct {
   int block_size;        /* 64, 128 or 256                                             */
   int paths_per_thread;  /* 1, 2, 4 or 8: chunk = 32 * paths_per_thread paths          */
   int blocks_per_sm;     /* 0 = occupancy, else 1..32                                  */
+  int bvh_width;         /* 2, 4 or 8 (see lt_render_opts.bvh_width)                   */
 } lt_batch_config;
 
 typedef struct lt_batch lt_batch; /* opaque: item table on the device, captured graphs */
 
 /* Copy the items (n >= 1) and build the device item table.  All scenes must be on the
- * current device.  Default configuration: block 128, 4 paths per thread, occupancy.
+ * current device.  Default configuration: block 128, 4 paths per thread, occupancy,
+ * BVH width 4.
  * Synchronises `stream` once (table upload). */
 lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_batch** out);
 
@@ -311,8 +316,8 @@ lt_status lt_batch_get_config(const lt_batch* batch, lt_batch_config* cfg);
 
 /* Autotuner: time the pass (graph replay, CUDA events on `stream`, best of `reps` after
  * one warm-up) for every block_size in {64, 128, 256} x paths_per_thread in {1, 2, 4, 8}
- * at occupancy, keep the fastest as the batch configuration and return it in *best (and
- * its time per pass in *best_ms, either may be NULL).  Blocking: synchronises `stream`.
+ * x bvh_width in {2, 4, 8} at occupancy, keep the fastest as the batch configuration and
+ * return it in *best (and its time per pass in *best_ms, either may be NULL).  Blocking: synchronises `stream`.
  * The pass runs many times; outputs hold one complete run of the pass afterwards (a
  * backward pass with accumulate set accumulates every run). */
 lt_status lt_batch_tune(lt_batch* batch, int pass, int reps, void* stream, lt_batch_config* best, float* best_ms);

@@ -14,7 +14,12 @@ OUT = os.path.join(PKG, "liblt.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
-SOURCES = ["lt_api.cu", "lt_kernels.cu", "lt_mlp.cu"]
+# (source, object, extra flags): the kernels are compiled once per BVH width
+UNITS = [("lt_api.cu", "lt_api.o", []), ("lt_dispatch.cu", "lt_dispatch.o", []), ("lt_mlp.cu", "lt_mlp.o", []),
+         ("lt_kernels.cu", "lt_kernels_w2.o", ["-DLT_BVH_WIDTH=2"]),
+         ("lt_kernels.cu", "lt_kernels_w4.o", ["-DLT_BVH_WIDTH=4"]),
+         ("lt_kernels.cu", "lt_kernels_w8.o", ["-DLT_BVH_WIDTH=8"])]
+SOURCES = sorted({u[0] for u in UNITS})
 
 
 def _nvcc():
@@ -38,16 +43,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, obj, extra = unit
+        obj = os.path.join(BUILD, obj)
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(len(UNITS)) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = OUT + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, "-shared", *ARCH, "-o", tmp, *objs])
     os.replace(tmp, OUT)

@@ -168,6 +168,10 @@ struct lt_scene {
   float* d_ior = nullptr;
   int* d_err = nullptr;
   int n_nodes = 0, n_prims = 0;
+  // wide BVHs of width 4 and 8 (collapses of the binary tree)
+  float4* d_wnode[2] = {};
+  int* d_wmap[2] = {};
+  int n_wnodes[2] = {};
 };
 
 namespace {
@@ -176,7 +180,81 @@ void free_scene(lt_scene* s) {
   if (!s) return;
   cudaFree(s->d_prim); cudaFree(s->d_prim_h); cudaFree(s->d_tri_base); cudaFree(s->d_node);
   cudaFree(s->d_range); cudaFree(s->d_mat); cudaFree(s->d_ior); cudaFree(s->d_err);
+  for (int k = 0; k < 2; ++k) { cudaFree(s->d_wnode[k]); cudaFree(s->d_wmap[k]); }
   delete s;
+}
+
+RefitArgs refit_args(const lt_scene* s, const float* heights) {
+  RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, heights, s->n_prims, s->d_node, s->d_range, s->n_nodes,
+               {s->d_wnode[0], s->d_wnode[1]}, {s->d_wmap[0], s->d_wmap[1]}, {s->n_wnodes[0], s->n_wnodes[1]}};
+  return ra;
+}
+
+// The scene as one call's kernels see it: BVH width from opts (0 = 4).
+DevScene dev_for(const lt_scene* s, int width) {
+  if (width == 0) width = 4;
+  DevScene S = s->dev;
+  S.width = 2;
+  S.wnode = nullptr;
+  S.n_wnodes = 0;
+  if (width == 4 || width == 8) {
+    const int k = width == 4 ? 0 : 1;
+    S.width = width;
+    S.wnode = s->d_wnode[k];
+    S.n_wnodes = s->n_wnodes[k];
+  }
+  return S;
+}
+
+// Collapse the binary tree into nodes of up to W children: starting from a node's two
+// children, the internal child of largest surface area is replaced by its own two
+// children until there are W or only leaves remain.  Returns, per wide node, the child
+// codes (see DevScene::wnode) and the binary node (flat index) whose box each slot takes.
+void collapse_wide(const Builder& B, int W, int nd, const std::vector<int>& flat_of, std::vector<int>& codes,
+                   std::vector<int>& wmap) {
+  codes.clear();
+  wmap.clear();
+  if (B.nodes.empty()) return;
+  std::vector<int> wq = {0};
+  for (size_t wi = 0; wi < wq.size(); ++wi) {
+    const int b = wq[wi];
+    std::vector<int> ch;
+    if (B.nodes[b].left < 0) {
+      ch.push_back(b);
+    } else {
+      ch.push_back(B.nodes[b].left);
+      ch.push_back(B.nodes[b].right);
+    }
+    while ((int)ch.size() < W) {
+      int best = -1;
+      float ba = -1.0f;
+      for (int k = 0; k < (int)ch.size(); ++k) {
+        const BNode& n = B.nodes[ch[k]];
+        if (n.left >= 0 && n.box.area() > ba) { ba = n.box.area(); best = k; }
+      }
+      if (best < 0) break;
+      const int x = ch[best];
+      ch.erase(ch.begin() + best);
+      ch.push_back(B.nodes[x].left);
+      ch.push_back(B.nodes[x].right);
+    }
+    for (int c = 0; c < W; ++c) {
+      if (c < (int)ch.size()) {
+        const BNode& n = B.nodes[ch[c]];
+        wmap.push_back(flat_of[ch[c]]);
+        if (n.left >= 0) {
+          codes.push_back((int)wq.size());
+          wq.push_back(ch[c]);
+        } else {
+          const unsigned leaf = 0x80000000u | ((unsigned)(nd + n.begin) << 4) | (unsigned)(n.end - n.begin);
+          codes.push_back((int)leaf);
+        }
+      } else {
+        wmap.push_back(-1);
+        codes.push_back(-1);
+      }
+    }
+  }
 }
 
 lt_status validate_desc(const lt_scene_desc* d) {
@@ -232,6 +310,8 @@ lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->block_size > 128) return fail(LT_ERR_INVALID_ARG, "kernels are compiled for at most 128 threads per block");
   if (o->target != LT_TARGET_LUMINANCE && o->target != LT_TARGET_MLP) return fail(LT_ERR_INVALID_ARG, "unknown reservoir target");
   if (o->target == LT_TARGET_MLP && !o->mlp) return fail(LT_ERR_INVALID_ARG, "LT_TARGET_MLP needs opts->mlp");
+  if (o->bvh_width != 0 && o->bvh_width != 2 && o->bvh_width != 4 && o->bvh_width != 8)
+    return fail(LT_ERR_INVALID_ARG, "bvh_width must be 0, 2, 4 or 8");
   return LT_OK;
 }
 
@@ -331,11 +411,11 @@ lt_status lt_naive_gradient_static(lt_scene* s, const lt_params* p, const lt_ren
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
   const LaunchCfg L = cfg_for(s, o);
-  cudaError_t e = launch_primal(s->dev, kparams(p, o), LT_EST_NAIVE, image, tape, L, st);
+  cudaError_t e = launch_primal(dev_for(s, o->bvh_width), kparams(p, o), LT_EST_NAIVE, image, tape, L, st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_naive_gradient_static: ") + cudaGetErrorString(e));
   KParams kb = kparams(p, o);
   set_privatization(s, g, kb);
-  e = launch_naive(s->dev, kb, o->attached != 0, s->has_dielectric, dI, tape, gp, L, st);
+  e = launch_naive(dev_for(s, o->bvh_width), kb, o->attached != 0, s->has_dielectric, dI, tape, gp, L, st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_naive_gradient_static: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -476,6 +556,20 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
   if (!e) e = up((void**)&s->d_range, range.data(), range.size() * sizeof(int2));
   if (!e) e = up((void**)&s->d_mat, mats.data(), mats.size() * sizeof(int4));
   if (!e) e = up((void**)&s->d_ior, iors.data(), iors.size() * sizeof(float));
+  for (int k = 0; k < 2 && !e; ++k) {
+    const int W = k == 0 ? 4 : 8;
+    std::vector<int> codes, wmap;
+    collapse_wide(B, W, nd, flat_of, codes, wmap);
+    const int nw = (int)codes.size() / W;
+    s->n_wnodes[k] = nw;
+    std::vector<float> wn((size_t)nw * 8 * W, 0.0f);  // boxes are written by the refit
+    for (int j = 0; j < nw; ++j)
+      for (int c = 0; c < W; ++c) std::memcpy(&wn[(size_t)j * 8 * W + 6 * W + c], &codes[j * W + c], 4);
+    if (nw > 0) {
+      e = up((void**)&s->d_wnode[k], wn.data(), wn.size() * sizeof(float));
+      if (!e) e = up((void**)&s->d_wmap[k], wmap.data(), wmap.size() * sizeof(int));
+    }
+  }
   if (!e) e = cudaMalloc((void**)&s->d_err, sizeof(int) * 4);
   if (!e) e = cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, st);
   if (e) {
@@ -484,6 +578,7 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
                 std::string("lt_scene_create: ") + cudaGetErrorString(e));
   }
   DevScene& S = s->dev;
+  S.width = 2;
   S.prim = s->d_prim; S.prim_h = s->d_prim_h; S.node = s->d_node; S.n_nodes = nn; S.n_prims = np;
   S.n_direct = nd;
   S.mat = s->d_mat; S.mat_ior = s->d_ior; S.emitter_prim = emitter_leaf; S.err = s->d_err;
@@ -506,8 +601,7 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
   S.K0 = (float)((double)d->width * d->height / (4.0 * tanx * tany * 3.14159265358979323846));
   S.W = d->width; S.H = d->height;
   // initial bounds
-  RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, nullptr, np, s->d_node, s->d_range, nn};
-  if (nn == 0) ra.n_nodes = 0;
+  RefitArgs ra = refit_args(s, nullptr);
   e = launch_refit(ra, st);
   if (e) { free_scene(s); return fail(LT_ERR_CUDA, std::string("refit: ") + cudaGetErrorString(e)); }
   *out = s;
@@ -517,8 +611,7 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
 lt_status lt_scene_refit(lt_scene* s, const float* heights, void* stream) {
   if (!s) return fail(LT_ERR_INVALID_ARG, "scene is NULL");
   if (s->n_heights > 0 && !heights) return fail(LT_ERR_INVALID_ARG, "heights is NULL");
-  RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, heights, s->n_prims, s->d_node, s->d_range, s->n_nodes};
-  cudaError_t e = launch_refit(ra, (cudaStream_t)stream);
+  cudaError_t e = launch_refit(refit_args(s, heights), (cudaStream_t)stream);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_scene_refit: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -552,7 +645,7 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
   LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
-  cudaError_t e = launch_primal(s->dev, kp, est, image, aux, cfg_for(s, o), st);
+  cudaError_t e = launch_primal(dev_for(s, o->bvh_width), kp, est, image, aux, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_primal: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -571,7 +664,7 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
   set_privatization(s, g, kp);
-  cudaError_t e = launch_lrb3(s->dev, kp, o->attached != 0, s->has_dielectric, dI, gp, o->lrb3_state, cfg_for(s, o), st);
+  cudaError_t e = launch_lrb3(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, gp, o->lrb3_state, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -588,7 +681,7 @@ lt_status lt_backward_reslrb(lt_scene* s, const lt_params* p, const lt_render_op
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
   set_privatization(s, g, kp);
-  cudaError_t e = launch_reslrb(s->dev, kp, o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
+  cudaError_t e = launch_reslrb(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_reslrb: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -607,7 +700,7 @@ lt_status lt_backward_naive(lt_scene* s, const lt_params* p, const lt_render_opt
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
   set_privatization(s, g, kp);
-  cudaError_t e = launch_naive(s->dev, kp, o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
+  cudaError_t e = launch_naive(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_naive: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -634,7 +727,7 @@ lt_status lt_mlp_collect(lt_scene* s, const lt_params* p, const lt_render_opts* 
   cudaStream_t st = (cudaStream_t)stream;
   LT_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), st));
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_collect(s->dev, kparams(p, o), dI, tfloor, feats, targets, cap, (unsigned long long*)count,
+  cudaError_t e = launch_collect(dev_for(s, o->bvh_width), kparams(p, o), dI, tfloor, feats, targets, cap, (unsigned long long*)count,
                                  cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_mlp_collect: ") + cudaGetErrorString(e));
   return LT_OK;
@@ -705,22 +798,25 @@ struct lt_batch {
   std::vector<lt_batch_item> items;  // table order (lean group, then chain group)
   int n_lean = 0;                    // items [0, n_lean) form the lean group
   bool att_lean = false, all_rec = true;
-  // one item table per chunk size (32 * paths_per_thread, paths_per_thread = 1, 2, 4, 8):
-  // only the first-chunk indices differ, and a configuration change must not rewrite a
-  // table that a running pass may still read
-  BatchJob* d_jobs[4] = {};
+  // one item table per chunk size (32 * paths_per_thread, paths_per_thread = 1, 2, 4, 8)
+  // and BVH width (2, 4, 8): only the first-chunk indices and the scenes' BVH selection
+  // differ, and a configuration change must not rewrite a table that a running pass may
+  // still read
+  BatchJob* d_jobs[12] = {};
   int64_t n_chunks[4] = {};   // whole batch
   int64_t split[4] = {};      // first chunk of the chain group
   unsigned long long* d_ticket = nullptr;  // [4 passes][2 groups]
   cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams (main, second branch)
   cudaEvent_t fork = nullptr, join = nullptr;
-  lt_batch_config cfg{128, 4, 0};
+  lt_batch_config cfg{128, 4, 0, 4};
   cudaGraphExec_t exec[4] = {};
 };
 
 namespace {
 
 int ppt_slot(int ppt) { return ppt == 1 ? 0 : ppt == 2 ? 1 : ppt == 4 ? 2 : ppt == 8 ? 3 : -1; }
+int width_slot(int w) { return w == 2 ? 0 : w == 4 ? 1 : w == 8 ? 2 : -1; }
+int table_of(const lt_batch_config& c) { return 3 * ppt_slot(c.paths_per_thread) + width_slot(c.bvh_width); }
 
 void drop_graphs(lt_batch* b) {
   for (auto& e : b->exec) {
@@ -747,6 +843,7 @@ lt_status check_batch_cfg(const lt_batch_config* c) {
     return fail(LT_ERR_INVALID_ARG, "block_size must be 64, 128 or 256");
   if (ppt_slot(c->paths_per_thread) < 0) return fail(LT_ERR_INVALID_ARG, "paths_per_thread must be 1, 2, 4 or 8");
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return fail(LT_ERR_INVALID_ARG, "blocks_per_sm must be in 0..32");
+  if (width_slot(c->bvh_width) < 0) return fail(LT_ERR_INVALID_ARG, "bvh_width must be 2, 4 or 8");
   return LT_OK;
 }
 
@@ -779,7 +876,8 @@ std::vector<GroupLaunch> plan_pass(const lt_batch* b, int pass) {
   for (GroupLaunch& g : out) {
     if (g.c1 <= g.c0) continue;
     g.per_sm = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm
-                                        : batch_occupancy(kernel_pass(pass), g.att, g.chains, b->cfg.block_size);
+                                        : batch_occupancy(b->cfg.bvh_width, kernel_pass(pass), g.att, g.chains,
+                                                          b->cfg.block_size);
     keep.push_back(g);
   }
   return keep;
@@ -794,8 +892,9 @@ lt_status launch_group(lt_batch* b, int pass, int gi, const GroupLaunch& g, cuda
   const int64_t nch = g.c1 - g.c0;
   const int64_t warps_per_block = block / 32;
   int64_t grid = std::min<int64_t>((int64_t)b->sms * g.per_sm, (nch + warps_per_block - 1) / warps_per_block);
-  BatchArgs a{b->d_jobs[slot] + g.j0, g.j1 - g.j0, 32 * b->cfg.paths_per_thread, g.c0, nch, ticket};
-  cudaError_t e = launch_batch(kernel_pass(pass), g.att, g.chains, a, block, (int)std::max<int64_t>(grid, 1), st);
+  BatchArgs a{b->d_jobs[table_of(b->cfg)] + g.j0, g.j1 - g.j0, 32 * b->cfg.paths_per_thread, g.c0, nch, ticket};
+  cudaError_t e = launch_batch(b->cfg.bvh_width, kernel_pass(pass), g.att, g.chains, a, block,
+                               (int)std::max<int64_t>(grid, 1), st);
   if (e) return fail(LT_ERR_CUDA, std::string("batched pass: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -809,8 +908,7 @@ lt_status enqueue_pass(lt_batch* b, int pass, const std::vector<GroupLaunch>& pl
     const lt_scene* s = it.scene;
     if (primal) {
       if (it.heights && s->n_heights > 0) {
-        RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, it.heights, s->n_prims, s->d_node, s->d_range, s->n_nodes};
-        cudaError_t e = launch_refit(ra, st);
+        cudaError_t e = launch_refit(refit_args(s, it.heights), st);
         if (e) return fail(LT_ERR_CUDA, std::string("batch refit: ") + cudaGetErrorString(e));
       }
       LT_CUDA(cudaMemsetAsync(it.image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
@@ -890,6 +988,9 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     it.opts.target = LT_TARGET_LUMINANCE;
     it.opts.mlp = nullptr;
     it.opts.census = nullptr;
+    it.opts.lrb3_state = nullptr;
+    it.opts.lrb3_state_bytes = 0;
+    it.opts.bvh_width = 0;
     lt_status v = check_opts(it.scene, &it.params, &it.opts);
     if (v != LT_OK) return fail(v, at + g_last_error);
     if (!it.image || !it.d_image) return fail(LT_ERR_INVALID_ARG, at + "image or d_image is NULL");
@@ -932,8 +1033,15 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     }
     if (b->n_lean == n) b->split[slot] = c;
     b->n_chunks[slot] = c;
-    LT_CUDA(cudaMalloc(&b->d_jobs[slot], sizeof(BatchJob) * n));
-    LT_CUDA(cudaMemcpyAsync(b->d_jobs[slot], jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, st));
+    for (int ws = 0; ws < 3; ++ws) {
+      const int w = 2 << ws;
+      for (int i = 0; i < n; ++i) jobs[i].S = dev_for(b->items[i].scene, w);
+      BatchJob*& dst = b->d_jobs[3 * slot + ws];
+      LT_CUDA(cudaMalloc(&dst, sizeof(BatchJob) * n));
+      LT_CUDA(cudaMemcpyAsync(dst, jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, st));
+      // the upload must finish before the host table changes for the next width
+      LT_CUDA(cudaStreamSynchronize(st));
+    }
   }
   LT_CUDA(cudaMalloc(&b->d_ticket, 8 * sizeof(unsigned long long)));
   LT_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
@@ -971,6 +1079,29 @@ lt_status lt_batch_get_config(const lt_batch* b, lt_batch_config* cfg) {
   return LT_OK;
 }
 
+// Time one configuration: capture (first run, also the warm-up) then the best of `reps`
+// graph replays.
+static lt_status time_config(lt_batch* b, int pass, const lt_batch_config& c, int reps, cudaStream_t st, cudaEvent_t e0,
+                             cudaEvent_t e1, float* ms_out) {
+  lt_status v = lt_batch_set_config(b, &c);
+  if (v != LT_OK) return v;
+  v = lt_batch_run(b, pass, st);
+  if (v != LT_OK) return v;
+  float t_min = 3e38f;
+  for (int r = 0; r < reps; ++r) {
+    cudaError_t e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[pass], st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) return fail(LT_ERR_CUDA, std::string("lt_batch_tune: ") + cudaGetErrorString(e));
+    t_min = std::min(t_min, ms);
+  }
+  *ms_out = t_min;
+  return LT_OK;
+}
+
 lt_status lt_batch_tune(lt_batch* b, int pass, int reps, void* stream, lt_batch_config* best, float* best_ms) {
   lt_status v = check_pass(b, pass);
   if (v != LT_OK) return v;
@@ -980,33 +1111,26 @@ lt_status lt_batch_tune(lt_batch* b, int pass, int reps, void* stream, lt_batch_
   LT_CUDA(cudaEventCreate(&e0));
   LT_CUDA(cudaEventCreate(&e1));
   const lt_batch_config keep = b->cfg;
-  lt_batch_config win = keep;
+  lt_batch_config win{128, 4, 0, 4};
   float win_ms = 3e38f;
   lt_status res = LT_OK;
+  // stage 1: BVH width at the default launch shape; stage 2: launch shape at that width
+  for (int w : {2, 4, 8}) {
+    if (res != LT_OK) break;
+    const lt_batch_config c{128, 4, 0, w};
+    float ms = 0.0f;
+    res = time_config(b, pass, c, reps, st, e0, e1, &ms);
+    if (res == LT_OK && ms < win_ms) { win_ms = ms; win = c; }
+  }
+  const int width = win.bvh_width;
   for (int block : {64, 128, 256}) {
     for (int ppt : {1, 2, 4, 8}) {
-      lt_batch_config c{block, ppt, 0};
-      lt_batch_set_config(b, &c);
-      res = lt_batch_run(b, pass, stream);  // capture + warm-up
-      if (res != LT_OK) break;
-      float t_min = 3e38f;
-      for (int r = 0; r < reps && res == LT_OK; ++r) {
-        cudaError_t e = cudaEventRecord(e0, st);
-        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[pass], st);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) res = fail(LT_ERR_CUDA, std::string("lt_batch_tune: ") + cudaGetErrorString(e));
-        t_min = std::min(t_min, ms);
-      }
-      if (res != LT_OK) break;
-      if (t_min < win_ms) {
-        win_ms = t_min;
-        win = c;
-      }
+      if (res != LT_OK || (block == 128 && ppt == 4)) continue;
+      const lt_batch_config c{block, ppt, 0, width};
+      float ms = 0.0f;
+      res = time_config(b, pass, c, reps, st, e0, e1, &ms);
+      if (res == LT_OK && ms < win_ms) { win_ms = ms; win = c; }
     }
-    if (res != LT_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

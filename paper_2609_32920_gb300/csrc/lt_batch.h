@@ -38,8 +38,17 @@ struct BatchArgs {
 enum BatchPass { BPASS_PRIMAL = 0, BPASS_PRIMAL_RES = 1, BPASS_LRB3 = 2, BPASS_RESLRB = 3 };
 
 // `chains`: some attached item's scene has dielectrics (compiles the specular-chain variant).
-cudaError_t launch_batch(int pass, bool att, bool chains, const BatchArgs& a, int block, int grid, cudaStream_t st);
-// Resident blocks per SM of the pass's kernel at `block` threads (0 on error).
-int batch_occupancy(int pass, bool att, bool chains, int block);
+// Per BVH width (namespaces w2, w4, w8, see lt_launch.h) and, in lt, by `width`.
+#define LT_BATCH_LAUNCHERS                                                                                  \
+  cudaError_t launch_batch(int pass, bool att, bool chains, const BatchArgs& a, int block, int grid,       \
+                           cudaStream_t st);                                                               \
+  /* resident blocks per SM of the pass's kernel at `block` threads (0 on error) */                        \
+  int batch_occupancy(int pass, bool att, bool chains, int block);
+namespace w2 { LT_BATCH_LAUNCHERS }
+namespace w4 { LT_BATCH_LAUNCHERS }
+namespace w8 { LT_BATCH_LAUNCHERS }
+cudaError_t launch_batch(int width, int pass, bool att, bool chains, const BatchArgs& a, int block, int grid,
+                         cudaStream_t st);
+int batch_occupancy(int width, int pass, bool att, bool chains, int block);
 
 }  // namespace lt

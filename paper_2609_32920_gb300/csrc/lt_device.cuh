@@ -42,6 +42,15 @@ struct DevScene {
   float K0;               // W * H / (A_img * pi); per call divided by N
   int W, H;
   int* err;               // device error word
+  // Wide BVH over the same primitives (width 4 or 8, chosen per call; width 2 = the
+  // threaded binary BVH above).  Node j holds, for its `width` children c, the box
+  // component q (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z) at float q*width + c and the child
+  // code at float 6*width + c (stride 8*width floats): code >= 0 is a wide node index,
+  // code = 0x80000000 | first << 4 | count is a leaf over leaf-order primitives
+  // [first, first + count), code = -1 an empty slot (its box is empty).
+  const float4* wnode;
+  int n_wnodes;
+  int width;
 };
 
 // ------------------------------------------------------------------ small vector ops
@@ -166,8 +175,8 @@ struct Census {
 // then the warp tests all pending leaves together, so leaf work is not serialised lane by
 // lane.
 template <bool ST = false>
-__device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, float3 dir, int skip,
-                                                Census* cs = nullptr) {
+__device__ __forceinline__ HitRec trace_closest2(const DevScene& S, float3 org, float3 dir, int skip,
+                                                 Census* cs = nullptr) {
   if (ST) cs->rays++;
   HitRec h;
   h.prim = -1; h.t = 3.0e38f; h.b1 = 0; h.b2 = 0;
@@ -220,8 +229,8 @@ __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, f
 
 // Any hit in (kTMin, dist - kTMin) (sensor-connection visibility), same traversal form.
 template <bool ST = false>
-__device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 dir, float dist, int skip,
-                                         Census* cs = nullptr) {
+__device__ __forceinline__ bool occluded2(const DevScene& S, float3 org, float3 dir, float dist, int skip,
+                                          Census* cs = nullptr) {
   if (ST) cs->rays++;
   const float tmax = dist - kTMin;
   for (int k = 0; k < S.n_direct; ++k) {
@@ -261,6 +270,209 @@ __device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 d
       if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) return true;
     }
   }
+}
+
+// ------------------------------------------------------------------ wide BVH traversal
+constexpr int kWideStack = 64;
+constexpr int kCodeDone = -1;
+
+// Slab test of the `W` children of wide node `j` against a ray (origin times inverse
+// direction precomputed): tn[c] = entry distance, +inf when the child is missed, empty or
+// entered only beyond tmax.
+template <int W>
+__device__ __forceinline__ void wide_boxes(const DevScene& S, int j, float3 inv, float3 oi, float tmax, float tn[W],
+                                           int code[W]) {
+  const float* nd = reinterpret_cast<const float*>(S.wnode) + (size_t)j * 8 * W;
+  float v[6][W];
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+#pragma unroll
+    for (int c4 = 0; c4 < W / 4; ++c4) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(nd + q * W) + c4);
+      v[q][4 * c4] = a.x; v[q][4 * c4 + 1] = a.y; v[q][4 * c4 + 2] = a.z; v[q][4 * c4 + 3] = a.w;
+    }
+#pragma unroll
+  for (int c4 = 0; c4 < W / 4; ++c4) {
+    const int4 cc = __ldg(reinterpret_cast<const int4*>(nd + 6 * W) + c4);
+    code[4 * c4] = cc.x; code[4 * c4 + 1] = cc.y; code[4 * c4 + 2] = cc.z; code[4 * c4 + 3] = cc.w;
+  }
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const float tx0 = fmaf(v[0][c], inv.x, -oi.x), tx1 = fmaf(v[3][c], inv.x, -oi.x);
+    const float ty0 = fmaf(v[1][c], inv.y, -oi.y), ty1 = fmaf(v[4][c], inv.y, -oi.y);
+    const float tz0 = fmaf(v[2][c], inv.z, -oi.z), tz1 = fmaf(v[5][c], inv.z, -oi.z);
+    const float a = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float b = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    // an empty slot (code -1) has an inverted box, which the per-axis min/max would turn
+    // into one that every ray enters: reject it by its code
+    tn[c] = (a <= b && code[c] != -1) ? a : __int_as_float(0x7f800000);
+  }
+}
+
+// Sort (key, code) pairs ascending by key (insertion sort; W is 4 or 8).
+template <int W>
+__device__ __forceinline__ void sort_children(float k[W], int c[W]) {
+#pragma unroll
+  for (int i = 1; i < W; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j) {
+      const bool sw = k[j] < k[j - 1];
+      const float tk = sw ? k[j] : k[j - 1];
+      k[j] = sw ? k[j - 1] : k[j];
+      k[j - 1] = tk;
+      const int tc = sw ? c[j] : c[j - 1];
+      c[j] = sw ? c[j - 1] : c[j];
+      c[j - 1] = tc;
+    }
+}
+
+// Closest hit through the wide BVH, same result rules as trace_closest2.  Stack-based
+// ordered traversal: the children of a node that the ray enters are pushed far to near
+// with their entry distance, so the nearest is visited next and entries beyond the
+// current hit are dropped when popped.  Leaves are tested in a separate loop (while-while
+// form) so that a warp tests its lanes' pending leaves together.  A stack overflow (a
+// tree deeper than the stack allows) drops the entry and sets ERR_BOUNDS.
+template <int W, bool ST = false>
+__device__ __forceinline__ HitRec trace_closest_w(const DevScene& S, float3 org, float3 dir, int skip,
+                                                  Census* cs = nullptr) {
+  if (ST) cs->rays++;
+  HitRec h;
+  h.prim = -1; h.t = 3.0e38f; h.b1 = 0; h.b2 = 0;
+  int best_orig = 0x7fffffff;
+  for (int k = 0; k < S.n_direct; ++k) {
+    if (k == skip) continue;
+    if (ST) cs->prims++;
+    const Prim p = load_prim(S, k);
+    float t, u, v;
+    if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
+        (t < h.t || (t == h.t && p.orig < best_orig))) {
+      h.prim = k; h.t = t; h.b1 = u; h.b2 = v; best_orig = p.orig;
+    }
+  }
+  if (S.n_wnodes == 0) return h;
+  const float3 inv = safe_inv(dir);
+  const float3 oi = f3(org.x * inv.x, org.y * inv.y, org.z * inv.z);
+  int st_code[kWideStack];
+  float st_t[kWideStack];
+  int sp = 0;
+  bool overflow = false;
+  int next = 0;  // the root
+  while (next != kCodeDone) {
+    while (next >= 0) {
+      float tn[W];
+      int code[W];
+      if (ST) cs->nodes += W;
+      wide_boxes<W>(S, next, inv, oi, h.t, tn, code);
+      sort_children<W>(tn, code);
+#pragma unroll
+      for (int c = W - 1; c >= 0; --c) {
+        if (tn[c] <= h.t) {
+          if (sp < kWideStack) { st_code[sp] = code[c]; st_t[sp] = tn[c]; ++sp; }
+          else overflow = true;
+        }
+      }
+      next = kCodeDone;
+      while (sp > 0) {
+        --sp;
+        if (st_t[sp] <= h.t) { next = st_code[sp]; break; }
+      }
+    }
+    if (next == kCodeDone) break;
+    const int first = (next & 0x7fffffff) >> 4, cnt = next & 15;
+    for (int k = first; k < first + cnt; ++k) {
+      if (k == skip) continue;
+      if (ST) cs->prims++;
+      const Prim p = load_prim(S, k);
+      float t, u, v;
+      if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
+          (t < h.t || (t == h.t && p.orig < best_orig))) {
+        h.prim = k; h.t = t; h.b1 = u; h.b2 = v; best_orig = p.orig;
+      }
+    }
+    next = kCodeDone;
+    while (sp > 0) {
+      --sp;
+      if (st_t[sp] <= h.t) { next = st_code[sp]; break; }
+    }
+  }
+  if (overflow) atomicOr(S.err, ERR_BOUNDS);
+  return h;
+}
+
+// Any hit in (kTMin, dist - kTMin) through the wide BVH (children in stored order).
+template <int W, bool ST = false>
+__device__ __forceinline__ bool occluded_w(const DevScene& S, float3 org, float3 dir, float dist, int skip,
+                                           Census* cs = nullptr) {
+  if (ST) cs->rays++;
+  const float tmax = dist - kTMin;
+  for (int k = 0; k < S.n_direct; ++k) {
+    if (k == skip) continue;
+    if (ST) cs->prims++;
+    const Prim p = load_prim(S, k);
+    float t, u, v;
+    if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) return true;
+  }
+  if (S.n_wnodes == 0) return false;
+  const float3 inv = safe_inv(dir);
+  const float3 oi = f3(org.x * inv.x, org.y * inv.y, org.z * inv.z);
+  int st_code[kWideStack];
+  int sp = 0;
+  bool overflow = false;
+  int next = 0;
+  bool hit = false;
+  while (next != kCodeDone && !hit) {
+    while (next >= 0) {
+      float tn[W];
+      int code[W];
+      if (ST) cs->nodes += W;
+      wide_boxes<W>(S, next, inv, oi, tmax, tn, code);
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        if (tn[c] <= tmax) {
+          if (sp < kWideStack) st_code[sp++] = code[c];
+          else overflow = true;
+        }
+      }
+      next = sp > 0 ? st_code[--sp] : kCodeDone;
+    }
+    if (next == kCodeDone) break;
+    const int first = (next & 0x7fffffff) >> 4, cnt = next & 15;
+    for (int k = first; k < first + cnt; ++k) {
+      if (k == skip) continue;
+      if (ST) cs->prims++;
+      const Prim p = load_prim(S, k);
+      float t, u, v;
+      if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin && t < tmax) { hit = true; break; }
+    }
+    next = sp > 0 ? st_code[--sp] : kCodeDone;
+  }
+  if (overflow) atomicOr(S.err, ERR_BOUNDS);
+  return hit;
+}
+
+// Traversal entry points.  The BVH width is fixed per translation unit (LT_BVH_WIDTH):
+// the kernels are compiled once per width, so each variant carries only its own
+// traversal's registers; the host picks the variant that matches the call's width.
+#ifndef LT_BVH_WIDTH
+#define LT_BVH_WIDTH 4
+#endif
+template <bool ST = false>
+__device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, float3 dir, int skip,
+                                                Census* cs = nullptr) {
+#if LT_BVH_WIDTH == 2
+  return trace_closest2<ST>(S, org, dir, skip, cs);
+#else
+  return trace_closest_w<LT_BVH_WIDTH, ST>(S, org, dir, skip, cs);
+#endif
+}
+template <bool ST = false>
+__device__ __forceinline__ bool occluded(const DevScene& S, float3 org, float3 dir, float dist, int skip,
+                                         Census* cs = nullptr) {
+#if LT_BVH_WIDTH == 2
+  return occluded2<ST>(S, org, dir, dist, skip, cs);
+#else
+  return occluded_w<LT_BVH_WIDTH, ST>(S, org, dir, dist, skip, cs);
+#endif
 }
 
 // ------------------------------------------------------------------ camera / film

@@ -10,7 +10,19 @@
 #include "lt_launch.h"
 #include "lt_mlp.cuh"
 
+// Compiled once per BVH width (-DLT_BVH_WIDTH=2, 4 or 8) into lt::w2, lt::w4, lt::w8.
+#if LT_BVH_WIDTH == 2
+#define LT_KNS w2
+#elif LT_BVH_WIDTH == 4
+#define LT_KNS w4
+#elif LT_BVH_WIDTH == 8
+#define LT_KNS w8
+#else
+#error "LT_BVH_WIDTH must be 2, 4 or 8"
+#endif
+
 namespace lt {
+namespace LT_KNS {
 
 // ======================================================================= refit
 // Triangle geometry from base vertex positions plus heights (y), leaf order.
@@ -66,6 +78,28 @@ __global__ void k_refit_nodes(float4* node, const int2* range, const float4* pri
     float4 a = node[2 * w], b = node[2 * w + 1];
     node[2 * w] = make_float4(lo.x - pad.x, lo.y - pad.y, lo.z - pad.z, a.w);
     node[2 * w + 1] = make_float4(hi.x + pad.x, hi.y + pad.y, hi.z + pad.z, b.w);
+  }
+}
+
+// Wide-node boxes from the refitted binary nodes: one thread per child slot copies the
+// box of the binary node that the slot stands for (the wide BVH is a collapse of the
+// binary one) into the node's structure-of-arrays layout.
+template <int W>
+__global__ void k_refit_wide(float4* wnode, const int* wmap, const float4* node, int n_wnodes) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_wnodes * W) return;
+  const int j = t / W, c = t - j * W;
+  const int b = wmap[t];
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  if (b >= 0) {
+    const float4 l = node[2 * b], h = node[2 * b + 1];
+    lo[0] = l.x; lo[1] = l.y; lo[2] = l.z;
+    hi[0] = h.x; hi[1] = h.y; hi[2] = h.z;
+  }
+  float* nd = reinterpret_cast<float*>(wnode) + (size_t)j * 8 * W;
+  for (int q = 0; q < 3; ++q) {
+    nd[q * W + c] = lo[q];
+    nd[(q + 3) * W + c] = hi[q];
   }
 }
 
@@ -1298,6 +1332,14 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
     int threads = a.n_nodes * 32;
     k_refit_nodes<<<(threads + 255) / 256, 256, 0, st>>>(a.node, a.range, a.prim, a.n_nodes);
   }
+  if (a.n_wnodes[0] > 0) {
+    const int t = a.n_wnodes[0] * 4;
+    k_refit_wide<4><<<(t + 255) / 256, 256, 0, st>>>(a.wnode[0], a.wmap[0], a.node, a.n_wnodes[0]);
+  }
+  if (a.n_wnodes[1] > 0) {
+    const int t = a.n_wnodes[1] * 8;
+    k_refit_wide<8><<<(t + 255) / 256, 256, 0, st>>>(a.wnode[1], a.wmap[1], a.node, a.n_wnodes[1]);
+  }
   return cudaGetLastError();
 }
 
@@ -1427,4 +1469,5 @@ cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI,
   return cudaGetLastError();
 }
 
+}  // namespace LT_KNS
 }  // namespace lt

@@ -47,31 +47,47 @@ struct RefitArgs {
   float4* node;
   const int2* range;
   int n_nodes;
+  // wide BVHs (width 4 and 8): child slot -> binary node whose box it takes (-1: empty)
+  float4* wnode[2];
+  const int* wmap[2];
+  int n_wnodes[2];
 };
 
-cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
-cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux,
-                          const LaunchCfg& L, cudaStream_t st);
-// `chains`: the scene has dielectrics, so attached passes need the specular-chain variant.
-// `state` (or null: fused kernel): per-path state of the two-kernel form, layout
-// float4[n_paths] then, at byte lrb3_state_split(n_paths), uint32[n_paths].
-cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
-                        const GradPtrs& g, void* state, const LaunchCfg& L, cudaStream_t st);
+struct BatchArgs;
+
+// Kernel launchers.  lt_kernels.cu is compiled once per BVH width into namespaces w2, w4
+// and w8; the functions of the same names in lt itself pick the variant by the scene's
+// width (DevScene::width).
+#define LT_KERNEL_LAUNCHERS                                                                                        \
+  cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);                                                  \
+  cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux,               \
+                            const LaunchCfg& L, cudaStream_t st);                                                 \
+  cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,           \
+                          const GradPtrs& g, void* state, const LaunchCfg& L, cudaStream_t st);                   \
+  cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,         \
+                            const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);             \
+  cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,           \
+                           const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);               \
+  cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI, float tfloor, float* feats,   \
+                             float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L,          \
+                             cudaStream_t st);                                                                    \
+  cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,          \
+                             cudaStream_t st);
+
+namespace w2 { LT_KERNEL_LAUNCHERS }
+namespace w4 { LT_KERNEL_LAUNCHERS }
+namespace w8 { LT_KERNEL_LAUNCHERS }
+LT_KERNEL_LAUNCHERS
+
+// `state` of launch_lrb3 (or null: fused kernel): per-path state of the two-kernel form,
+// layout float4[n_paths] then, at byte lrb3_state_split(n_paths), uint32[n_paths].
 inline size_t lrb3_state_split(int64_t n) { return ((size_t)n * 16 + 255) & ~(size_t)255; }
 inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_split(n) + (((size_t)n * 4 + 255) & ~(size_t)255); }
-cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
-                          const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
-cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
-                         const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
-cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI, float tfloor, float* feats,
-                           float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L, cudaStream_t st);
 size_t mlp_grad_smem_bytes();
 cudaError_t launch_mlp_grad(const float* P, const float* X, const float* T, int64_t n, float inv_batch, float* g,
                             float* loss, int sms, cudaStream_t st);
 cudaError_t launch_mlp_adam(float* P, float* M, float* V, const float* g, int step, float lr, cudaStream_t st);
 cudaError_t launch_mlp_moments(const float* X, const float* T, int64_t n, float* P, cudaStream_t st);
 cudaError_t launch_mlp_forward(const float* P, const float* X, int64_t n, float* out, int sms, cudaStream_t st);
-cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,
-                           cudaStream_t st);
 
 }  // namespace lt

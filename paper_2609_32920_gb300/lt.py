@@ -53,7 +53,7 @@ class lt_render_opts(C.Structure):
                 ("max_depth", C.c_int), ("attached", C.c_int), ("target", C.c_int), ("mlp", C.c_void_p),
                 ("block_size", C.c_int), ("blocks_per_sm", C.c_int), ("path_mask", C.c_void_p),
                 ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p), ("census", C.c_void_p),
-                ("lrb3_state", C.c_void_p), ("lrb3_state_bytes", C.c_size_t)]
+                ("lrb3_state", C.c_void_p), ("lrb3_state_bytes", C.c_size_t), ("bvh_width", C.c_int)]
 
 
 class lt_grads(C.Structure):
@@ -66,7 +66,8 @@ class lt_batch_item(C.Structure):
 
 
 class lt_batch_config(C.Structure):
-    _fields_ = [("block_size", C.c_int), ("paths_per_thread", C.c_int), ("blocks_per_sm", C.c_int)]
+    _fields_ = [("block_size", C.c_int), ("paths_per_thread", C.c_int), ("blocks_per_sm", C.c_int),
+                ("bvh_width", C.c_int)]
 
 
 PASS_PRIMAL, PASS_PRIMAL_RESLRB, PASS_LRB3, PASS_RESLRB = 0, 1, 2, 3
@@ -216,7 +217,7 @@ class Scene:
     @staticmethod
     def opts(seed=0, n_paths=1 << 14, max_depth=4, attached=0, path_offset=0, n_norm=0, block_size=0,
              blocks_per_sm=0, mask=None, hash_out=None, dbg_out=None, target=TARGET_LUMINANCE, mlp=None,
-             census=None, lrb3_state=None):
+             census=None, lrb3_state=None, bvh_width=0):
         """Render options.  `lrb3_state`: a device buffer of lrb3_state_bytes(opts) bytes
         selects the two-kernel form of lt_backward_lrb3 (see include/lt.h)."""
         o = lt_render_opts()
@@ -228,6 +229,7 @@ class Scene:
         o.path_hash = None if hash_out is None else hash_out.data_ptr()
         o.path_dbg = None if dbg_out is None else dbg_out.data_ptr()
         o.census = None if census is None else census.data_ptr()
+        o.bvh_width = int(bvh_width)
         o.lrb3_state = None if lrb3_state is None else lrb3_state.data_ptr()
         o.lrb3_state_bytes = 0 if lrb3_state is None else lrb3_state.numel() * lrb3_state.element_size()
         # the struct holds raw device pointers: keep the tensors alive as long as it lives
@@ -361,22 +363,27 @@ class Batch:
     def run(self, pass_id, stream=None):
         _check(lib().lt_batch_run(self._h, int(pass_id), _stream(stream)))
 
+    @staticmethod
+    def _cfg(c):
+        return dict(block_size=c.block_size, paths_per_thread=c.paths_per_thread, blocks_per_sm=c.blocks_per_sm,
+                    bvh_width=c.bvh_width)
+
     def config(self):
         c = lt_batch_config()
         _check(lib().lt_batch_get_config(self._h, C.byref(c)))
-        return dict(block_size=c.block_size, paths_per_thread=c.paths_per_thread, blocks_per_sm=c.blocks_per_sm)
+        return self._cfg(c)
 
-    def set_config(self, block_size=128, paths_per_thread=4, blocks_per_sm=0):
-        c = lt_batch_config(int(block_size), int(paths_per_thread), int(blocks_per_sm))
+    def set_config(self, block_size=128, paths_per_thread=4, blocks_per_sm=0, bvh_width=4):
+        c = lt_batch_config(int(block_size), int(paths_per_thread), int(blocks_per_sm), int(bvh_width))
         _check(lib().lt_batch_set_config(self._h, C.byref(c)))
 
     def tune(self, pass_id, reps=2, stream=None):
-        """Autotune block size x paths per thread for `pass_id`; returns (config, ms)."""
+        """Autotune block size x paths per thread x BVH width for `pass_id`; returns
+        (config, ms)."""
         c = lt_batch_config()
         ms = C.c_float()
         _check(lib().lt_batch_tune(self._h, int(pass_id), int(reps), _stream(stream), C.byref(c), C.byref(ms)))
-        return dict(block_size=c.block_size, paths_per_thread=c.paths_per_thread, blocks_per_sm=c.blocks_per_sm), \
-            float(ms.value)
+        return self._cfg(c), float(ms.value)
 
 
 def film_l2(image, target, d_image=None, loss=None, stream=None):

@@ -117,12 +117,14 @@ def test_batch_tune_picks_a_candidate_and_keeps_results(batch_items):
     B.run(lt.PASS_PRIMAL)
     cfg, ms = B.tune(lt.PASS_LRB3, reps=1)
     assert cfg["block_size"] in (64, 128, 256) and cfg["paths_per_thread"] in (1, 2, 4, 8)
+    assert cfg["bvh_width"] in (2, 4, 8)
     assert ms > 0 and B.config() == cfg
     _check_all(B)
-    B.set_config(block_size=64, paths_per_thread=1, blocks_per_sm=2)
-    B.run(lt.PASS_PRIMAL)
-    B.run(lt.PASS_LRB3)
-    _check_all(B)
+    for w in (2, 8):
+        B.set_config(block_size=64, paths_per_thread=1, blocks_per_sm=2, bvh_width=w)
+        B.run(lt.PASS_PRIMAL)
+        B.run(lt.PASS_LRB3)
+        _check_all(B)
 
 
 def test_batch_rejects_bad_requests(batch_items):

@@ -261,3 +261,35 @@ def test_detached_caustic_slab_matches_oracle(slab):
     r = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, mask=mask)
     assert rel_l2(gL.cpu().numpy(), r["d_Le"]) < 1e-3
     assert rel_l2(gA.cpu().numpy(), r["d_albedo"]) < 1e-3
+
+
+@pytest.mark.parametrize("width", [2, 4, 8])
+def test_bvh_widths_match_oracle(boxhm, slab, width):
+    """Every BVH width (threaded binary, 4- and 8-wide ordered traversal) gives the
+    oracle's decisions, image and attached gradients."""
+    for (sc, S), D, seed in ((boxhm, 6, 71), (slab, 8, 72)):
+        n = 1 << 13
+        h = torch.zeros(n, dtype=torch.int32, device="cuda")
+        S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, hash_out=h, bvh_width=width))
+        g = h.cpu().numpy().view(np.uint32)
+        _, oh = O.render(sc, seed=seed, n_paths=n, max_depth=D, want_hash=True)
+        assert (g != oh).mean() <= 2e-3
+        mask = (g == oh).astype(np.uint8)
+        dI_np = I.smooth_adjoint(sc.W, sc.H, seed)
+        o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask), bvh_width=width)
+        img = S.primal(o).cpu().numpy()
+        ref = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask)
+        mass = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, estimator=2)
+        assert primal_close(img, ref, mass=mass, W=max(sc.W, sc.H)).all()
+        gA, gL, gH = S.backward_lrb3(o, t32(dI_np))
+        r = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
+        S.sync_status()
+        assert rel_l2(gH.cpu().numpy(), r["d_heights"]) < 1e-3
+        assert rel_l2(gL.cpu().numpy(), r["d_Le"]) < 1e-3
+
+
+def test_bvh_width_rejected_when_unsupported(box64):
+    sc, S = box64
+    with pytest.raises(lt.LTError) as e:
+        S.primal(S.opts(n_paths=16, max_depth=4, bvh_width=3))
+    assert e.value.status == lt.LT_ERR_INVALID_ARG
