@@ -38,6 +38,27 @@ METRIC = "adjoint light paths/s (LRB-3-pass attached: refit + primal + film + ba
 FLOPS_PER = {"node": 24, "prim": 30, "vertex": 150, "conn": 100}
 
 
+KERNEL_SOURCES = ("lt_kernels.cu", "lt_device.cuh", "lt_launch.h", "lt_batch.h", "lt_mlp.cuh")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "traffic_box256_hm32_2p22.md")
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the LRB-3 backward pair from the committed ncu summary, or
+    None when the kernel sources have changed since that capture."""
+    import hashlib
+    import re
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, "paper_2609_32920_gb300", "csrc", f), "rb").read())
+        fp = re.search(r"kernel_sources_sha256_16: (\w+)", text).group(1)
+        tb = int(re.search(r"traffic_bytes_lrb3_backward_per_launch: (\d+)", text).group(1))
+    except (OSError, AttributeError, ValueError):
+        return None
+    return tb if fp == h.hexdigest()[:16] else None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,7 +325,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": "LRB-3-pass backward, attached: k_lrb3_p2 + k_lrb3_p3 (passes 2 and 3)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                "traffic": None, "kernel_ms": 1e3 * bwd_mean_s,
+                "traffic": profiled_traffic(), "traffic_source": "profiles/traffic_box256_hm32_2p22.md",
+                "kernel_ms": 1e3 * bwd_mean_s,
                 "census": {"rays": c[0], "box_tests": c[1], "prim_tests": c[2], "vertices": c[3],
                            "connections": c[4], "flops_per": FLOPS_PER}}
 
