@@ -372,13 +372,14 @@ def run_ours(args):
     return 0
 
 
-METHODS = ("lrb3", "lrb3_fused", "reslrb", "naive")
+METHODS = ("lrb3", "lrb3_fused", "lrb2", "reslrb", "naive")
 
 
 def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
     """run(method, D, reps) -> (median ms, peak extra device bytes) of one attached
     gradient: primal + film L2 + backward.  lrb3 = two-kernel form with its per-path
-    state; lrb3_fused = one fused backward kernel without per-path state."""
+    state; lrb3_fused = one fused backward kernel without per-path state; lrb2 = the
+    buffered two-pass baseline (per-vertex splat records, linear in depth)."""
     import torch
 
     from paper_2609_32920_gb300 import lt
@@ -400,6 +401,8 @@ def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
             aux = torch.empty((n_paths, 8), dtype=torch.float32, device=dev)
         elif method == "naive":
             aux = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device=dev)
+        elif method == "lrb2":
+            aux = torch.empty(S.lrb2_buffer_bytes(o), dtype=torch.uint8, device=dev)
 
         def once():
             if method.startswith("lrb3"):
@@ -410,6 +413,10 @@ def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
                 S.primal(o, estimator=lt.EST_RESLRB, image=img, aux=aux)
                 lt.film_l2(img, target, d_image=dI, loss=loss)
                 S.backward_reslrb(o, dI, aux, grads=grads)
+            elif method == "lrb2":
+                S.primal(o, estimator=lt.EST_BUFFERED, image=img, aux=aux)
+                lt.film_l2(img, target, d_image=dI, loss=loss)
+                S.backward_lrb2(o, dI, aux, grads=grads)
             else:
                 S.primal(o, estimator=lt.EST_NAIVE, image=img, aux=aux)
                 lt.film_l2(img, target, d_image=dI, loss=loss)

@@ -45,7 +45,7 @@ typedef enum {
 } lt_status;
 
 enum { LT_MAT_DIFFUSE = 0, LT_MAT_DIELECTRIC = 1, LT_MAT_EMITTER = 2 };
-enum { LT_EST_PLAIN = 0, LT_EST_RESLRB = 1, LT_EST_NAIVE = 2 };
+enum { LT_EST_PLAIN = 0, LT_EST_RESLRB = 1, LT_EST_NAIVE = 2, LT_EST_BUFFERED = 3 };
 enum { LT_TARGET_LUMINANCE = 0, LT_TARGET_MLP = 1 };
 
 typedef struct lt_scene lt_scene; /* opaque: device geometry, BVH, error word */
@@ -323,6 +323,20 @@ lt_status lt_batch_get_config(const lt_batch* batch, lt_batch_config* cfg);
 lt_status lt_batch_tune(lt_batch* batch, int pass, int reps, void* stream, lt_batch_config* best, float* best_ms);
 
 void lt_batch_destroy(lt_batch* batch);
+
+/* Buffered two-pass backward (the paper's lrb_2pass baseline, Sec. 4.1 and Sec. 6.2): the
+ * primal lt_primal(LT_EST_BUFFERED) splats like LT_EST_PLAIN and also stores every traced
+ * vertex's splat record (film position and contribution L_i, 20 B per vertex, memory
+ * linear in max_depth) in `buffer`; this call computes delta_total = sum_i Lbar_i * L_i
+ * from those records without tracing (Eq. 14) and then replays each path once to
+ * backpropagate (Eq. 15-17), so two traversals in all instead of LRB-3's three.  Same
+ * result as lt_backward_lrb3.  buffer: DEVICE, lt_lrb2_buffer_bytes(opts) bytes, written
+ * by lt_primal(LT_EST_BUFFERED) with the same opts (LT_ERR_OOM if smaller).  path_dbg
+ * (optional) [n_paths][4] = (delta_total rgb, n valid connections). */
+lt_status lt_backward_lrb2(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                           const float* d_image, void* buffer, size_t buffer_bytes, const lt_grads* grads,
+                           void* stream);
+size_t lt_lrb2_buffer_bytes(const lt_render_opts* opts);
 
 /* Bytes of the optional LRB-3 per-path state (opts->lrb3_state): 16 B (delta_total rgb,
  * validity bits 0-31) then 4 B (validity bits 32-63) per path, each array 256-B aligned. */

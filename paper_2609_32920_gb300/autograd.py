@@ -5,6 +5,8 @@ I(theta) [H, W, 3]; ``I.backward(dI)`` (or any loss built on I) produces gradien
 albedo, Le and heights through liblt's constant-memory adjoints (LRB-3-pass or ResLRB) or
 the naive baseline.  The forward pass refits the height field, then runs the primal kernel
 of the chosen method; the backward pass replays the same paths (same seed and path range).
+Methods: "lrb3" (LRB-3-pass), "reslrb" (ResLRB), "naive" (tape AD), "lrb2" (buffered
+two-pass).
 All work runs in liblt's CUDA kernels.
 """
 from __future__ import annotations
@@ -13,7 +15,7 @@ import torch
 
 from . import lt
 
-METHODS = ("lrb3", "reslrb", "naive")
+METHODS = ("lrb3", "reslrb", "naive", "lrb2")
 
 
 class _LightTrace(torch.autograd.Function):
@@ -31,6 +33,9 @@ class _LightTrace(torch.autograd.Function):
         elif method == "naive":
             aux = torch.empty(scene.naive_workspace_bytes(o), device=scene.device, dtype=torch.uint8)
             est = lt.EST_NAIVE
+        elif method == "lrb2":
+            aux = torch.empty(scene.lrb2_buffer_bytes(o), device=scene.device, dtype=torch.uint8)
+            est = lt.EST_BUFFERED
         else:
             est = lt.EST_PLAIN
         img = scene.primal(o, estimator=est, aux=aux, albedo=albedo.detach(), Le=Le.detach())
@@ -49,6 +54,8 @@ class _LightTrace(torch.autograd.Function):
             gA, gL, gH = S.backward_lrb3(o, gI, **kw)
         elif ctx.method == "reslrb":
             gA, gL, gH = S.backward_reslrb(o, gI, ctx.aux, **kw)
+        elif ctx.method == "lrb2":
+            gA, gL, gH = S.backward_lrb2(o, gI, ctx.aux, **kw)
         else:
             gA, gL, gH = S.backward_naive(o, gI, ctx.aux, **kw)
         ctx.aux = None

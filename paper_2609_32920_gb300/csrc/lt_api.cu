@@ -620,6 +620,11 @@ void lt_scene_destroy(lt_scene* s) { free_scene(s); }
 
 size_t lt_record_size(const lt_render_opts*) { return 32; }
 
+size_t lt_lrb2_buffer_bytes(const lt_render_opts* o) {
+  if (!o || o->n_paths < 0 || o->max_depth < 1) return 0;
+  return lrb2_layout(o->n_paths, o->max_depth).total;
+}
+
 size_t lt_lrb3_state_bytes(const lt_render_opts* o) {
   if (!o || o->n_paths < 0) return 0;
   return lrb3_state_bytes(o->n_paths);
@@ -636,11 +641,13 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
   lt_status v = check_opts(s, p, o);
   if (v != LT_OK) return v;
   if (!image) return fail(LT_ERR_INVALID_ARG, "image is NULL");
-  if (est < LT_EST_PLAIN || est > LT_EST_NAIVE) return fail(LT_ERR_INVALID_ARG, "unknown estimator");
+  if (est < LT_EST_PLAIN || est > LT_EST_BUFFERED) return fail(LT_ERR_INVALID_ARG, "unknown estimator");
   if (est == LT_EST_RESLRB && (!aux || aux_bytes < (size_t)o->n_paths * lt_record_size(o)))
     return fail(LT_ERR_INVALID_ARG, "ResLRB records buffer missing or too small");
   if (est == LT_EST_NAIVE && (!aux || aux_bytes < lt_naive_workspace_bytes(o)))
     return fail(LT_ERR_OOM, "naive-AD workspace missing or smaller than lt_naive_workspace_bytes()");
+  if (est == LT_EST_BUFFERED && (!aux || aux_bytes < lt_lrb2_buffer_bytes(o)))
+    return fail(LT_ERR_OOM, "buffered two-pass buffer missing or smaller than lt_lrb2_buffer_bytes()");
   cudaStream_t st = (cudaStream_t)stream;
   LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
   if (o->n_paths == 0) return LT_OK;
@@ -683,6 +690,26 @@ lt_status lt_backward_reslrb(lt_scene* s, const lt_params* p, const lt_render_op
   set_privatization(s, g, kp);
   cudaError_t e = launch_reslrb(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_reslrb: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_backward_lrb2(lt_scene* s, const lt_params* p, const lt_render_opts* o, const float* dI, void* buf,
+                           size_t buf_bytes, const lt_grads* g, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!dI) return fail(LT_ERR_INVALID_ARG, "d_image is NULL");
+  if (!buf || buf_bytes < lt_lrb2_buffer_bytes(o))
+    return fail(LT_ERR_OOM, "buffered two-pass buffer missing or smaller than lt_lrb2_buffer_bytes()");
+  cudaStream_t st = (cudaStream_t)stream;
+  GradPtrs gp;
+  v = prep_grads(s, g, st, gp);
+  if (v != LT_OK) return v;
+  if (o->n_paths == 0) return LT_OK;
+  KParams kp = kparams(p, o);
+  set_privatization(s, g, kp);
+  cudaError_t e = launch_lrb2(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, buf, gp,
+                              cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb2: ") + cudaGetErrorString(e));
   return LT_OK;
 }
 

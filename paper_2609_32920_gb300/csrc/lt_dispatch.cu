@@ -32,6 +32,11 @@ cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool ch
   return LT_BY_WIDTH(S.width, launch_naive(S, kp, att, chains, dI, ws, g, L, st));
 }
 
+cudaError_t launch_lrb2(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI, void* buf,
+                        const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
+  return LT_BY_WIDTH(S.width, launch_lrb2(S, kp, att, chains, dI, buf, g, L, st));
+}
+
 cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI, float tfloor, float* feats,
                            float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L, cudaStream_t st) {
   return LT_BY_WIDTH(S.width, launch_collect(S, kp, dI, tfloor, feats, targets, cap, count, L, st));

@@ -838,6 +838,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
         rec[1] = make_float4(Sh.x, Sh.y, Sh.z, 0.0f);
       }
       if (EST == 2) ((int*)aux)[p] = active ? k : 0;
+      if (EST == 3) ((int*)((char*)aux + lrb2_layout(kp.n_paths, kp.max_depth).counts))[p] = active ? k : 0;
       if (kp.hash) kp.hash[p] = hash;
       if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4((float)nconn, (float)k, 0.0f, 0.0f);
       busy = false;
@@ -870,6 +871,13 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
     bool refl = walk_scatter(S, w, v, ns, rho, r);
     fnv(hash, (uint32_t)v.P.orig);
     fnv(hash, vtx_flags(v, refl, c.valid));
+    if (EST == 3 && active) {
+      // buffered two-pass: the splat record of this vertex, [depth][path]
+      const Lrb2Layout lay = lrb2_layout(kp.n_paths, kp.max_depth);
+      const size_t at = (size_t)k * kp.n_paths + p;
+      ((float4*)((char*)aux + lay.rec4))[at] = make_float4(c.valid ? c.ux : -1.0f, c.uy, L.x, L.y);
+      ((float*)((char*)aux + lay.recz))[at] = L.z;
+    }
     if (EST == 2 && active) {
       // naive-AD tape: [depth][path] records of two float4
       float4* tape = (float4*)((char*)aux + kp.tape_offset) + 2 * ((size_t)k * kp.n_paths + p);
@@ -1196,6 +1204,44 @@ __global__ void __launch_bounds__(256) k_reslrb_batch(BatchArgs ba) {
   add3(ba.jobs[jb].g.d_Le, gLe);
 }
 
+// ======================================================================= buffered two-pass
+// lrb_2pass backward, first step: delta_total = sum_i Lbar_i * L_i (Eq. 14) and the
+// connection-validity mask of every path from the splat records the primal stored, with
+// no traversal; pass 3 of LRB-3 then backpropagates from that state.
+__global__ void __launch_bounds__(128) k_lrb2_reduce(DevScene S, KParams kp, const float* __restrict__ dI,
+                                                     void* buf, float* d_Le) {
+  const Lrb2Layout lay = lrb2_layout(kp.n_paths, kp.max_depth);
+  float4* xrec = (float4*)buf;
+  uint32_t* xhi = (uint32_t*)((char*)buf + lrb3_state_split(kp.n_paths));
+  const int* cnt = (const int*)((const char*)buf + lay.counts);
+  const float4* r4 = (const float4*)((const char*)buf + lay.rec4);
+  const float* rz = (const float*)((const char*)buf + lay.recz);
+  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  float3 gLe = f3(0, 0, 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
+    int K = cnt[p];
+    if (K > kp.max_depth) { set_err(S, ERR_BOUNDS); K = 0; }
+    float3 dtot = f3(0, 0, 0);
+    uint64_t valid = 0;
+    int nconn = 0;
+    for (int k = 0; k < K; ++k) {
+      const size_t at = (size_t)k * kp.n_paths + p;
+      const float4 a = r4[at];
+      if (a.x < 0.0f) continue;
+      const float3 L = f3(a.z, a.w, rz[at]);
+      dtot = dtot + mul(adjoint_read(dI, S.W, S.H, a.x, a.y, L, nullptr), L);
+      valid |= 1ull << k;
+      ++nconn;
+    }
+    xrec[p] = make_float4(dtot.x, dtot.y, dtot.z, __uint_as_float((uint32_t)valid));
+    xhi[p] = (uint32_t)(valid >> 32);
+    gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);  // emitted factor, weight delta_total
+    if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4(dtot.x, dtot.y, dtot.z, (float)nconn);
+  }
+  block_add3(d_Le, gLe);
+}
+
 // ======================================================================= naive reverse
 // Reverse sweep over the per-vertex tape: suffix sums of Lbar_i L_i replace the replay.
 template <bool ATT, bool CH>
@@ -1352,7 +1398,8 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
   switch (est) {
     case 0: k_primal<0><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
     case 1: k_primal<1><<<grid, L.block, smem, st>>>(S, kp, image, aux); break;
-    default: k_primal<2><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
+    case 2: k_primal<2><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
+    default: k_primal<3><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
   }
   return cudaGetLastError();
 }
@@ -1410,6 +1457,21 @@ cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool ch
   if (att && chains) k_naive<true, true><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
   else if (att) k_naive<true, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
   else k_naive<false, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lrb2(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI, void* buf,
+                        const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
+  int grid = grid_for(L, kp.n_paths);
+  k_lrb2_reduce<<<grid, L.block, 0, st>>>(S, kp, dI, buf, g.d_Le);
+  float4* xrec = (float4*)buf;
+  uint32_t* xhi = (uint32_t*)((char*)buf + lrb3_state_split(kp.n_paths));
+  const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
+  GradPtrs g3 = g;
+  g3.d_Le = nullptr;  // added by the reduction
+  if (att && chains) k_lrb3_p3<true, false, true><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+  else if (att) k_lrb3_p3<true, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+  else k_lrb3_p3<false, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
   return cudaGetLastError();
 }
 

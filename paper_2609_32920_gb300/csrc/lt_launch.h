@@ -68,6 +68,8 @@ struct BatchArgs;
                             const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);             \
   cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,           \
                            const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);               \
+  cudaError_t launch_lrb2(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,           \
+                          void* buf, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);                     \
   cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI, float tfloor, float* feats,   \
                              float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L,          \
                              cudaStream_t st);                                                                    \
@@ -81,8 +83,24 @@ LT_KERNEL_LAUNCHERS
 
 // `state` of launch_lrb3 (or null: fused kernel): per-path state of the two-kernel form,
 // layout float4[n_paths] then, at byte lrb3_state_split(n_paths), uint32[n_paths].
-inline size_t lrb3_state_split(int64_t n) { return ((size_t)n * 16 + 255) & ~(size_t)255; }
-inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_split(n) + (((size_t)n * 4 + 255) & ~(size_t)255); }
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ inline size_t lrb3_state_split(int64_t n) { return align256((size_t)n * 16); }
+__host__ __device__ inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_split(n) + align256((size_t)n * 4); }
+
+// Buffer of the buffered two-pass estimator (lrb_2pass): the LRB-3 per-path state, then
+// per path its traced vertex count (int), then per vertex [depth][path] the splat record
+// (u_x, u_y, L.r, L.g) (float4; u_x < 0 = no valid connection) and L.b (float).
+struct Lrb2Layout {
+  size_t counts, rec4, recz, total;
+};
+__host__ __device__ inline Lrb2Layout lrb2_layout(int64_t n, int d) {
+  Lrb2Layout L;
+  L.counts = lrb3_state_bytes(n);
+  L.rec4 = L.counts + align256((size_t)n * 4);
+  L.recz = L.rec4 + align256((size_t)n * (size_t)d * 16);
+  L.total = L.recz + align256((size_t)n * (size_t)d * 4);
+  return L;
+}
 size_t mlp_grad_smem_bytes();
 cudaError_t launch_mlp_grad(const float* P, const float* X, const float* T, int64_t n, float inv_batch, float* g,
                             float* loss, int sms, cudaStream_t st);

@@ -19,7 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblt.so")
 
 LT_OK, LT_ERR_INVALID_ARG, LT_ERR_OOM, LT_ERR_CUDA, LT_ERR_TIMEOUT, LT_ERR_DEVICE_CHECK, LT_ERR_UNSUPPORTED = range(7)
-EST_PLAIN, EST_RESLRB, EST_NAIVE = 0, 1, 2
+EST_PLAIN, EST_RESLRB, EST_NAIVE, EST_BUFFERED = 0, 1, 2, 3
 TARGET_LUMINANCE, TARGET_MLP = 0, 1
 STATUS_NAMES = {0: "LT_OK", 1: "LT_ERR_INVALID_ARG", 2: "LT_ERR_OOM", 3: "LT_ERR_CUDA", 4: "LT_ERR_TIMEOUT",
                 5: "LT_ERR_DEVICE_CHECK", 6: "LT_ERR_UNSUPPORTED"}
@@ -80,7 +80,8 @@ EXPORTS = ["lt_scene_create", "lt_scene_refit", "lt_scene_destroy", "lt_primal",
            "lt_backward_reslrb", "lt_backward_naive", "lt_film_l2", "lt_record_size", "lt_naive_workspace_bytes",
            "lt_sync_status", "lt_last_error", "lt_version", "lt_mlp_collect", "lt_mlp_init_stats", "lt_mlp_grad",
            "lt_mlp_adam", "lt_mlp_forward", "lt_naive_gradient_static", "lt_batch_create", "lt_batch_run",
-           "lt_batch_set_config", "lt_batch_get_config", "lt_batch_tune", "lt_batch_destroy", "lt_lrb3_state_bytes"]
+           "lt_batch_set_config", "lt_batch_get_config", "lt_batch_tune", "lt_batch_destroy", "lt_lrb3_state_bytes",
+           "lt_backward_lrb2", "lt_lrb2_buffer_bytes"]
 MLP_PARAMS, MLP_WEIGHTS = 5352, 5313
 
 
@@ -106,6 +107,9 @@ def lib():
             L.lt_record_size.restype = C.c_size_t
             L.lt_naive_workspace_bytes.argtypes = [P(lt_render_opts)]
             L.lt_naive_workspace_bytes.restype = C.c_size_t
+            L.lt_backward_lrb2.argtypes = [V, P(lt_params), P(lt_render_opts), V, V, C.c_size_t, P(lt_grads), V]
+            L.lt_lrb2_buffer_bytes.argtypes = [P(lt_render_opts)]
+            L.lt_lrb2_buffer_bytes.restype = C.c_size_t
             L.lt_lrb3_state_bytes.argtypes = [P(lt_render_opts)]
             L.lt_lrb3_state_bytes.restype = C.c_size_t
             L.lt_sync_status.argtypes = [V, V]
@@ -251,6 +255,9 @@ class Scene:
     def naive_workspace_bytes(self, o) -> int:
         return int(lib().lt_naive_workspace_bytes(C.byref(o)))
 
+    def lrb2_buffer_bytes(self, o) -> int:
+        return int(lib().lt_lrb2_buffer_bytes(C.byref(o)))
+
     def new_image(self):
         return torch.empty((self.H, self.W, 3), device=self.device, dtype=torch.float32)
 
@@ -285,6 +292,16 @@ class Scene:
         gr = self._grads(*g, accumulate)
         _check(lib().lt_backward_reslrb(self._h, C.byref(p), C.byref(o), _ptr(d_image.contiguous()), _ptr(records),
                                         C.byref(gr), _stream(stream)))
+        return g
+
+    def backward_lrb2(self, o, d_image, buffer, grads=None, accumulate=False, albedo=None, Le=None, stream=None):
+        """Buffered two-pass backward from the buffer lt_primal(EST_BUFFERED) filled."""
+        g = grads if grads is not None else self.new_grads()
+        p = self.params(albedo, Le)
+        gr = self._grads(*g, accumulate)
+        nbytes = buffer.numel() * buffer.element_size()
+        _check(lib().lt_backward_lrb2(self._h, C.byref(p), C.byref(o), _ptr(d_image.contiguous()), _ptr(buffer),
+                                      nbytes, C.byref(gr), _stream(stream)))
         return g
 
     def backward_naive(self, o, d_image, workspace, grads=None, accumulate=False, albedo=None, Le=None, stream=None):

@@ -29,6 +29,41 @@ def test_autograd_gradient_equals_direct_backward():
     assert torch.allclose(h.grad, gH[: h.numel()], rtol=1e-4, atol=1e-9)
 
 
+@pytest.mark.parametrize("method", ["lrb3", "naive"])
+def test_autograd_gradient_matches_central_differences(method):
+    """Detached albedo and emitted-radiance gradients through the autograd wrapper against
+    central differences of the GPU image at the same seed (the light-traced image of a
+    fixed seed is a polynomial in the albedos and linear in Le; no discrete decision
+    depends on either).  Differences are taken in FP64 from FP32 images."""
+    sc = I.box_scene(32)
+    S = lt.Scene(sc)
+    kw = dict(method=method, seed=9, n_paths=1 << 15, max_depth=4, attached=False)
+    dI = torch.tensor(I.smooth_adjoint(sc.W, sc.H, 6), dtype=torch.float32, device="cuda")
+    h0 = S.heights.clone()
+    albedo = S.albedo.clone().requires_grad_(True)
+    Le = S.Le.clone().requires_grad_(True)
+    (render(S, albedo, Le, h0, **kw) * dI).sum().backward()
+    torch.cuda.synchronize()
+
+    def loss(a, le):
+        with torch.no_grad():
+            img = render(S, a, le, h0, **kw)
+        return float((img.double() * dI.double()).sum())
+
+    rng = np.random.default_rng(0)
+    va = torch.tensor(rng.normal(size=albedo.numel()), dtype=torch.float32, device="cuda")
+    step = 5e-3
+    a0 = albedo.detach()
+    fd = (loss(a0 + step * va, Le.detach()) - loss(a0 - step * va, Le.detach())) / (2 * step)
+    ad = float((albedo.grad.double() * va.double()).sum())
+    assert abs(fd - ad) <= 1e-3 * abs(ad), (fd, ad)
+    for c in range(3):
+        e = torch.zeros(3, device="cuda")
+        e[c] = 0.05
+        fd = (loss(a0, Le.detach() + e) - loss(a0, Le.detach() - e)) / 0.1
+        assert abs(fd - float(Le.grad[c])) <= 1e-3 * abs(float(Le.grad[c])), (c, fd, float(Le.grad[c]))
+
+
 @pytest.mark.parametrize("method", ["lrb3", "reslrb", "naive"])
 def test_caustic_height_field_optimisation_reduces_loss(method):
     true_sc = I.slab_scene(48, n=12, seed=1)

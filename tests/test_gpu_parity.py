@@ -116,7 +116,43 @@ def test_naive_detached_matches_oracle(box64):
     assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
 
 
-@pytest.mark.parametrize("method", ["lrb3", "lrb3_split", "reslrb", "naive"])
+def _lrb2(S, o, dI, **kw):
+    """Buffered two-pass: primal with splat records, then the backward from them."""
+    buf = torch.empty(S.lrb2_buffer_bytes(o), dtype=torch.uint8, device="cuda")
+    img = S.primal(o, estimator=lt.EST_BUFFERED, aux=buf)
+    return img, S.backward_lrb2(o, dI, buf, **kw)
+
+
+def test_lrb2_detached_matches_naive_ad_and_lrb3(box64):
+    sc, S = box64
+    n, D, seed = 1 << 14, 9, 8
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 18)
+    mask = agree_mask(S, sc, seed, n, D)
+    dbg = torch.zeros((n, 4), device="cuda")
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask), dbg_out=dbg)
+    img, (gA, gL, _) = _lrb2(S, o, t32(dI_np))
+    ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, mask=mask, want_dbg=True)
+    assert rel_l2(gA.cpu().numpy(), ref["d_albedo"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+    m = mask.astype(bool)
+    d = dbg.cpu().numpy()
+    assert np.array_equal(d[m, 3], ref["dbg"][m, 3])
+    assert rel_l2(d[m, :3], ref["dbg"][m, :3]) < 1e-4
+    # the same gradient as LRB-3 per seed, and the same image as the plain primal
+    g3 = S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask)), t32(dI_np))
+    assert rel_l2(gA.cpu().numpy(), g3[0].cpu().numpy()) < 1e-5
+    plain = S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, mask=_dev_mask(mask)))
+    assert rel_l2(img.cpu().numpy(), plain.cpu().numpy()) < 1e-6
+    small = torch.empty(S.lrb2_buffer_bytes(o) - 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lt.LTError) as e:
+        S.primal(o, estimator=lt.EST_BUFFERED, aux=small)
+    assert e.value.status == lt.LT_ERR_OOM
+    with pytest.raises(lt.LTError) as e:
+        S.backward_lrb2(o, t32(dI_np), small)
+    assert e.value.status == lt.LT_ERR_OOM
+
+
+@pytest.mark.parametrize("method", ["lrb3", "lrb3_split", "lrb2", "reslrb", "naive"])
 def test_attached_height_field_matches_oracle(boxhm, method):
     sc, S = boxhm
     n, D, seed = 1 << 14, 6, 6
@@ -127,6 +163,9 @@ def test_attached_height_field_matches_oracle(boxhm, method):
     dI = t32(dI_np)
     if method.startswith("lrb3"):
         gA, gL, gH = S.backward_lrb3(o, dI)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
+    elif method == "lrb2":
+        _, (gA, gL, gH) = _lrb2(S, o, dI)
         ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
     elif method == "reslrb":
         rec = torch.zeros((n, 8), device="cuda")
@@ -218,7 +257,7 @@ def slab():
 
 
 @pytest.mark.parametrize("method,D", [("lrb3", 4), ("lrb3", 8), ("reslrb", 8), ("naive", 8), ("lrb3", 12),
-                                      ("lrb3_split", 12)])
+                                      ("lrb3_split", 12), ("lrb2", 12)])
 def test_attached_caustic_slab_matches_oracle(slab, method, D):
     """Dielectric height field: attached gradients through specular chains (first- and
     later-generation chains, anchors that are themselves chain ends)."""
@@ -231,6 +270,9 @@ def test_attached_caustic_slab_matches_oracle(slab, method, D):
     dI = t32(dI_np)
     if method.startswith("lrb3"):
         gA, gL, gH = S.backward_lrb3(o, dI)
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
+    elif method == "lrb2":
+        _, (gA, gL, gH) = _lrb2(S, o, dI)
         ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask)
     elif method == "reslrb":
         rec = torch.zeros((n, 8), device="cuda")
