@@ -212,12 +212,14 @@ def run_ours(args):
     target = T_S.primal(T_S.opts(seed=12345, n_paths=N_PATHS, max_depth=DEPTH))
     del T_S
     heights = S.heights.clone()
-    o_plain = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, path_offset=path_offset, n_norm=n_norm)
     # LRB-3 in the paper's three-pass form: passes 2 and 3 are two kernels that hand over
-    # delta_total and the connection-validity mask per path (20 B per path, flat in depth)
+    # delta_total and the connection-validity mask per path (20 B per path, flat in depth);
+    # the primal stores the masks there, so pass 2 traces no visibility rays
     lrb3_state = S.new_lrb3_state(N_PATHS)
+    o_plain = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, path_offset=path_offset, n_norm=n_norm,
+                     lrb3_state=lrb3_state)
     o_att = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset, n_norm=n_norm,
-                   lrb3_state=lrb3_state)
+                   lrb3_state=lrb3_state, lrb3_mask_ready=1)
     img = S.new_image()
     dI = torch.empty_like(img)
     loss = torch.empty(1, device=dev)
@@ -306,7 +308,7 @@ def run_ours(args):
     # ---------------- algorithmic work of the dominant kernel (counting variant, untimed)
     census = torch.zeros(5, dtype=torch.int64, device=dev)
     o_cnt = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset,
-                   n_norm=N_PATHS * ws, census=census, lrb3_state=lrb3_state)
+                   n_norm=N_PATHS * ws, census=census, lrb3_state=lrb3_state, lrb3_mask_ready=1)
     S.backward_lrb3(o_cnt, dI, grads=S.new_grads())
     torch.cuda.synchronize()
     c = [int(x) for x in census.cpu()]
@@ -396,7 +398,7 @@ def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
         aux = None
         state = S.new_lrb3_state(n_paths) if method == "lrb3" else None
         o = S.opts(seed=3, n_paths=n_paths, max_depth=D, attached=1, path_offset=path_offset, n_norm=n_norm,
-                   lrb3_state=state)
+                   lrb3_state=state, lrb3_mask_ready=int(state is not None))
         if method == "reslrb":
             aux = torch.empty((n_paths, 8), dtype=torch.float32, device=dev)
         elif method == "naive":

@@ -108,13 +108,19 @@ typedef struct {
                            work done (rays traced, BVH box tests, primitive tests,
                            path vertices, valid connections) using a counting kernel
                            variant; for measurement, not for timed runs           */
-  void* lrb3_state;     /* DEVICE optional, lt_backward_lrb3 only: per-path state of
+  void* lrb3_state;     /* DEVICE optional, for lt_backward_lrb3 (and written by a
+                           plain lt_primal, see lrb3_mask_ready): per-path state of
                            lt_lrb3_state_bytes(opts) bytes.  Given, passes 2 and 3 run
                            as two kernels and pass 2 stores each path's delta_total
                            and connection-validity mask there (20 B per path, the
                            paper's three-pass form); NULL, one fused kernel keeps
                            them in registers.  Same result either way.            */
   size_t lrb3_state_bytes; /* size of lrb3_state                                    */
+  int lrb3_mask_ready;  /* lt_primal(LT_EST_PLAIN) given lrb3_state also stores each
+                           path's connection-validity mask there.  Set 1 in the opts of
+                           lt_backward_lrb3 when that primal ran with the same seed,
+                           paths, depth and scene geometry: pass 2 then takes validity
+                           from the mask and traces no visibility rays.            */
   int bvh_width;        /* BVH node width traversed: 2 (threaded binary BVH, stackless),
                            4 or 8 (wide BVH, ordered stack traversal); 0 = 4.  The
                            scene holds all three; results agree up to ties.        */

@@ -25,8 +25,13 @@ class _LightTrace(torch.autograd.Function):
             raise ValueError(f"method must be one of {METHODS}")
         if scene.n_heights:
             scene.refit(heights.detach())
-        o = scene.opts(**opts_kw)
         aux = None
+        if method == "lrb3":
+            # LRB-3 state: the primal stores the validity masks, the backward reuses them
+            aux = scene.new_lrb3_state(opts_kw["n_paths"])
+            o = scene.opts(**opts_kw, lrb3_state=aux)
+        else:
+            o = scene.opts(**opts_kw)
         if method == "reslrb":
             aux = torch.empty((o.n_paths, 8), device=scene.device, dtype=torch.float32)
             est = lt.EST_RESLRB
@@ -38,7 +43,8 @@ class _LightTrace(torch.autograd.Function):
             est = lt.EST_BUFFERED
         else:
             est = lt.EST_PLAIN
-        img = scene.primal(o, estimator=est, aux=aux, albedo=albedo.detach(), Le=Le.detach())
+        img = scene.primal(o, estimator=est, aux=None if method == "lrb3" else aux, albedo=albedo.detach(),
+                           Le=Le.detach())
         ctx.scene, ctx.opts_kw, ctx.method, ctx.aux = scene, opts_kw, method, aux
         ctx.save_for_backward(albedo, Le, heights)
         return img
@@ -47,7 +53,10 @@ class _LightTrace(torch.autograd.Function):
     def backward(ctx, grad_image):
         albedo, Le, heights = ctx.saved_tensors
         S = ctx.scene
-        o = S.opts(**ctx.opts_kw)
+        if ctx.method == "lrb3":
+            o = S.opts(**ctx.opts_kw, lrb3_state=ctx.aux, lrb3_mask_ready=1)
+        else:
+            o = S.opts(**ctx.opts_kw)
         gI = grad_image.contiguous().float()
         kw = dict(albedo=albedo.detach(), Le=Le.detach())
         if ctx.method == "lrb3":

@@ -331,6 +331,7 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.census = (unsigned long long*)o->census;
   k.n_alb = k.n_h = k.priv_n = 0;
   k.mlp = o->target == LT_TARGET_MLP ? (const float*)o->mlp : nullptr;
+  k.vstate = nullptr;
   return k;
 }
 
@@ -648,10 +649,13 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
     return fail(LT_ERR_OOM, "naive-AD workspace missing or smaller than lt_naive_workspace_bytes()");
   if (est == LT_EST_BUFFERED && (!aux || aux_bytes < lt_lrb2_buffer_bytes(o)))
     return fail(LT_ERR_OOM, "buffered two-pass buffer missing or smaller than lt_lrb2_buffer_bytes()");
+  if (est == LT_EST_PLAIN && o->lrb3_state && o->lrb3_state_bytes < lt_lrb3_state_bytes(o))
+    return fail(LT_ERR_INVALID_ARG, "lrb3_state smaller than lt_lrb3_state_bytes()");
   cudaStream_t st = (cudaStream_t)stream;
   LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
+  if (est == LT_EST_PLAIN) kp.vstate = o->lrb3_state;
   cudaError_t e = launch_primal(dev_for(s, o->bvh_width), kp, est, image, aux, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_primal: ") + cudaGetErrorString(e));
   return LT_OK;
@@ -671,7 +675,8 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
   set_privatization(s, g, kp);
-  cudaError_t e = launch_lrb3(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, gp, o->lrb3_state, cfg_for(s, o), st);
+  cudaError_t e = launch_lrb3(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, gp,
+                              o->lrb3_state, o->lrb3_state && o->lrb3_mask_ready, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -1017,6 +1022,7 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     it.opts.census = nullptr;
     it.opts.lrb3_state = nullptr;
     it.opts.lrb3_state_bytes = 0;
+    it.opts.lrb3_mask_ready = 0;
     it.opts.bvh_width = 0;
     lt_status v = check_opts(it.scene, &it.params, &it.opts);
     if (v != LT_OK) return fail(v, at + g_last_error);

@@ -18,8 +18,8 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
 }
 
 cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
-                        const GradPtrs& g, void* state, const LaunchCfg& L, cudaStream_t st) {
-  return LT_BY_WIDTH(S.width, launch_lrb3(S, kp, att, chains, dI, g, state, L, st));
+                        const GradPtrs& g, void* state, bool mask_ready, const LaunchCfg& L, cudaStream_t st) {
+  return LT_BY_WIDTH(S.width, launch_lrb3(S, kp, att, chains, dI, g, state, mask_ready, L, st));
 }
 
 cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,

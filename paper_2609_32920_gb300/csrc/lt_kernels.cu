@@ -762,6 +762,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
   int64_t p = 0;
   int k = 0, nconn = 0;
   uint32_t hash = 0;
+  uint64_t vmask = 0;  // connection-validity bits (for kp.vstate)
   Walk w;
   // reservoir (capacity one)
   float Om = 0.0f, wR = 0.0f, Rux = 0.0f, Ruy = 0.0f;
@@ -786,6 +787,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
         float3 x0;
         walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
         hash = 2166136261u;
+        vmask = 0;
         nconn = 0;
         k = 0;
         Om = wR = Rux = Ruy = 0.0f;
@@ -837,6 +839,14 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
         rec[0] = make_float4(__int_as_float(active ? R : -1), wgt, Rux, Ruy);
         rec[1] = make_float4(Sh.x, Sh.y, Sh.z, 0.0f);
       }
+      if (EST == 0 && kp.vstate) {
+        // the validity mask for LRB-3 pass 2 (bits 0-31 in the w of the float4 record,
+        // bits 32-63 in the uint32 array); the rgb part is pass 2's to write
+        float4* xrec = (float4*)kp.vstate;
+        uint32_t* xhi = (uint32_t*)((char*)kp.vstate + lrb3_state_split(kp.n_paths));
+        reinterpret_cast<float*>(xrec + p)[3] = __uint_as_float((uint32_t)(active ? vmask : 0ull));
+        xhi[p] = (uint32_t)((active ? vmask : 0ull) >> 32);
+      }
       if (EST == 2) ((int*)aux)[p] = active ? k : 0;
       if (EST == 3) ((int*)((char*)aux + lrb2_layout(kp.n_paths, kp.max_depth).counts))[p] = active ? k : 0;
       if (kp.hash) kp.hash[p] = hash;
@@ -851,6 +861,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
       rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
       if (c.valid) {
         ++nconn;
+        vmask |= 1ull << k;
         L = mul(w.beta, rho) * (c.geo * kp.inv_n);
         if (active) {
           if (EST == 1) {
@@ -910,7 +921,9 @@ __global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
 // MODE 0: passes 2 and 3 fused per lane.  MODE 1: pass 2 only, storing delta_total and the
 // validity mask of path p in xrec[p] (rgb, bits 0-31) and xhi[p] (bits 32-63).  MODE 2:
 // pass 3 only, starting from that state (paths without a valid connection are skipped).
-template <bool ATT, bool ST, bool CH, bool BATCH, int MODE = 0>
+// MK (MODE 1): the primal stored each path's validity mask in xrec/xhi, so pass 2 takes
+// connection validity from it and traces no visibility rays.
+template <bool ATT, bool ST, bool CH, bool BATCH, int MODE = 0, bool MK = false>
 __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0, const float* __restrict__ dI0,
                                           const GradPtrs& g0, const BatchArgs& ba, float4* xrec = nullptr,
                                           uint32_t* xhi = nullptr) {
@@ -935,7 +948,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   int64_t p = 0;
   Walk w;
   float3 dtot = f3(0, 0, 0), rem = f3(0, 0, 0);
-  uint64_t valid = 0;
+  uint64_t valid = 0, known = 0;
   PendAdj pv;
   ChainInfo chain;
   chain.ka = -1;
@@ -979,6 +992,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
         dtot = f3(0, 0, 0);
         valid = 0;
+        if (MK) known = (uint64_t)__float_as_uint(xrec[p].w) | ((uint64_t)xhi[p] << 32);
         nconn = 0;
         k = 0;
         phase = PASS2;
@@ -999,9 +1013,14 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
       if (phase == PASS2 || ((valid >> k) & 1ull)) c = connect_pre(S, v.x, ns);
     }
-    // visibility only in pass 2; pass 3 reuses pass 2's validity bits
-    const bool vis = phase == PASS2 && c.valid;
-    if (vis && occluded<ST>(S, v.x, c.wc, c.dist, v.prim, &cs)) c.valid = false;
+    // visibility only in pass 2; pass 3 reuses pass 2's validity bits (and with MK pass 2
+    // reuses the primal's)
+    if (MK) {
+      if (phase == PASS2 && c.valid) c.valid = (known >> k) & 1ull;
+    } else {
+      const bool vis = phase == PASS2 && c.valid;
+      if (vis && occluded<ST>(S, v.x, c.wc, c.dist, v.prim, &cs)) c.valid = false;
+    }
     if (phase == IDLE) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
     if (MODE != 2 && phase == PASS2) {
@@ -1096,10 +1115,10 @@ __global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const floa
 }
 
 // Two-kernel form: pass 2 (per-path state out, emitted-radiance gradient) ...
-template <bool ST>
+template <bool ST, bool MK>
 __global__ void __launch_bounds__(128) k_lrb3_p2(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
                                                  float4* xrec, uint32_t* xhi) {
-  lrb3_body<false, ST, false, false, 1>(S, kp, dI, g0, BatchArgs{}, xrec, xhi);
+  lrb3_body<false, ST, false, false, 1, MK>(S, kp, dI, g0, BatchArgs{}, xrec, xhi);
 }
 // ... then pass 3 (albedo and height gradients) from that state.
 template <bool ATT, bool ST, bool CH>
@@ -1405,7 +1424,7 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
 }
 
 cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
-                        const GradPtrs& g, void* state, const LaunchCfg& L, cudaStream_t st) {
+                        const GradPtrs& g, void* state, bool mask_ready, const LaunchCfg& L, cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
   const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
   if (state) {
@@ -1415,8 +1434,13 @@ cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool cha
     k2.priv_n = 0;  // pass 2 writes no albedo or height gradients
     GradPtrs g3 = g;
     g3.d_Le = nullptr;  // pass 3 writes no emitted-radiance gradient
-    if (kp.census) k_lrb3_p2<true><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
-    else k_lrb3_p2<false><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+    if (kp.census) {
+      if (mask_ready) k_lrb3_p2<true, true><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+      else k_lrb3_p2<true, false><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+    } else {
+      if (mask_ready) k_lrb3_p2<false, true><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+      else k_lrb3_p2<false, false><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+    }
     if (kp.census) {
       if (att && chains) k_lrb3_p3<true, true, true><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
       else if (att) k_lrb3_p3<true, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);

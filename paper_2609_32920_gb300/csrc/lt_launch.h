@@ -24,6 +24,8 @@ struct KParams {
   int n_alb, n_h;              // parameter counts
   int priv_n;                  // > 0: gradients accumulate in n_alb + n_h floats of shared memory per block
   const float* mlp;            // learned reservoir target parameters (DEVICE) or null (luminance)
+  void* vstate;                // plain primal: LRB-3 per-path state that receives each path's
+                               // connection-validity mask (or null)
 };
 
 struct GradPtrs {
@@ -63,7 +65,7 @@ struct BatchArgs;
   cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux,               \
                             const LaunchCfg& L, cudaStream_t st);                                                 \
   cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,           \
-                          const GradPtrs& g, void* state, const LaunchCfg& L, cudaStream_t st);                   \
+                          const GradPtrs& g, void* state, bool mask_ready, const LaunchCfg& L, cudaStream_t st);  \
   cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,         \
                             const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);             \
   cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,           \

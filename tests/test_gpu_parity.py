@@ -116,6 +116,26 @@ def test_naive_detached_matches_oracle(box64):
     assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
 
 
+@pytest.mark.parametrize("fixture_name,attached", [("box64", 0), ("boxhm", 1), ("slab", 1)])
+def test_lrb3_reuses_primal_validity_masks(request, fixture_name, attached):
+    """A plain primal given the LRB-3 state stores each path's connection-validity mask;
+    pass 2 then traces no visibility rays and the gradient is the one of the full passes."""
+    sc, S = request.getfixturevalue(fixture_name)
+    n, D, seed = 1 << 13, 8, 31
+    dI = t32(I.smooth_adjoint(sc.W, sc.H, 33))
+    state = S.new_lrb3_state(n)
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state)
+    img = S.primal(o)
+    ref_img = S.primal(S.opts(seed=seed, n_paths=n, max_depth=D))
+    assert rel_l2(img.cpu().numpy(), ref_img.cpu().numpy()) < 1e-6
+    om = S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state, lrb3_mask_ready=1)
+    g = S.backward_lrb3(om, dI)
+    ref = S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached), dI)
+    S.sync_status()
+    for x, y in zip(g, ref):
+        assert rel_l2(x.cpu().numpy(), y.cpu().numpy()) < 1e-5
+
+
 def _lrb2(S, o, dI, **kw):
     """Buffered two-pass: primal with splat records, then the backward from them."""
     buf = torch.empty(S.lrb2_buffer_bytes(o), dtype=torch.uint8, device="cuda")
