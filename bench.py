@@ -564,7 +564,8 @@ def batched_study(dev, n_scenes=64, reps=3):
     items = []
     for k, spec in enumerate(I.batched_set(n_scenes, seed=0, max_paths_log2=22)):
         S = lt.Scene(spec["scene"])
-        it = dict(scene=S, n_paths=spec["n_paths"], max_depth=spec["max_depth"], attached=spec["attached"], seed=k)
+        it = dict(scene=S, n_paths=spec["n_paths"], max_depth=spec["max_depth"], attached=spec["attached"], seed=k,
+                  lrb3_state=True)
         if S.n_heights:
             it["heights"] = S.heights.clone()
         it["d_image"] = torch.tensor(I.smooth_adjoint(S.W, S.H, 500 + k), dtype=torch.float32, device=dev)
@@ -594,17 +595,22 @@ def batched_study(dev, n_scenes=64, reps=3):
         B.run(lt.PASS_PRIMAL)
         B.run(lt.PASS_LRB3)
 
+    # the same work scene by scene: two-kernel LRB-3 reusing the primal's validity masks
+    states = [it["scene"].new_lrb3_state(it["n_paths"]) for it in items]
+    opts_p = [it["scene"].opts(seed=it["seed"], n_paths=it["n_paths"], max_depth=it["max_depth"],
+                               attached=it["attached"], lrb3_state=st) for it, st in zip(items, states)]
     opts = [it["scene"].opts(seed=it["seed"], n_paths=it["n_paths"], max_depth=it["max_depth"],
-                             attached=it["attached"]) for it in items]
+                             attached=it["attached"], lrb3_state=st, lrb3_mask_ready=1)
+            for it, st in zip(items, states)]
     grads = [it["scene"].new_grads() for it in items]
     imgs = [it["scene"].new_image() for it in items]
 
     def sequential():
-        for it, o, g, im in zip(items, opts, grads, imgs):
+        for it, op, o, g, im in zip(items, opts_p, opts, grads, imgs):
             S = it["scene"]
             if S.n_heights:
                 S.refit(it["heights"])
-            S.primal(o, image=im)
+            S.primal(op, image=im)
             S.backward_lrb3(o, it["d_image"], grads=g)
 
     ms_b = timed(batched)

@@ -279,9 +279,14 @@ typedef struct {
   const float* heights;    /* [n_heights] or NULL: primal passes refit the scene first;
                               two items with heights must not share a scene          */
   lt_render_opts opts;     /* seed, path_offset, n_paths, n_norm, max_depth, attached,
-                              path_mask, path_hash and path_dbg are used as by the
-                              single-scene calls; the launch shape and BVH width come
-                              from the batch configuration                          */
+                              path_mask, path_hash, path_dbg, lrb3_state and
+                              lrb3_mask_ready are used as by the single-scene calls
+                              (each item its own state).  When every item has an
+                              lrb3_state, LT_PASS_LRB3 runs pass 2 for all items, then
+                              pass 3, as separate persistent launches, and
+                              LT_PASS_PRIMAL stores the validity masks that
+                              lrb3_mask_ready lets pass 2 reuse.  The launch shape
+                              and BVH width come from the batch configuration       */
   float* image;            /* [H][W][3] primal passes: overwritten                   */
   void* records;           /* [n_paths][lt_record_size] ResLRB records, or NULL when the
                               ResLRB passes are not run                              */

@@ -830,6 +830,9 @@ struct lt_batch {
   std::vector<lt_batch_item> items;  // table order (lean group, then chain group)
   int n_lean = 0;                    // items [0, n_lean) form the lean group
   bool att_lean = false, all_rec = true;
+  // every item carries an LRB-3 state: the LRB-3 pass runs pass 2 (all items) and pass 3
+  // (per group) as separate launches; mask_ready: pass 2 reuses the primal pass's masks
+  bool all_state = true, mask_ready = true;
   // one item table per chunk size (32 * paths_per_thread, paths_per_thread = 1, 2, 4, 8)
   // and BVH width (2, 4, 8): only the first-chunk indices and the scenes' BVH selection
   // differ, and a configuration change must not rewrite a table that a running pass may
@@ -837,7 +840,7 @@ struct lt_batch {
   BatchJob* d_jobs[12] = {};
   int64_t n_chunks[4] = {};   // whole batch
   int64_t split[4] = {};      // first chunk of the chain group
-  unsigned long long* d_ticket = nullptr;  // [4 passes][2 groups]
+  unsigned long long* d_ticket = nullptr;  // [4 passes][3 launches]
   cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams (main, second branch)
   cudaEvent_t fork = nullptr, join = nullptr;
   lt_batch_config cfg{128, 4, 0, 4};
@@ -885,11 +888,13 @@ int kernel_pass(int pass) {
          : pass == LT_PASS_LRB3 ? BPASS_LRB3 : BPASS_RESLRB;
 }
 
-// One persistent launch of the pass over the items [j0, j1) of the table.
+// One persistent launch over the items [j0, j1) of the table: kernel `kpass` (BatchPass),
+// queue ticket `slot` of its pass.
 struct GroupLaunch {
   int j0 = 0, j1 = 0;
   int64_t c0 = 0, c1 = 0;  // chunk range
   bool att = false, chains = false;
+  int kpass = 0, slot = 0;
   int per_sm = 0;
 };
 
@@ -898,26 +903,31 @@ std::vector<GroupLaunch> plan_pass(const lt_batch* b, int pass) {
   const int n = (int)b->items.size();
   std::vector<GroupLaunch> out;
   const bool primal = pass == LT_PASS_PRIMAL || pass == LT_PASS_PRIMAL_RESLRB;
+  const int kp = kernel_pass(pass);
   if (primal) {
-    out.push_back(GroupLaunch{0, n, 0, b->n_chunks[slot], false, false, 0});
+    out.push_back(GroupLaunch{0, n, 0, b->n_chunks[slot], false, false, kp, 0, 0});
+  } else if (pass == LT_PASS_LRB3 && b->all_state) {
+    const int p2 = b->mask_ready ? BPASS_LRB3_P2_MASK : BPASS_LRB3_P2;
+    out.push_back(GroupLaunch{0, n, 0, b->n_chunks[slot], false, false, p2, 2, 0});
+    out.push_back(GroupLaunch{0, b->n_lean, 0, b->split[slot], b->att_lean, false, BPASS_LRB3_P3, 0, 0});
+    out.push_back(GroupLaunch{b->n_lean, n, b->split[slot], b->n_chunks[slot], true, true, BPASS_LRB3_P3, 1, 0});
   } else {
-    out.push_back(GroupLaunch{0, b->n_lean, 0, b->split[slot], b->att_lean, false, 0});
-    out.push_back(GroupLaunch{b->n_lean, n, b->split[slot], b->n_chunks[slot], true, true, 0});
+    out.push_back(GroupLaunch{0, b->n_lean, 0, b->split[slot], b->att_lean, false, kp, 0, 0});
+    out.push_back(GroupLaunch{b->n_lean, n, b->split[slot], b->n_chunks[slot], true, true, kp, 1, 0});
   }
   std::vector<GroupLaunch> keep;
   for (GroupLaunch& g : out) {
     if (g.c1 <= g.c0) continue;
-    g.per_sm = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm
-                                        : batch_occupancy(b->cfg.bvh_width, kernel_pass(pass), g.att, g.chains,
-                                                          b->cfg.block_size);
+    g.per_sm = b->cfg.blocks_per_sm > 0
+                   ? b->cfg.blocks_per_sm
+                   : batch_occupancy(b->cfg.bvh_width, g.kpass, g.att, g.chains, b->cfg.block_size);
     keep.push_back(g);
   }
   return keep;
 }
 
-lt_status launch_group(lt_batch* b, int pass, int gi, const GroupLaunch& g, cudaStream_t st) {
-  const int slot = ppt_slot(b->cfg.paths_per_thread);
-  unsigned long long* ticket = b->d_ticket + 2 * pass + gi;
+lt_status launch_group(lt_batch* b, int pass, const GroupLaunch& g, cudaStream_t st) {
+  unsigned long long* ticket = b->d_ticket + 3 * pass + g.slot;
   LT_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st));
   const int block = b->cfg.block_size;
   // a resident grid, but no more warps than chunks
@@ -925,15 +935,16 @@ lt_status launch_group(lt_batch* b, int pass, int gi, const GroupLaunch& g, cuda
   const int64_t warps_per_block = block / 32;
   int64_t grid = std::min<int64_t>((int64_t)b->sms * g.per_sm, (nch + warps_per_block - 1) / warps_per_block);
   BatchArgs a{b->d_jobs[table_of(b->cfg)] + g.j0, g.j1 - g.j0, 32 * b->cfg.paths_per_thread, g.c0, nch, ticket};
-  cudaError_t e = launch_batch(b->cfg.bvh_width, kernel_pass(pass), g.att, g.chains, a, block,
-                               (int)std::max<int64_t>(grid, 1), st);
+  cudaError_t e = launch_batch(b->cfg.bvh_width, g.kpass, g.att, g.chains, a, block, (int)std::max<int64_t>(grid, 1),
+                               st);
   if (e) return fail(LT_ERR_CUDA, std::string("batched pass: ") + cudaGetErrorString(e));
   return LT_OK;
 }
 
-// Enqueue one pass on `st`: clears and refits of every item, then the group launches
-// (a second group runs on a forked branch `st2`, joined back into `st`).
-lt_status enqueue_pass(lt_batch* b, int pass, const std::vector<GroupLaunch>& plan, cudaStream_t st,
+// Enqueue one pass on `st`: clears and refits of every item, a pass-2 launch if the plan
+// has one, then the group launches (a second group runs on a forked branch `st2`, joined
+// back into `st`).
+lt_status enqueue_pass(lt_batch* b, int pass, const std::vector<GroupLaunch>& full_plan, cudaStream_t st,
                        cudaStream_t st2) {
   const bool primal = pass == LT_PASS_PRIMAL || pass == LT_PASS_PRIMAL_RESLRB;
   for (const lt_batch_item& it : b->items) {
@@ -950,15 +961,24 @@ lt_status enqueue_pass(lt_batch* b, int pass, const std::vector<GroupLaunch>& pl
       if (v != LT_OK) return v;
     }
   }
+  std::vector<GroupLaunch> plan;
+  for (const GroupLaunch& g : full_plan) {
+    if (g.kpass == BPASS_LRB3_P2 || g.kpass == BPASS_LRB3_P2_MASK) {
+      lt_status v = launch_group(b, pass, g, st);  // pass 2 of every item before any pass 3
+      if (v != LT_OK) return v;
+    } else {
+      plan.push_back(g);
+    }
+  }
   if (plan.size() == 2) {
     LT_CUDA(cudaEventRecord(b->fork, st));
     LT_CUDA(cudaStreamWaitEvent(st2, b->fork, 0));
-    lt_status v = launch_group(b, pass, 1, plan[1], st2);
+    lt_status v = launch_group(b, pass, plan[1], st2);
     if (v != LT_OK) return v;
     LT_CUDA(cudaEventRecord(b->join, st2));
   }
   if (!plan.empty()) {
-    lt_status v = launch_group(b, pass, 0, plan[0], st);
+    lt_status v = launch_group(b, pass, plan[0], st);
     if (v != LT_OK) return v;
   }
   if (plan.size() == 2) LT_CUDA(cudaStreamWaitEvent(st, b->join, 0));
@@ -1020,10 +1040,9 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     it.opts.target = LT_TARGET_LUMINANCE;
     it.opts.mlp = nullptr;
     it.opts.census = nullptr;
-    it.opts.lrb3_state = nullptr;
-    it.opts.lrb3_state_bytes = 0;
-    it.opts.lrb3_mask_ready = 0;
     it.opts.bvh_width = 0;
+    if (it.opts.lrb3_state && it.opts.lrb3_state_bytes < lt_lrb3_state_bytes(&it.opts))
+      return fail(LT_ERR_INVALID_ARG, at + "lrb3_state smaller than lt_lrb3_state_bytes()");
     lt_status v = check_opts(it.scene, &it.params, &it.opts);
     if (v != LT_OK) return fail(v, at + g_last_error);
     if (!it.image || !it.d_image) return fail(LT_ERR_INVALID_ARG, at + "image or d_image is NULL");
@@ -1033,6 +1052,8 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
           return fail(LT_ERR_INVALID_ARG, at + "two items with heights share a scene");
     b->sms = it.scene->sms;
     b->all_rec &= it.records != nullptr || it.opts.n_paths == 0;
+    b->all_state &= it.opts.lrb3_state != nullptr || it.opts.n_paths == 0;
+    b->mask_ready &= it.opts.lrb3_mask_ready != 0 || it.opts.n_paths == 0;
     if (it.opts.attached != 0 && it.scene->has_dielectric) {
       chain.push_back(it);
     } else {
@@ -1053,6 +1074,8 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     J.g = GradPtrs{it.grads.d_albedo, it.grads.d_Le, it.grads.d_heights};
     J.image = it.image;
     J.rec = it.records;
+    J.state = it.opts.lrb3_state;
+    J.kp.vstate = it.opts.lrb3_state;  // the batched plain primal stores validity masks there
     J.att = it.opts.attached != 0;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -1076,7 +1099,7 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
       LT_CUDA(cudaStreamSynchronize(st));
     }
   }
-  LT_CUDA(cudaMalloc(&b->d_ticket, 8 * sizeof(unsigned long long)));
+  LT_CUDA(cudaMalloc(&b->d_ticket, 12 * sizeof(unsigned long long)));
   LT_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   LT_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
   LT_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));

@@ -17,6 +17,7 @@ struct BatchJob {
   GradPtrs g;
   float* image;      // primal image
   void* rec;         // ResLRB records (32 B per path) or null
+  void* state;       // LRB-3 per-path state (two-kernel form) or null; kp.vstate = state
   int att;           // attached formulation
   int64_t chunk0;    // index of this item's first chunk in the batch's chunk sequence
 };
@@ -35,7 +36,17 @@ struct BatchArgs {
   unsigned long long* ticket;
 };
 
-enum BatchPass { BPASS_PRIMAL = 0, BPASS_PRIMAL_RES = 1, BPASS_LRB3 = 2, BPASS_RESLRB = 3 };
+// Kernel of a batched launch: the fused LRB-3 kernel, or its two-kernel form (pass 2,
+// with or without the primal's validity masks, then pass 3).
+enum BatchPass {
+  BPASS_PRIMAL = 0,
+  BPASS_PRIMAL_RES = 1,
+  BPASS_LRB3 = 2,
+  BPASS_RESLRB = 3,
+  BPASS_LRB3_P2 = 4,
+  BPASS_LRB3_P2_MASK = 5,
+  BPASS_LRB3_P3 = 6
+};
 
 // `chains`: some attached item's scene has dielectrics (compiles the specular-chain variant).
 // Per BVH width (namespaces w2, w4, w8, see lt_launch.h) and, in lt, by `width`.

@@ -309,21 +309,24 @@ __device__ __forceinline__ void wide_boxes(const DevScene& S, int j, float3 inv,
   }
 }
 
-// Sort (key, code) pairs ascending by key (insertion sort; W is 4 or 8).
+// Sort (key, code) pairs ascending by key: the optimal 5-comparator network for 4
+// children, insertion order otherwise.
+__device__ __forceinline__ void cas(float* k, int* c, int a, int b) {
+  const bool sw = k[b] < k[a];
+  const float ka = sw ? k[b] : k[a], kb = sw ? k[a] : k[b];
+  const int ca = sw ? c[b] : c[a], cb = sw ? c[a] : c[b];
+  k[a] = ka; k[b] = kb; c[a] = ca; c[b] = cb;
+}
 template <int W>
 __device__ __forceinline__ void sort_children(float k[W], int c[W]) {
+  if (W == 4) {
+    cas(k, c, 0, 1); cas(k, c, 2, 3); cas(k, c, 0, 2); cas(k, c, 1, 3); cas(k, c, 1, 2);
+    return;
+  }
 #pragma unroll
   for (int i = 1; i < W; ++i)
 #pragma unroll
-    for (int j = i; j > 0; --j) {
-      const bool sw = k[j] < k[j - 1];
-      const float tk = sw ? k[j] : k[j - 1];
-      k[j] = sw ? k[j - 1] : k[j];
-      k[j - 1] = tk;
-      const int tc = sw ? c[j] : c[j - 1];
-      c[j] = sw ? c[j - 1] : c[j];
-      c[j - 1] = tc;
-    }
+    for (int j = i; j > 0; --j) cas(k, c, j - 1, j);
 }
 
 // Closest hit through the wide BVH, same result rules as trace_closest2.  Stack-based

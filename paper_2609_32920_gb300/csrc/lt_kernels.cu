@@ -967,14 +967,22 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     const float* dI = BATCH ? ba.jobs[jb].dI : dI0;
     const GradPtrs& g = BATCH ? ba.jobs[jb].g : gs;
     const bool att = ATT && (!BATCH || ba.jobs[jb].att);
+    // per-path state of the two-kernel form (the lane's item's, in a batch)
+    float4* xr = xrec;
+    uint32_t* xh = xhi;
+    if (BATCH && MODE != 0) {
+      xr = (float4*)ba.jobs[jb].state;
+      xh = (uint32_t*)((char*)ba.jobs[jb].state + lrb3_state_split(kp.n_paths));
+    }
     if (want) {
       if (got < 0) {
         more = false;
       } else if (MODE == 2) {
-        const float4 a = xrec[got];
-        const uint64_t vm = (uint64_t)__float_as_uint(a.w) | ((uint64_t)xhi[got] << 32);
+        const float4 a = xr[got];
+        const uint64_t vm = (uint64_t)__float_as_uint(a.w) | ((uint64_t)xh[got] << 32);
         if (vm && (!kp.mask || kp.mask[got])) {
           p = got;
+          if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
           float3 x0;
           walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
           rem = f3(a.x, a.y, a.z);
@@ -992,7 +1000,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
         dtot = f3(0, 0, 0);
         valid = 0;
-        if (MK) known = (uint64_t)__float_as_uint(xrec[p].w) | ((uint64_t)xhi[p] << 32);
+        if (MK) known = (uint64_t)__float_as_uint(xr[p].w) | ((uint64_t)xh[p] << 32);
         nconn = 0;
         k = 0;
         phase = PASS2;
@@ -1028,8 +1036,8 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4(dtot.x, dtot.y, dtot.z, (float)nconn);
         gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);  // emitted factor, weight delta_total
         if (MODE == 1) {
-          xrec[p] = make_float4(dtot.x, dtot.y, dtot.z, __uint_as_float((uint32_t)valid));
-          xhi[p] = (uint32_t)(valid >> 32);
+          xr[p] = make_float4(dtot.x, dtot.y, dtot.z, __uint_as_float((uint32_t)valid));
+          xh[p] = (uint32_t)(valid >> 32);
           phase = IDLE;
         } else if (valid) {
           float3 x0;
@@ -1126,6 +1134,16 @@ __global__ void __launch_bounds__(128) k_lrb3_p3(DevScene S, KParams kp, const f
                                                  const float4* xrec, const uint32_t* xhi) {
   lrb3_body<ATT, ST, CH, false, 2>(S, kp, dI, g0, BatchArgs{}, const_cast<float4*>(xrec),
                                    const_cast<uint32_t*>(xhi));
+}
+
+// Batched two-kernel form: pass 2 over every item, then pass 3 per kernel group.
+template <bool MK>
+__global__ void __launch_bounds__(256) k_lrb3_p2_batch(BatchArgs ba) {
+  lrb3_body<false, false, false, true, 1, MK>(ba.jobs[0].S, ba.jobs[0].kp, nullptr, ba.jobs[0].g, ba);
+}
+template <bool ATT, bool CH>
+__global__ void __launch_bounds__(256) k_lrb3_p3_batch(BatchArgs ba) {
+  lrb3_body<ATT, false, CH, true, 2>(ba.jobs[0].S, ba.jobs[0].kp, nullptr, ba.jobs[0].g, ba);
 }
 
 template <bool ATT, bool CH>
@@ -1522,6 +1540,13 @@ static int occupancy_of(K kern, int block) {
       if (att && chains) CALL((k_lrb3_batch<true, true>));                       \
       else if (att) CALL((k_lrb3_batch<true, false>));                           \
       else CALL((k_lrb3_batch<false, false>));                                   \
+      break;                                                                     \
+    case BPASS_LRB3_P2: CALL(k_lrb3_p2_batch<false>); break;                    \
+    case BPASS_LRB3_P2_MASK: CALL(k_lrb3_p2_batch<true>); break;                \
+    case BPASS_LRB3_P3:                                                          \
+      if (att && chains) CALL((k_lrb3_p3_batch<true, true>));                    \
+      else if (att) CALL((k_lrb3_p3_batch<true, false>));                        \
+      else CALL((k_lrb3_p3_batch<false, false>));                                \
       break;                                                                     \
     default:                                                                     \
       if (att && chains) CALL((k_reslrb_batch<true, true>));                     \

@@ -337,7 +337,9 @@ class Batch:
 
     `items`: list of dicts with keys scene (Scene), n_paths, max_depth and optionally seed,
     path_offset, n_norm, attached, albedo, Le, heights (refit by the primal passes),
-    d_image, reslrb (allocate ResLRB records), accumulate.  The batch allocates each item's
+    d_image, reslrb (allocate ResLRB records), lrb3_state (allocate an LRB-3 state: the
+    LRB-3 pass then runs in two kernels reusing the primal pass's validity masks),
+    accumulate.  The batch allocates each item's
     image, records and gradients (attributes of the item dicts: image, records, grads) and
     keeps every tensor alive; change parameter values in place (copy_) between runs."""
 
@@ -346,9 +348,11 @@ class Batch:
         arr = (lt_batch_item * len(items))()
         for k, it in enumerate(items):
             S = it["scene"]
+            it["_state"] = S.new_lrb3_state(it["n_paths"]) if it.get("lrb3_state") else None
             o = Scene.opts(seed=it.get("seed", 0), n_paths=it["n_paths"], max_depth=it["max_depth"],
                            attached=it.get("attached", 0), path_offset=it.get("path_offset", 0),
-                           n_norm=it.get("n_norm", 0), dbg_out=it.get("dbg_out"))
+                           n_norm=it.get("n_norm", 0), dbg_out=it.get("dbg_out"), lrb3_state=it["_state"],
+                           lrb3_mask_ready=int(it["_state"] is not None))
             it.setdefault("albedo", S.albedo)
             it.setdefault("Le", S.Le)
             it.setdefault("d_image", torch.zeros((S.H, S.W, 3), device=S.device))

@@ -69,6 +69,19 @@ def test_batch_primal_and_lrb3_match_single_scene_calls(batch_items):
     assert float(B.items[3]["image"].abs().sum()) == 0.0  # the empty item
 
 
+def test_batch_two_kernel_lrb3_matches_single_scene_calls(batch_items):
+    """Items with an LRB-3 state: pass 2 over all items (reusing the primal pass's
+    validity masks), then pass 3 per kernel group."""
+    items = [dict(it, lrb3_state=True) for it in batch_items]
+    B = lt.Batch(items)
+    B.run(lt.PASS_PRIMAL)
+    B.run(lt.PASS_LRB3)
+    _check_all(B)
+    B.run(lt.PASS_PRIMAL)
+    B.run(lt.PASS_LRB3)  # replayed graphs
+    _check_all(B)
+
+
 def test_batch_reslrb_matches_single_scene_calls(batch_items):
     B = lt.Batch(batch_items)
     B.run(lt.PASS_PRIMAL_RESLRB)
