@@ -59,6 +59,13 @@ def profiled_traffic():
     return tb if fp == h.hexdigest()[:16] else None
 
 
+def workload_config(n_paths):
+    """The `config` object of the JSON line (both arms)."""
+    return {"workload": WORKLOAD, "resolution": "256x256", "heightmap": "32x32 (1922 triangles)",
+            "paths_per_gpu": n_paths, "max_depth": DEPTH, "attached": True,
+            "params": "Le (3) + 1024 heights (+ albedo textures)", "l2": "flushed between steps"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,10 +179,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "paths_per_step": n, "max_depth": DEPTH, "resolution": 256,
-                       "heightmap": 32, "method": "naive tape reverse-mode AD (FP64 CPU oracle)"},
+            "config": workload_config(N_PATHS),
             "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{n} of {N_PATHS} paths per step, attached naive AD, FP64"},
+                             "sample": f"{n} of the workload's {N_PATHS} paths per step (the same scene, depth and "
+                                       f"attached gradient), naive tape reverse-mode AD in FP64 on the host cores"},
             "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -357,9 +364,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "resolution": f"{W}x{H}", "heightmap": "32x32 (1922 triangles)",
-                           "paths_per_gpu": N_PATHS, "max_depth": DEPTH, "attached": True,
-                           "params": "Le (3) + 1024 heights (+ albedo textures)", "l2": "flushed between steps"},
+                "config": workload_config(N_PATHS),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
