@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -77,6 +78,7 @@ def parse():
     ap.add_argument("--paths-log2", type=int, default=22, help="paths per GPU per step (profiling uses fewer)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-target study")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched many-scene study")
+    ap.add_argument("--no-inverse", action="store_true", help="skip the caustic inverse-rendering study")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: only warm-up and timed steps (no e2e, census, sweep or CPU baseline)")
     return ap.parse_args()
@@ -98,7 +100,7 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"lt_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -351,6 +353,12 @@ def run_ours(args):
     batched = None
     if not args.no_batch and rank == 0:
         batched = batched_study(dev)
+    inverse = None
+    if not args.no_inverse and rank == 0:
+        # Adam moves every height by about the learning rate per step; the slab's heights
+        # are centimetres and the caustic overshoots beyond steps of about 1 mm, so the
+        # configured 1e-3 is reported beside a rate of the problem's scale
+        inverse = {"lr_1e-3": caustic_inverse_study(dev, lr=1e-3), "lr_3e-5": caustic_inverse_study(dev, lr=3e-5)}
     clk = clocks.stop()
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N=1 only)
@@ -370,7 +378,7 @@ def run_ours(args):
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
                 "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory, "caustic_memory_vs_depth": caustic,
-                "learned_target": learned, "batched": batched,
+                "learned_target": learned, "batched": batched, "caustic_inverse": inverse,
                 "lib": lt.version()}
         print(json.dumps(line))
     if ws > 1:
@@ -554,6 +562,69 @@ def _learned_one(dev, kind, seeds, paths_log2, depth):
 
 def learned_target_study(dev):
     return {"caustic": _learned_one(dev, "caustic", 16, 20, 32), "interior": _learned_one(dev, "interior", 16, 20, 16)}
+
+
+def caustic_inverse_study(dev, steps=200, paths_log2=24, depth=8, lr=1e-3):
+    """The paper's geometric inverse problem on the caustic workload: starting from a flat
+    slab top, recover the 128x128 height field of the dielectric slab (512x512 film) from
+    the caustic it casts, by Adam on the heights with attached LRB-3 gradients of the L2
+    film loss, 2^24 light paths per iteration (a new seed each), against a target rendered
+    from the true height field (sum of Gaussians, seed 1) at 2^26 paths."""
+    import torch
+
+    from paper_2609_32920_gb300 import inputs as I
+    from paper_2609_32920_gb300 import lt
+    n = 1 << paths_log2
+    true_sc = I.slab_scene(512, n=128, seed=1)
+    T_S = lt.Scene(true_sc)
+    target = T_S.primal(T_S.opts(seed=12345, n_paths=4 * n, max_depth=depth))
+    del T_S
+    sc = I.slab_scene(512, n=128, seed=0, flat=True)
+    S = lt.Scene(sc)
+    h_true = torch.tensor(true_sc.heights, dtype=torch.float32, device=dev)
+    h = torch.zeros_like(h_true).requires_grad_(True)
+    opt = torch.optim.Adam([h], lr=lr)
+    state = S.new_lrb3_state(n)
+    img = S.new_image()
+    dI = torch.empty_like(img)
+    loss = torch.empty(1, device=dev)
+    grads = S.new_grads()
+    losses = []
+    rmse0 = float(torch.sqrt(((h.detach() - h_true) ** 2).mean()))
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for it in range(steps):
+        S.refit(h.detach())
+        o = S.opts(seed=1000 + it, n_paths=n, max_depth=depth, attached=1, lrb3_state=state)
+        S.primal(o, image=img)
+        lt.film_l2(img, target, d_image=dI, loss=loss)
+        om = S.opts(seed=1000 + it, n_paths=n, max_depth=depth, attached=1, lrb3_state=state, lrb3_mask_ready=1)
+        S.backward_lrb3(om, dI, grads=grads)
+        h.grad = grads[2][: h.numel()].clone()
+        opt.step()
+        losses.append(loss.clone())
+    b.record(stream)
+    torch.cuda.synchronize()
+    S.sync_status()
+    L = [float(x) for x in losses]
+    rmse1 = float(torch.sqrt(((h.detach() - h_true) ** 2).mean()))
+
+    def caustic_error(heights):
+        # relative L2 distance of a 2^26-path render from the target (both with little noise)
+        S.refit(heights)
+        im = S.primal(S.opts(seed=777, n_paths=4 * n, max_depth=depth))
+        return float(torch.linalg.norm(im - target) / torch.linalg.norm(target))
+
+    err = [caustic_error(torch.zeros_like(h_true)), caustic_error(h.detach())]
+    return {"workload": "slab512_hm128 (caustic), flat start, 128x128 heights, depth 8, 2^%d paths per "
+                        "iteration, %d Adam steps lr %g" % (paths_log2, steps, lr),
+            "ms_per_iteration": a.elapsed_time(b) / steps,
+            "loss_mean_of_10_at": {str(i): sum(L[i:i + 10]) / 10 for i in range(0, steps, max(10, steps // 5))},
+            "loss_first10_last10": [sum(L[:10]) / 10, sum(L[-10:]) / 10],
+            "height_rmse_m_start_end": [rmse0, rmse1],
+            "caustic_rel_l2_start_end_2p%d" % (paths_log2 + 2): err}
 
 
 def batched_study(dev, n_scenes=64, reps=3):

@@ -360,12 +360,26 @@ struct ChainState {
   bool refl;
 };
 
-// Replay the chain from its start to vertex j (a <= j) and trace the ray leaving j.
+// Replay the chain from its start to vertex j (a <= j) and trace the ray leaving j.  The
+// chain's first direction is the one the walk sampled at the anchor (the emitter's
+// cosine sample, or the diffuse anchor's, on the side of its normal that faces the chain
+// start), recomputed from the same Philox numbers, so the replay repeats the walk's
+// arithmetic exactly; normalize(x_a - x_p) differs from it in the last bits, which can
+// send a grazing ray to another triangle.
 __device__ __forceinline__ bool chain_replay(const DevScene& S, const KParams& kp, uint64_t n, const ChainInfo& c,
                                              int j, ChainState& st, HitRec& next) {
   Prim Pa = load_prim(S, c.prim_a);
   float3 x = Pa.o + Pa.e1 * c.ba1 + Pa.e2 * c.ba2;
-  float3 din = normalize(x - c.xp);
+  float3 din;
+  if (c.kanchor < 0) {
+    const float4 r0 = rand4(kp.seed, n, 0);
+    din = cosine_dir(S.ln, r0.z, r0.w);
+  } else {
+    const Prim Pp = load_prim(S, c.prim_p);
+    const float3 np = normalize(cross(Pp.e1, Pp.e2));
+    const float4 r = rand4(kp.seed, n, (uint32_t)(c.kanchor + 1));
+    din = cosine_dir(dot(x - c.xp, np) >= 0.0f ? np : -np, r.x, r.y);
+  }
   int prim = c.prim_a;
   for (int k = c.ka;; ++k) {
     Prim P = load_prim(S, prim);

@@ -23,9 +23,9 @@ Scene layout (all float64 / int32 numpy arrays):
 * camera: ``cam_pos``, ``cam_look``, ``cam_up``, ``fov_y_deg``, ``W``, ``H``.
 * parameters: ``albedo`` [n_albedo], ``Le`` [3], ``heights`` [n_h].
 
-The workload recipes follow the five synthetic configurations of the scope table
-(box, box+heightmap, caustic slab, batched set, learned-target workload) and are
-documented in DESIGN.md.
+The generators below build the synthetic workloads: the textured box, the box with a
+diffuse height field, the dielectric caustic slab, the batched set of uneven scenes and
+the scenes of the learned-target study, each fully determined by its arguments and seeds.
 """
 from __future__ import annotations
 
@@ -305,7 +305,7 @@ def slab_scene(res: int = 512, n: int = 128, seed: int = 0, Le_scale: float = 1.
     strip(list(top[:, 0]), c[0], c[3], np.array([-1.0, 0, 0]))      # x=-0.5
     strip(list(top[:, n - 1]), c[1], c[2], np.array([1.0, 0, 0]))   # x=+0.5
     heights = np.zeros(n * n) if flat else gaussian_bumps(n, 1.0, seed)
-    # Le chosen so the mean receiver pixel is O(1) for the default camera
+    # Le chosen so that the mean receiver pixel is O(1) for the default camera
     Le = np.full(3, 2000.0 * Le_scale)
     return b.build((0.0, 1.2, -1.6), (0.0, 0.0, 0.0), (0, 1, 0), 45.0, res, res, Le, heights,
                    f"slab{res}_hm{n}", meta={"kind": "slab", "heightmap": n})

@@ -40,7 +40,7 @@ def primal_close(a, b, rtol=1e-4, mass=None, W=None):
 
     The second term is the FP32 rounding of film positions: u = W/2 (1 + p_x / tan_x) comes
     from the hit point through about ten FP32 operations, so |du| <= 16 * 2^-24 * max(W, H)
-    pixels (see DESIGN.md); a tent tap's weight moves by at most |du|, so a pixel moves by at
+    pixels; a tent tap's weight moves by at most |du|, so a pixel moves by at
     most |du| times its tap mass (sum of |L| over splats touching it, from the oracle).  A
     splat within rounding of a pixel-centre line may use a tap set shifted by one pixel
     (with a near-zero weight there), so the mass is dilated over each pixel's 3x3

@@ -355,3 +355,21 @@ def test_bvh_width_rejected_when_unsupported(box64):
     with pytest.raises(lt.LTError) as e:
         S.primal(S.opts(n_paths=16, max_depth=4, bvh_width=3))
     assert e.value.status == lt.LT_ERR_INVALID_ARG
+
+
+def test_device_check_reports_a_corrupt_buffer(box64):
+    """Device-side checks return an error status instead of faulting: a buffered two-pass
+    buffer whose per-path vertex counts exceed max_depth (as after a primal with other
+    options) makes the reduction set the scene's error word, which lt_sync_status reports
+    as LT_ERR_DEVICE_CHECK and clears."""
+    sc, S = box64
+    n, D = 256, 4
+    o = S.opts(seed=1, n_paths=n, max_depth=D)
+    buf = torch.zeros(S.lrb2_buffer_bytes(o), dtype=torch.uint8, device="cuda")
+    head = S.lrb3_state_bytes(n)
+    buf[head: head + 4 * n].view(torch.int32).fill_(D + 5)  # impossible vertex counts
+    S.backward_lrb2(o, torch.zeros((sc.H, sc.W, 3), device="cuda"), buf)
+    with pytest.raises(lt.LTError) as e:
+        S.sync_status()
+    assert e.value.status == lt.LT_ERR_DEVICE_CHECK
+    S.sync_status()  # cleared
