@@ -342,9 +342,10 @@ def run_ours(args):
                            "connections": c[4], "flops_per": FLOPS_PER}}
 
     # ---------------- other estimators + memory vs depth (outside the headline timing)
-    methods, memory, caustic = {}, {}, None
+    methods, memory, caustic, roulette = {}, {}, None, None
     if not args.no_sweep:
         methods, memory = method_sweep(S, sc, target, heights, dev, path_offset, ws, flush)
+        roulette = roulette_study(S, target, dev, path_offset, ws, flush)
         if rank == 0:
             caustic = caustic_sweep(dev, flush)
     learned = None
@@ -378,6 +379,7 @@ def run_ours(args):
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
                 "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory, "caustic_memory_vs_depth": caustic,
+                "russian_roulette": roulette,
                 "learned_target": learned, "batched": batched, "caustic_inverse": inverse,
                 "lib": lt.version()}
         print(json.dumps(line))
@@ -470,6 +472,46 @@ def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
             ms, peak = run(m, D, timed_reps=1)
             memory[str(D)][m] = {"extra_bytes": peak, "ms": ms}
     return methods, memory
+
+
+def roulette_study(S, target, dev, path_offset, ws, flush, rr_depth=4, rr_prob=0.8):
+    """Time of one attached LRB-3 gradient (primal + film + backward) on the box workload
+    with Russian roulette (continue with probability 0.8 after depth 4) and without it,
+    at depths 16 and 64."""
+    import torch
+
+    from paper_2609_32920_gb300 import lt
+    stream = torch.cuda.current_stream()
+    img = S.new_image()
+    dI = torch.empty_like(img)
+    loss = torch.empty(1, device=dev)
+    grads = S.new_grads()
+    state = S.new_lrb3_state(N_PATHS)
+    out = {"setting": "continue with probability %g after depth %d" % (rr_prob, rr_depth)}
+    for D in (16, 64):
+        row = {}
+        for name, rr in (("off", {}), ("on", dict(rr_depth=rr_depth, rr_prob=rr_prob))):
+            kw = dict(seed=5, n_paths=N_PATHS, max_depth=D, attached=1, path_offset=path_offset,
+                      n_norm=N_PATHS * ws, lrb3_state=state, **rr)
+            op, om = S.opts(**kw), S.opts(lrb3_mask_ready=1, **kw)
+
+            def once():
+                S.primal(op, image=img)
+                lt.film_l2(img, target, d_image=dI, loss=loss)
+                S.backward_lrb3(om, dI, grads=grads)
+            once()
+            ms = []
+            for _ in range(3):
+                flush.fill_(3)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                once()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            row[name] = {"ms": statistics.median(ms), "paths_per_s": N_PATHS / (statistics.median(ms) * 1e-3)}
+        out[str(D)] = row
+    return out
 
 
 def caustic_sweep(dev, flush, paths_log2=24):

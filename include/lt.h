@@ -121,6 +121,12 @@ typedef struct {
                            lt_backward_lrb3 when that primal ran with the same seed,
                            paths, depth and scene geometry: pass 2 then takes validity
                            from the mask and traces no visibility rays.            */
+  int rr_depth;         /* Russian roulette: after each vertex of depth >= rr_depth a
+                           path continues with probability rr_prob (Philox stream 2
+                           of that depth) and its throughput is divided by rr_prob;
+                           0 = off.  Every pass replays the same decisions; 1/rr_prob
+                           is a constant factor of the path's function.            */
+  float rr_prob;        /* survival probability in (0, 1] when rr_depth > 0          */
   int bvh_width;        /* BVH node width traversed: 2 (threaded binary BVH, stackless),
                            4 or 8 (wide BVH, ordered stack traversal); 0 = 4.  The
                            scene holds all three; results agree up to ties.        */

@@ -22,6 +22,8 @@
 //                    pin the light tracer's normalisation by reciprocity.
 //   * helpers exported for pinning tests: Philox, dielectric sampling, reservoir draw,
 //                    the frozen-decision loss (for finite differences).
+//   * every method optionally applies Russian roulette with a fixed survival probability
+//     (see trace()), the path-termination rule the CUDA path replays identically.
 //
 // Model (the "frozen-decision" function that every method differentiates): every
 // discrete choice of a path (which primitive each ray hits, reflect/refract branch,
@@ -81,6 +83,8 @@ typedef struct {
   int method;          // see header comment
   int attached;        // 0 detached, 1 attached (geometry differentiated)
   int n_threads;
+  int rr_depth;        // Russian roulette after vertices of depth >= rr_depth (0: off)
+  double rr_q;         // its survival probability
 } or_run;
 
 typedef struct {
@@ -347,6 +351,7 @@ struct Vtx {
   bool conn;       // valid sensor connection (diffuse only)
   double g0 = -1;  // frozen value at theta0 of the attached segment weight G*A (or -1: not yet known)
   double F0 = -1;  // frozen value at theta0 of the chosen dielectric branch probability
+  double rr = 1.0; // Russian-roulette weight 1/q applied after this vertex (1: none)
 };
 struct Path {
   D3 x0, n_light;
@@ -377,8 +382,11 @@ bool connect_ok(const Scene& sc, const D3& x, const D3& ns, int prim) {
 // (Sec. 3.1 light tracing: emitter sample, then intersect / connect / scatter per vertex).
 // Uniforms: vertex depth d uses Philox counter (n, d, 0); at d=0 (emitter) u0,u1 pick the
 // point on the light and u2,u3 a cosine-weighted direction; at d>=1 u0,u1 sample the
-// diffuse direction, u2 the Fresnel branch, u3 the reservoir draw.
-Path trace(const Scene& sc, uint64_t seed, uint64_t n, int D) {
+// diffuse direction, u2 the Fresnel branch, u3 the reservoir draw.  Russian roulette
+// (rr_depth > 0): after the vertex of depth d >= rr_depth the path continues when the
+// first uniform of Philox counter (n, d, 2) is below q, with weight 1/q; the decision
+// does not depend on the parameters, so 1/q is a constant factor of the path function.
+Path trace(const Scene& sc, uint64_t seed, uint64_t n, int D, int rr_depth, double rr_q) {
   Path P;
   const double* h = sc.p->heights;
   D3 lo, le1, le2;
@@ -431,6 +439,10 @@ Path trace(const Scene& sc, uint64_t seed, uint64_t n, int D) {
     P.v.push_back(v);
     org = x;
     skip = prim;
+    if (rr_depth > 0 && d >= rr_depth) {
+      if (rand4(seed, n, (uint32_t)d, 2).u[0] < rr_q) P.v.back().rr = 1.0 / rr_q;
+      else break;
+    }
   }
   return P;
 }
@@ -600,6 +612,8 @@ void eval_path(const Scene& sc, const Path& P, const AA& albedo, const AL& Le, c
         dprev = rf;
       }
     }
+    if (v.rr != 1.0)
+      for (int c = 0; c < 3; ++c) beta[c] = beta[c] * T(v.rr);
     xprev = x;
     nprev = n;
   }
@@ -742,7 +756,7 @@ int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const
     std::vector<ConnOut<double>> cs;
     for (int64_t i = a; i < b; ++i) {
       uint64_t n = (uint64_t)(run->path_begin + i);
-      Path P = trace(sc, run->seed, n, run->max_depth);
+      Path P = trace(sc, run->seed, n, run->max_depth, run->rr_depth, run->rr_q);
       if (hashes) hashes[i] = P.hash;
       eval_path<double>(sc, P, Plain{p->albedo}, Plain{p->Le}, Plain{p->heights}, N, cs, &P);
       if (records) {
@@ -812,7 +826,7 @@ int or_gradient(const or_scene* s, const or_params* p, const or_run* run, const 
     std::vector<ConnOut<V>> cv;
     for (int64_t i = a; i < b; ++i) {
       uint64_t n = (uint64_t)(run->path_begin + i);
-      Path P = trace(sc, run->seed, n, run->max_depth);
+      Path P = trace(sc, run->seed, n, run->max_depth, run->rr_depth, run->rr_q);
       if (hashes) hashes[i] = P.hash;
       eval_path<double>(sc, P, Plain{p->albedo}, Plain{p->Le}, Plain{p->heights}, N, cs, &P);
       double dt[3] = {0, 0, 0};
@@ -934,7 +948,7 @@ double or_frozen_loss(const or_scene* s, const or_params* p0, const or_params* p
     for (int64_t i = a; i < b; ++i) {
       if (mask && !mask[i]) continue;
       uint64_t n = (uint64_t)(run->path_begin + i);
-      Path P = trace(sc0, run->seed, n, run->max_depth);
+      Path P = trace(sc0, run->seed, n, run->max_depth, run->rr_depth, run->rr_q);
       eval_path<double>(sc0, P, Plain{p0->albedo}, Plain{p0->Le}, Plain{p0->heights}, N, cs, &P);
       if (run->method == 2) {
         path_reservoir(run->seed, n, P, cs);

@@ -312,6 +312,8 @@ lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->target == LT_TARGET_MLP && !o->mlp) return fail(LT_ERR_INVALID_ARG, "LT_TARGET_MLP needs opts->mlp");
   if (o->bvh_width != 0 && o->bvh_width != 2 && o->bvh_width != 4 && o->bvh_width != 8)
     return fail(LT_ERR_INVALID_ARG, "bvh_width must be 0, 2, 4 or 8");
+  if (o->rr_depth < 0 || (o->rr_depth > 0 && !(o->rr_prob > 0.0f && o->rr_prob <= 1.0f)))
+    return fail(LT_ERR_INVALID_ARG, "rr_depth must be >= 0 and rr_prob in (0, 1]");
   return LT_OK;
 }
 
@@ -332,6 +334,8 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.n_alb = k.n_h = k.priv_n = 0;
   k.mlp = o->target == LT_TARGET_MLP ? (const float*)o->mlp : nullptr;
   k.vstate = nullptr;
+  k.rr_depth = o->rr_depth;
+  k.rr_q = o->rr_prob;
   return k;
 }
 

@@ -319,14 +319,14 @@ __device__ __forceinline__ void cas(float* k, int* c, int a, int b) {
 }
 template <int W>
 __device__ __forceinline__ void sort_children(float k[W], int c[W]) {
-  if (W == 4) {
+  if constexpr (W == 4) {
     cas(k, c, 0, 1); cas(k, c, 2, 3); cas(k, c, 0, 2); cas(k, c, 1, 3); cas(k, c, 1, 2);
-    return;
+  } else {
+#pragma unroll
+    for (int i = 1; i < W; ++i)
+#pragma unroll
+      for (int j = i; j > 0; --j) cas(k, c, j - 1, j);
   }
-#pragma unroll
-  for (int i = 1; i < W; ++i)
-#pragma unroll
-    for (int j = i; j > 0; --j) cas(k, c, j - 1, j);
 }
 
 // Closest hit through the wide BVH, same result rules as trace_closest2.  Stack-based

@@ -110,6 +110,7 @@ struct Walk {
   int skip;
   int prev_kind;
   float3 beta;
+  bool dead;  // ended by Russian roulette
 };
 
 // Emitter sample (uniform point, cosine direction, beta_0 = Le A pi) from counter (n, 0).
@@ -122,6 +123,18 @@ __device__ __forceinline__ void walk_start(const DevScene& S, uint64_t seed, uin
   w.skip = S.emitter_prim;
   w.prev_kind = K_EMITTER;
   w.beta = Le * (S.light_area * kPi);
+  w.dead = false;
+}
+
+// Russian roulette after vertex k (depth k + 1), once the walk has scattered: the path
+// continues with probability rr_q, decided by Philox stream 2 at that depth, and its
+// throughput is divided by rr_q.  The decision and rr_q do not depend on the parameters,
+// so every replay ends the path at the same vertex and the derivative treats 1/rr_q as a
+// constant factor.
+__device__ __forceinline__ void walk_rr(const KParams& kp, uint64_t n, int k, Walk& w) {
+  if (kp.rr_depth <= 0 || k + 1 < kp.rr_depth) return;
+  if (rand4(kp.seed, n, (uint32_t)(k + 1), 2).x < kp.rr_q) w.beta = w.beta * (1.0f / kp.rr_q);
+  else w.dead = true;
 }
 
 // One surface vertex: closest hit and its local frame.
@@ -154,6 +167,7 @@ __device__ __forceinline__ bool walk_finish(const DevScene& S, const Walk& w, co
 // Per-lane version (divergent callers): trace and complete the next vertex.
 template <bool ST = false>
 __device__ __forceinline__ bool walk_hit(const DevScene& S, const Walk& w, Vtx& v, Census* cs = nullptr) {
+  if (w.dead) return false;
   HitRec h = trace_closest<ST>(S, w.org, w.dir, w.skip, cs);
   if (h.prim < 0) return false;
   v.prim = h.prim;
@@ -659,6 +673,7 @@ __global__ void __launch_bounds__(128) k_collect(DevScene S, KParams kp, const f
         }
       }
       walk_scatter(S, w, v, ns, rho, r);
+      walk_rr(kp, n, k, w);
     }
   }
 }
@@ -811,7 +826,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
       }
     }
     if (!__any_sync(0xffffffffu, busy || more)) break;
-    const bool trav = busy && k < kp.max_depth;
+    const bool trav = busy && k < kp.max_depth && !w.dead;
     HitRec h;
     h.prim = -1;
     if (trav) h = trace_closest(S, w.org, w.dir, w.skip);
@@ -894,6 +909,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
       }
     }
     bool refl = walk_scatter(S, w, v, ns, rho, r);
+    walk_rr(kp, n, k, w);
     fnv(hash, (uint32_t)v.P.orig);
     fnv(hash, vtx_flags(v, refl, c.valid));
     if (EST == 3 && active) {
@@ -1022,7 +1038,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     }
     if (!__any_sync(0xffffffffu, phase != IDLE || more)) break;
     const int kmax = phase == PASS2 ? kp.max_depth : last + 1;
-    const bool trav = phase != IDLE && k < kmax;
+    const bool trav = phase != IDLE && k < kmax && !w.dead;
     HitRec h;
     h.prim = -1;
     if (trav) h = trace_closest<ST>(S, w.org, w.dir, w.skip, &cs);
@@ -1082,6 +1098,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         }
       }
       walk_scatter(S, w, v, ns, rho, r);
+      walk_rr(kp, n, k, w);
       ++k;
     } else if (MODE != 1) {
       if (!alive) {
@@ -1113,6 +1130,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
           pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
       }
       walk_scatter(S, w, v, ns, rho, r);
+      walk_rr(kp, n, k, w);
       ++k;
     }
   }
@@ -1210,6 +1228,7 @@ __device__ __forceinline__ void reslrb_path(const DevScene& S, const KParams& kp
       }
     }
     walk_scatter(S, w, v, ns, rho, r);
+    walk_rr(kp, n, k, w);
   }
   if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights);
 }

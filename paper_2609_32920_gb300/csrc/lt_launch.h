@@ -26,6 +26,8 @@ struct KParams {
   const float* mlp;            // learned reservoir target parameters (DEVICE) or null (luminance)
   void* vstate;                // plain primal: LRB-3 per-path state that receives each path's
                                // connection-validity mask (or null)
+  int rr_depth;                // Russian roulette after vertices of depth >= rr_depth (0: off)
+  float rr_q;                  // survival probability of the roulette
 };
 
 struct GradPtrs {

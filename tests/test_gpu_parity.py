@@ -373,3 +373,49 @@ def test_device_check_reports_a_corrupt_buffer(box64):
         S.sync_status()
     assert e.value.status == lt.LT_ERR_DEVICE_CHECK
     S.sync_status()  # cleared
+
+
+@pytest.mark.parametrize("method", ["lrb3", "lrb2", "reslrb", "naive"])
+def test_russian_roulette_matches_oracle(boxhm, slab, method):
+    """Russian roulette (continue with probability 0.7 after depth 2) gives the oracle's
+    decisions, image and attached gradients in every method: each replay ends a path at
+    the vertex the primal ended it."""
+    rr = dict(rr_depth=2, rr_prob=0.7)
+    for (sc, S), seed in ((boxhm, 81), (slab, 82)):
+        n, D = 1 << 13, 10
+        h = torch.zeros(n, dtype=torch.int32, device="cuda")
+        S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, hash_out=h, **rr))
+        g = h.cpu().numpy().view(np.uint32)
+        _, oh = O.render(sc, seed=seed, n_paths=n, max_depth=D, want_hash=True, **rr)
+        assert (g != oh).mean() <= 2e-3
+        mask = (g == oh).astype(np.uint8)
+        dI_np = I.smooth_adjoint(sc.W, sc.H, seed)
+        dI = t32(dI_np)
+        state = S.new_lrb3_state(n)
+        o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask), lrb3_state=state, **rr)
+        if method == "lrb3":
+            img = S.primal(o)
+            om = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask), lrb3_state=state,
+                        lrb3_mask_ready=1, **rr)
+            gA, gL, gH = S.backward_lrb3(om, dI)
+            ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask, **rr)
+            oimg = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, **rr)
+            mass = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, estimator=2, **rr)
+            assert primal_close(img.cpu().numpy(), oimg, mass=mass, W=max(sc.W, sc.H)).all()
+        elif method == "lrb2":
+            _, (gA, gL, gH) = _lrb2(S, o, dI)
+            ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask, **rr)
+        elif method == "reslrb":
+            rec = torch.zeros((n, 8), device="cuda")
+            S.primal(o, estimator=lt.EST_RESLRB, aux=rec)
+            gA, gL, gH = S.backward_reslrb(o, dI, rec)
+            ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, method=O.RESLRB_AD,
+                             mask=mask, **rr)
+        else:
+            ws = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device="cuda")
+            S.primal(o, estimator=lt.EST_NAIVE, aux=ws)
+            gA, gL, gH = S.backward_naive(o, dI, ws)
+            ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask, **rr)
+        S.sync_status()
+        assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
+        assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3

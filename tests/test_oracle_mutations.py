@@ -37,6 +37,10 @@ MUTANTS = {
     "reservoir_prob": ("if (u[i] < w[i] / Om) { R = (int)i; wR = w[i]; }",
                        "if (u[i] < w[i] / (Om + w[i])) { R = (int)i; wR = w[i]; }",
                        ["test_reservoir_selection_pmf_and_unbiasedness"]),
+    # Russian roulette without the 1/q weight of the surviving paths
+    "rr_no_weight": ("if (rand4(seed, n, (uint32_t)d, 2).u[0] < rr_q) P.v.back().rr = 1.0 / rr_q;",
+                     "if (rand4(seed, n, (uint32_t)d, 2).u[0] < rr_q) P.v.back().rr = 1.0;",
+                     ["test_russian_roulette_unbiased_and_exact"]),
     # attached slide: intersection parameter with the wrong sign
     "slide_sign": ("T tt = dot(o - xprev, n) / dot(din, n);", "T tt = dot(xprev - o, n) / dot(din, n);",
                    ["test_attached_height_gradient_vs_frozen_central_differences"]),
