@@ -127,6 +127,10 @@ typedef struct {
                            0 = off.  Every pass replays the same decisions; 1/rr_prob
                            is a constant factor of the path's function.            */
   float rr_prob;        /* survival probability in (0, 1] when rr_depth > 0          */
+  int filter;           /* reconstruction filter of splat and adjoint read (Eq. 20-21):
+                           0 tent of radius 1 pixel; 1 truncated Gaussian, standard
+                           deviation 0.5 pixel, radius 1.5 pixel, shifted to reach 0
+                           at the radius and normalised to unit integral           */
   int bvh_width;        /* BVH node width traversed: 2 (threaded binary BVH, stackless),
                            4 or 8 (wide BVH, ordered stack traversal); 0 = 4.  The
                            scene holds all three; results agree up to ties.        */

@@ -23,7 +23,8 @@
 //   * helpers exported for pinning tests: Philox, dielectric sampling, reservoir draw,
 //                    the frozen-decision loss (for finite differences).
 //   * every method optionally applies Russian roulette with a fixed survival probability
-//     (see trace()), the path-termination rule the CUDA path replays identically.
+//     (see trace()), the path-termination rule the CUDA path replays identically, and
+//     either the tent or a wider truncated-Gaussian reconstruction filter (filter_taps).
 //
 // Model (the "frozen-decision" function that every method differentiates): every
 // discrete choice of a path (which primitive each ray hits, reflect/refract branch,
@@ -85,6 +86,7 @@ typedef struct {
   int n_threads;
   int rr_depth;        // Russian roulette after vertices of depth >= rr_depth (0: off)
   double rr_q;         // its survival probability
+  int filter;          // reconstruction filter: 0 tent (radius 1 px), 1 Gaussian (see filter_taps)
 } or_run;
 
 typedef struct {
@@ -173,6 +175,8 @@ inline V operator*(V x, V y) { return node(x.v * y.v, x.i, y.v, y.i, x.v); }
 inline V operator/(V x, V y) { double q = x.v / y.v; return node(q, x.i, 1.0 / y.v, y.i, -q / y.v); }
 inline V sqrt(V x) { double s = std::sqrt(x.v); return node(s, x.i, 0.5 / s); }
 inline V fabs(V x) { return x.v < 0 ? -x : x; }
+inline V expo(V x) { double e = std::exp(x.v); return node(e, x.i, e); }
+inline double expo(double x) { return std::exp(x); }
 
 inline double val(double x) { return x; }
 inline double val(const V& x) { return x.v; }
@@ -514,10 +518,36 @@ template <class T> int tent_taps(int W, int H, T ux, T uy, int px[4], int py[4],
     }
   return k;
 }
-template <class T> void adjoint_read(const double* dI, int W, int H, T ux, T uy, T out[3]) {
-  int px[4], py[4];
-  T w[4];
-  int k = tent_taps<T>(W, H, ux, uy, px, py, w);
+// Wider filter (filter 1): separable truncated Gaussian of standard deviation 0.5 pixel
+// over pixel centres, shifted down by its value at the radius 1.5 pixel so that it falls
+// continuously to zero there, and normalised to unit integral per axis:
+// g(d) = (exp(-2 d^2) - exp(-4.5)) / C for |d| < 1.5, C = sqrt(pi/2) erf(1.5 sqrt(2)) - 3 exp(-4.5).
+// Up to three taps per axis.  filter 0 is the tent of tent_taps.
+inline double gauss_norm() { return std::sqrt(PI / 2) * std::erf(1.5 * std::sqrt(2.0)) - 3.0 * std::exp(-4.5); }
+template <class T> int filter_taps(int filter, int W, int H, T ux, T uy, int px[9], int py[9], T w[9]) {
+  if (filter == 0) return tent_taps<T>(W, H, ux, uy, px, py, w);
+  const double inv_c = 1.0 / gauss_norm(), cut = std::exp(-4.5);
+  int xs[3], ys[3], nx = 0, ny = 0;
+  T wx[3], wy[3];
+  const double bx = std::floor(val(ux) - 0.5), by = std::floor(val(uy) - 0.5);
+  for (int i = -1; i <= 2; ++i) {
+    const int X = (int)bx + i;
+    T dx = ux - T(X + 0.5);
+    if (std::fabs(val(dx)) < 1.5 && X >= 0 && X < W && nx < 3) { xs[nx] = X; wx[nx] = (expo(T(-2.0) * dx * dx) - T(cut)) * T(inv_c); ++nx; }
+    const int Y = (int)by + i;
+    T dy = uy - T(Y + 0.5);
+    if (std::fabs(val(dy)) < 1.5 && Y >= 0 && Y < H && ny < 3) { ys[ny] = Y; wy[ny] = (expo(T(-2.0) * dy * dy) - T(cut)) * T(inv_c); ++ny; }
+  }
+  int k = 0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) { px[k] = xs[i]; py[k] = ys[j]; w[k] = wx[i] * wy[j]; ++k; }
+  return k;
+}
+
+template <class T> void adjoint_read(const double* dI, int W, int H, T ux, T uy, T out[3], int filter) {
+  int px[9], py[9];
+  T w[9];
+  int k = filter_taps<T>(filter, W, H, ux, uy, px, py, w);
   for (int c = 0; c < 3; ++c) {
     out[c] = T(0.0);
     for (int i = 0; i < k; ++i) out[c] = out[c] + w[i] * dI[(py[i] * W + px[i]) * 3 + c];
@@ -660,10 +690,10 @@ struct Acc {
   double loss = 0;
 };
 
-void splat(const Scene& sc, double* img, const double L[3], double ux, double uy) {
-  int px[4], py[4];
-  double w[4];
-  int k = tent_taps<double>(sc.s->W, sc.s->H, ux, uy, px, py, w);
+void splat(const Scene& sc, double* img, const double L[3], double ux, double uy, int filter) {
+  int px[9], py[9];
+  double w[9];
+  int k = filter_taps<double>(filter, sc.s->W, sc.s->H, ux, uy, px, py, w);
   for (int i = 0; i < k; ++i)
     for (int c = 0; c < 3; ++c) img[(py[i] * sc.s->W + px[i]) * 3 + c] += w[i] * L[c];
 }
@@ -702,6 +732,12 @@ void or_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out) {
   U4 c = {{ctr[0], ctr[1], ctr[2], ctr[3]}};
   U4 o = philox(k0, k1, c);
   for (int i = 0; i < 4; ++i) out[i] = o.v[i];
+}
+
+// Taps of the reconstruction filter at film position (ux, uy): pixel coordinates and
+// weights (at most 9); returns their count.
+int or_filter_taps(int filter, int W, int H, double ux, double uy, int* px, int* py, double* w) {
+  return filter_taps<double>(filter, W, H, ux, uy, px, py, w);
 }
 
 void or_uniforms(uint64_t seed, uint64_t n, uint32_t d, uint32_t s, double* out4) {
@@ -767,14 +803,14 @@ int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const
       }
       if (mask && !mask[i]) continue;
       if (estimator == 0) {
-        for (auto& c : cs) splat(sc, A.img.data(), c.L, c.ux, c.uy);
+        for (auto& c : cs) splat(sc, A.img.data(), c.L, c.ux, c.uy, run->filter);
       } else if (estimator == 2) {
         // tap mass: |L| added with weight one to every on-film tap of each splat (bounds
         // how much a film-position error can move a pixel)
         for (auto& c : cs) {
-          int px[4], py[4];
-          double w[4];
-          int k = tent_taps<double>(sc.s->W, sc.s->H, c.ux, c.uy, px, py, w);
+          int px[9], py[9];
+          double w[9];
+          int k = filter_taps<double>(run->filter, sc.s->W, sc.s->H, c.ux, c.uy, px, py, w);
           for (int t = 0; t < k; ++t)
             for (int ch = 0; ch < 3; ++ch) A.img[(py[t] * sc.s->W + px[t]) * 3 + ch] += std::fabs(c.L[ch]);
         }
@@ -783,7 +819,7 @@ int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const
         if (P.R < 0) continue;
         const ConnOut<double>& c = cs[P.R];
         double S[3] = {c.L[0] * P.res_w, c.L[1] * P.res_w, c.L[2] * P.res_w};
-        splat(sc, A.img.data(), S, c.ux, c.uy);
+        splat(sc, A.img.data(), S, c.ux, c.uy, run->filter);
         if (records) {
           double* r = records + 8 * i;
           r[0] = c.vi; r[1] = P.res_w; r[2] = c.ux; r[3] = c.uy;
@@ -832,7 +868,7 @@ int or_gradient(const or_scene* s, const or_params* p, const or_run* run, const 
       double dt[3] = {0, 0, 0};
       for (auto& c : cs) {
         double Lb[3];
-        adjoint_read<double>(dI, W, H, c.ux, c.uy, Lb);
+        adjoint_read<double>(dI, W, H, c.ux, c.uy, Lb, run->filter);
         for (int k = 0; k < 3; ++k) dt[k] += Lb[k] * c.L[k];
       }
       if (path_dbg) {
@@ -859,7 +895,7 @@ int or_gradient(const or_scene* s, const or_params* p, const or_run* run, const 
         for (size_t j = 0; j < cv.size(); ++j) {
           if (run->method == 2 && (int)j != P.R) continue;
           V Lb[3];
-          adjoint_read<V>(dI, W, H, cv[j].ux, cv[j].uy, Lb);
+          adjoint_read<V>(dI, W, H, cv[j].ux, cv[j].uy, Lb, run->filter);
           V term = cv[j].L[0] * Lb[0] + cv[j].L[1] * Lb[1] + cv[j].L[2] * Lb[2];
           if (run->method == 2) term = term * V(P.res_w);
           loss = loss + term;
@@ -883,7 +919,7 @@ int or_gradient(const or_scene* s, const or_params* p, const or_run* run, const 
         std::vector<double> Pw(3 * cs.size());
         for (size_t j = 0; j < cs.size(); ++j) {
           double Lb[3];
-          adjoint_read<double>(dI, W, H, cs[j].ux, cs[j].uy, Lb);
+          adjoint_read<double>(dI, W, H, cs[j].ux, cs[j].uy, Lb, run->filter);
           for (int c = 0; c < 3; ++c) Pw[3 * j + c] = Lb[c] * cs[j].L[c];
         }
         double rem[3];
@@ -958,7 +994,7 @@ double or_frozen_loss(const or_scene* s, const or_params* p0, const or_params* p
       for (size_t j = 0; j < cs.size(); ++j) {
         if (run->method == 2 && (int)j != P.R) continue;
         double Lb[3];
-        adjoint_read<double>(dI, s->W, s->H, cs[j].ux, cs[j].uy, Lb);
+        adjoint_read<double>(dI, s->W, s->H, cs[j].ux, cs[j].uy, Lb, run->filter);
         double term = cs[j].L[0] * Lb[0] + cs[j].L[1] * Lb[1] + cs[j].L[2] * Lb[2];
         part[tid] += run->method == 2 ? term * P.res_w : term;
       }

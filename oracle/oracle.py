@@ -50,7 +50,8 @@ class or_params(C.Structure):
 class or_run(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("path_begin", C.c_int64), ("n_paths", C.c_int64),
                 ("n_norm", C.c_int64), ("max_depth", C.c_int), ("method", C.c_int),
-                ("attached", C.c_int), ("n_threads", C.c_int), ("rr_depth", C.c_int), ("rr_q", C.c_double)]
+                ("attached", C.c_int), ("n_threads", C.c_int), ("rr_depth", C.c_int), ("rr_q", C.c_double),
+                ("filter", C.c_int)]
 
 
 class or_grads(C.Structure):
@@ -79,6 +80,8 @@ def lib():
             L.or_render_pt.argtypes = [P(or_scene), P(or_params), C.c_uint64, C.c_int, C.c_int, C.c_int,
                                        C.c_void_p]
             L.or_philox.argtypes = [C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]
+            L.or_filter_taps.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]
             L.or_uniforms.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_void_p]
             L.or_dielectric.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p,
                                         C.c_void_p, C.c_void_p]
@@ -153,12 +156,12 @@ def _rr(rr_depth, rr_prob):
 
 def render(scene, seed=0, n_paths=1 << 12, max_depth=4, path_begin=0, n_norm=0, estimator=0, mask=None,
            want_hash=False, want_records=False, n_threads=0, albedo=None, Le=None, heights=None, rr_depth=0,
-           rr_prob=1.0):
+           rr_prob=1.0, filter=0):
     """Light-traced image [H, W, 3] (float64).  estimator 0 = every connection, 1 = reservoir."""
     b = _Bound(scene, albedo, Le, heights)
     img = np.zeros((scene.H, scene.W, 3))
     run = or_run(seed, path_begin, n_paths, n_norm or n_paths, max_depth, 0, 0, _threads(n_threads),
-                 *_rr(rr_depth, rr_prob))
+                 *_rr(rr_depth, rr_prob), int(filter))
     hashes = np.zeros(n_paths, dtype=np.uint32) if want_hash else None
     recs = np.zeros((n_paths, 8)) if want_records else None
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
@@ -174,7 +177,7 @@ def render(scene, seed=0, n_paths=1 << 12, max_depth=4, path_begin=0, n_norm=0, 
 
 def gradient(scene, dI, seed=0, n_paths=1 << 12, max_depth=4, method=NAIVE, attached=0, path_begin=0, n_norm=0,
              mask=None, want_hash=False, want_dbg=False, n_threads=0, albedo=None, Le=None, heights=None,
-             rr_depth=0, rr_prob=1.0):
+             rr_depth=0, rr_prob=1.0, filter=0):
     """dict(d_albedo, d_Le, d_heights, loss[, hash][, dbg]) of <dI, I_s>."""
     b = _Bound(scene, albedo, Le, heights)
     dI = np.ascontiguousarray(dI, dtype=np.float64)
@@ -185,7 +188,7 @@ def gradient(scene, dI, seed=0, n_paths=1 << 12, max_depth=4, method=NAIVE, atta
     loss = np.zeros(1)
     g = or_grads(_dp(ga), _dp(gl), _dp(gh), _dp(loss))
     run = or_run(seed, path_begin, n_paths, n_norm or n_paths, max_depth, method, attached, _threads(n_threads),
-                 *_rr(rr_depth, rr_prob))
+                 *_rr(rr_depth, rr_prob), int(filter))
     hashes = np.zeros(n_paths, dtype=np.uint32) if want_hash else None
     dbg = np.zeros((n_paths, 4)) if want_dbg else None
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
@@ -202,14 +205,14 @@ def gradient(scene, dI, seed=0, n_paths=1 << 12, max_depth=4, method=NAIVE, atta
 
 
 def frozen_loss(scene, dI, params0, params1, seed=0, n_paths=1 << 10, max_depth=4, method=NAIVE, path_begin=0,
-                n_norm=0, mask=None, n_threads=0, rr_depth=0, rr_prob=1.0):
+                n_norm=0, mask=None, n_threads=0, rr_depth=0, rr_prob=1.0, filter=0):
     """<dI, I_s> with decisions frozen at params0=(albedo, Le, heights) and values at params1."""
     b = _Bound(scene)
     p0 = b.make_params(*params0)
     p1 = b.make_params(*params1)
     dI = np.ascontiguousarray(dI, dtype=np.float64)
     run = or_run(seed, path_begin, n_paths, n_norm or n_paths, max_depth, method, 0, _threads(n_threads),
-                 *_rr(rr_depth, rr_prob))
+                 *_rr(rr_depth, rr_prob), int(filter))
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     return float(lib().or_frozen_loss(C.byref(b.sc), C.byref(p0), C.byref(p1), C.byref(run), dI.ctypes.data,
                                       _ptr(m)))
@@ -227,6 +230,14 @@ def philox(key, ctr):
     o = np.zeros(4, dtype=np.uint32)
     lib().or_philox(int(key[0]), int(key[1]), c.ctypes.data, o.ctypes.data)
     return o
+
+
+def filter_taps(filter, W, H, ux, uy):
+    """(px, py, w) of the reconstruction filter's taps at film position (ux, uy)."""
+    px, py, w = np.zeros(9, dtype=np.int32), np.zeros(9, dtype=np.int32), np.zeros(9)
+    k = lib().or_filter_taps(int(filter), int(W), int(H), float(ux), float(uy), px.ctypes.data, py.ctypes.data,
+                             w.ctypes.data)
+    return px[:k], py[:k], w[:k]
 
 
 def uniforms(seed, n, d, s=0):

@@ -314,6 +314,7 @@ lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts
     return fail(LT_ERR_INVALID_ARG, "bvh_width must be 0, 2, 4 or 8");
   if (o->rr_depth < 0 || (o->rr_depth > 0 && !(o->rr_prob > 0.0f && o->rr_prob <= 1.0f)))
     return fail(LT_ERR_INVALID_ARG, "rr_depth must be >= 0 and rr_prob in (0, 1]");
+  if (o->filter != 0 && o->filter != 1) return fail(LT_ERR_INVALID_ARG, "filter must be 0 (tent) or 1 (Gaussian)");
   return LT_OK;
 }
 
@@ -336,6 +337,7 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.vstate = nullptr;
   k.rr_depth = o->rr_depth;
   k.rr_q = o->rr_prob;
+  k.filter = o->filter;
   return k;
 }
 

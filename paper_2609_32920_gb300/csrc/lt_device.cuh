@@ -602,6 +602,72 @@ __device__ __forceinline__ float3 adjoint_read(const float* dI, int W, int H, fl
   return Lb;
 }
 
+// Wider filter (filter 1): separable truncated Gaussian of standard deviation 0.5 pixel
+// over pixel centres, shifted down by its value at the radius 1.5 pixel so that it falls
+// continuously to zero, normalised to unit integral per axis:
+// g(d) = (exp(-2 d^2) - exp(-4.5)) / C, C = sqrt(pi/2) erf(1.5 sqrt(2)) - 3 exp(-4.5).
+// Up to three taps per axis; taps off the film are dropped.
+constexpr float kGaussInvC = 0.82196051292f;  // 1 / C
+constexpr float kGaussCut = 0.01110899654f;   // exp(-4.5)
+struct Axis3 {
+  int x[3];
+  float w[3], dw[3];  // weights and their derivatives along u
+  int n;
+};
+__device__ __forceinline__ Axis3 gauss_axis(float u, int extent) {
+  Axis3 a;
+  a.n = 0;
+  const int b = (int)floorf(u - 0.5f);
+#pragma unroll
+  for (int i = -1; i <= 2; ++i) {
+    const int X = b + i;
+    const float d = u - ((float)X + 0.5f);
+    if (fabsf(d) < 1.5f && X >= 0 && X < extent && a.n < 3) {
+      const float e = expf(-2.0f * d * d);
+      a.x[a.n] = X;
+      a.w[a.n] = (e - kGaussCut) * kGaussInvC;
+      a.dw[a.n] = -4.0f * d * e * kGaussInvC;
+      ++a.n;
+    }
+  }
+  return a;
+}
+
+// Splat and adjoint read with the chosen filter (0 tent, 1 Gaussian).
+__device__ __forceinline__ void splat_f(float* img, int W, int H, float ux, float uy, float3 L, int filter) {
+  if (filter == 0) {
+    splat(img, W, H, ux, uy, L);
+    return;
+  }
+  const Axis3 ax = gauss_axis(ux, W), ay = gauss_axis(uy, H);
+  for (int j = 0; j < ay.n; ++j)
+    for (int i = 0; i < ax.n; ++i) {
+      const float w = ax.w[i] * ay.w[j];
+      float* p = img + 3 * ((size_t)ay.x[j] * W + ax.x[i]);
+      atomicAdd(p + 0, w * L.x);
+      atomicAdd(p + 1, w * L.y);
+      atomicAdd(p + 2, w * L.z);
+    }
+}
+__device__ __forceinline__ float3 adjoint_read_f(const float* dI, int W, int H, float ux, float uy, float3 L,
+                                                 float2* q, int filter) {
+  if (filter == 0) return adjoint_read(dI, W, H, ux, uy, L, q);
+  const Axis3 ax = gauss_axis(ux, W), ay = gauss_axis(uy, H);
+  float3 Lb = f3(0, 0, 0);
+  float qx = 0.0f, qy = 0.0f;
+  for (int j = 0; j < ay.n; ++j)
+    for (int i = 0; i < ax.n; ++i) {
+      const float* p = dI + 3 * ((size_t)ay.x[j] * W + ax.x[i]);
+      const float3 v = f3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+      Lb = Lb + v * (ax.w[i] * ay.w[j]);
+      const float lv = dot(v, L);
+      qx += ax.dw[i] * ay.w[j] * lv;
+      qy += ax.w[i] * ay.dw[j] * lv;
+    }
+  if (q) *q = make_float2(qx, qy);
+  return Lb;
+}
+
 // ------------------------------------------------------------------ materials
 __device__ __forceinline__ float3 texel(const float* albedo, int idx) {
   return f3(__ldg(albedo + idx), __ldg(albedo + idx + 1), __ldg(albedo + idx + 2));

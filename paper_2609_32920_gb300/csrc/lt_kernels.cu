@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(128) k_collect(DevScene S, KParams kp, const f
         rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
         if (c.valid) {
           float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
-          float3 Lb = adjoint_read(dI, S.W, S.H, c.ux, c.uy, L, nullptr);
+          float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, nullptr, kp.filter);
           float3 P = mul(Lb, L);
           float lum = luminance(L);
           if (lum > 0.0f) {
@@ -864,7 +864,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
         float4* rec = (float4*)aux + 2 * p;
         float wgt = R >= 0 ? Om / wR : 0.0f;
         float3 Sh = LR * wgt;
-        if (active && R >= 0) splat(image, S.W, S.H, Rux, Ruy, Sh);
+        if (active && R >= 0) splat_f(image, S.W, S.H, Rux, Ruy, Sh, kp.filter);
         rec[0] = make_float4(__int_as_float(active ? R : -1), wgt, Rux, Ruy);
         rec[1] = make_float4(Sh.x, Sh.y, Sh.z, 0.0f);
       }
@@ -903,7 +903,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
               if (r.w < om / Om) { R = k; wR = om; LR = L; Rux = c.ux; Ruy = c.uy; }
             }
           } else {
-            splat(image, S.W, S.H, c.ux, c.uy, L);
+            splat_f(image, S.W, S.H, c.ux, c.uy, L, kp.filter);
           }
         }
       }
@@ -1093,7 +1093,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
           valid |= 1ull << k;
           ++nconn;
           float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
-          float3 Lb = adjoint_read(dI, S.W, S.H, c.ux, c.uy, L, nullptr);
+          float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, nullptr, kp.filter);
           dtot = dtot + mul(Lb, L);
         }
       }
@@ -1119,7 +1119,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         if ((valid >> k) & 1ull) {
           float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
           float2 q;
-          float3 Lb = adjoint_read(dI, S.W, S.H, c.ux, c.uy, L, att ? &q : nullptr);
+          float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, att ? &q : nullptr, kp.filter);
           float3 P = mul(Lb, L);
           wsplat = P;           // splat factor rho_k / pi (Eq. 15)
           rem = rem - P;        // Eq. 16
@@ -1200,7 +1200,7 @@ __device__ __forceinline__ void reslrb_path(const DevScene& S, const KParams& kp
   const uint64_t n = (uint64_t)(kp.path_offset + p);
   float3 Sh = f3(r1.x, r1.y, r1.z);
   float2 q;
-  float3 Lb = adjoint_read(dI, S.W, S.H, r0.z, r0.w, Sh, att ? &q : nullptr);
+  float3 Lb = adjoint_read_f(dI, S.W, S.H, r0.z, r0.w, Sh, att ? &q : nullptr, kp.filter);
   float3 P = mul(Lb, Sh);
   float lam = hsum(P);
   gLe = gLe + f3(P.x / Le.x, P.y / Le.y, P.z / Le.z);
@@ -1300,7 +1300,7 @@ __global__ void __launch_bounds__(128) k_lrb2_reduce(DevScene S, KParams kp, con
       const float4 a = r4[at];
       if (a.x < 0.0f) continue;
       const float3 L = f3(a.z, a.w, rz[at]);
-      dtot = dtot + mul(adjoint_read(dI, S.W, S.H, a.x, a.y, L, nullptr), L);
+      dtot = dtot + mul(adjoint_read_f(dI, S.W, S.H, a.x, a.y, L, nullptr, kp.filter), L);
       valid |= 1ull << k;
       ++nconn;
     }
@@ -1356,7 +1356,7 @@ __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const flo
         rho = tex_lookup(kp.albedo, m, t0.y, t0.z, &foot);
         float3 L = f3(t1.x, t1.y, t1.z);
         if (fl & 8u) {
-          float3 Lb = adjoint_read(dI, S.W, S.H, t0.w, t1.w, L, ATT ? &q : nullptr);
+          float3 Lb = adjoint_read_f(dI, S.W, S.H, t0.w, t1.w, L, ATT ? &q : nullptr, kp.filter);
           P3 = mul(Lb, L);
         }
         scatter_albedo(g.d_albedo, foot, P3 + acc, rho);

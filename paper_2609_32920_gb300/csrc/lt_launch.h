@@ -28,6 +28,7 @@ struct KParams {
                                // connection-validity mask (or null)
   int rr_depth;                // Russian roulette after vertices of depth >= rr_depth (0: off)
   float rr_q;                  // survival probability of the roulette
+  int filter;                  // reconstruction filter: 0 tent, 1 truncated Gaussian
 };
 
 struct GradPtrs {

@@ -419,3 +419,31 @@ def test_russian_roulette_matches_oracle(boxhm, slab, method):
         S.sync_status()
         assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
         assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+
+
+@pytest.mark.parametrize("method", ["lrb3", "reslrb"])
+def test_gaussian_filter_matches_oracle(boxhm, slab, method):
+    """The wider (Gaussian) reconstruction filter in splat and adjoint read, including the
+    splat-position derivative of the attached gradients, agrees with the oracle."""
+    for (sc, S), seed in ((boxhm, 91), (slab, 92)):
+        n, D = 1 << 13, 6
+        mask = agree_mask(S, sc, seed, n, D, max_divergent=2e-3)
+        dI_np = I.smooth_adjoint(sc.W, sc.H, seed)
+        dI = t32(dI_np)
+        o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, mask=_dev_mask(mask), filter=1)
+        if method == "lrb3":
+            img = S.primal(o).cpu().numpy()
+            ref_img = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, filter=1)
+            mass = O.render(sc, seed=seed, n_paths=n, max_depth=D, mask=mask, estimator=2, filter=1)
+            assert primal_close(img, ref_img, mass=mass, W=max(sc.W, sc.H)).all()
+            gA, gL, gH = S.backward_lrb3(o, dI)
+            ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, mask=mask, filter=1)
+        else:
+            rec = torch.zeros((n, 8), device="cuda")
+            S.primal(o, estimator=lt.EST_RESLRB, aux=rec)
+            gA, gL, gH = S.backward_reslrb(o, dI, rec)
+            ref = O.gradient(sc, dI_np, seed=seed, n_paths=n, max_depth=D, attached=1, method=O.RESLRB_AD,
+                             mask=mask, filter=1)
+        S.sync_status()
+        assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
+        assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3

@@ -41,6 +41,10 @@ MUTANTS = {
     "rr_no_weight": ("if (rand4(seed, n, (uint32_t)d, 2).u[0] < rr_q) P.v.back().rr = 1.0 / rr_q;",
                      "if (rand4(seed, n, (uint32_t)d, 2).u[0] < rr_q) P.v.back().rr = 1.0;",
                      ["test_russian_roulette_unbiased_and_exact"]),
+    # Gaussian filter without the cut at the radius (weights jump to zero there)
+    "gauss_no_cut": ("const double inv_c = 1.0 / gauss_norm(), cut = std::exp(-4.5);",
+                     "const double inv_c = 1.0 / gauss_norm(), cut = 0.0;",
+                     ["test_gaussian_filter_definition_and_flux"]),
     # attached slide: intersection parameter with the wrong sign
     "slide_sign": ("T tt = dot(o - xprev, n) / dot(din, n);", "T tt = dot(xprev - o, n) / dot(din, n);",
                    ["test_attached_height_gradient_vs_frozen_central_differences"]),

@@ -357,6 +357,51 @@ def test_russian_roulette_unbiased_and_exact(oracle):
         assert g["d_albedo"][k] == pytest.approx(fd, rel=1e-7, abs=1e-14)
 
 
+# ------------------------------------------------------------------ reconstruction filters
+def test_gaussian_filter_definition_and_flux(oracle):
+    """The wider (Gaussian) filter: nonnegative, symmetric, falling continuously to zero at
+    the 1.5-pixel radius, and of unit integral, so its lattice sum averages to one over
+    film positions (as the tent's is one everywhere); an image's total flux is therefore
+    the tent image's up to the lattice ripple, and attached derivatives through the filter
+    stay exact (central differences of the frozen function)."""
+    rng = np.random.default_rng(0)
+    sums = []
+    for ux, uy in rng.uniform(20, 40, size=(4000, 2)):
+        px, py, w = oracle.filter_taps(1, 64, 64, ux, uy)
+        assert len(w) <= 9 and np.all(w >= 0)
+        sums.append(w.sum())
+        tpx, tpy, tw = oracle.filter_taps(0, 64, 64, ux, uy)
+        assert tw.sum() == pytest.approx(1.0, abs=1e-12)
+    assert np.mean(sums) == pytest.approx(1.0, abs=2e-3)
+    assert np.std(sums) < 0.05
+    # symmetry and continuity at the radius: a tap entering at distance 1.5 has weight ~0
+    _, _, wa = oracle.filter_taps(1, 64, 64, 30.5 + 0.3, 30.5)
+    _, _, wb = oracle.filter_taps(1, 64, 64, 30.5 - 0.3, 30.5)
+    assert np.allclose(np.sort(wa), np.sort(wb), atol=1e-15)
+    _, _, we = oracle.filter_taps(1, 64, 64, 30.5 + 1.5 - 1e-9, 30.5)
+    assert we.min() < 1e-7
+    sc = I.box_scene(20)
+    kw = dict(seed=3, n_paths=1 << 14, max_depth=4)
+    flux_t = oracle.render(sc, **kw).sum()
+    flux_g = oracle.render(sc, filter=1, **kw).sum()
+    # the wider filter loses a little more at the film border (taps off the film drop)
+    assert flux_g == pytest.approx(flux_t, rel=1e-2) and flux_g <= flux_t
+    hsc = I.box_scene(16, heightmap=4, hm_std=0.04)
+    dI = I.smooth_adjoint(hsc.W, hsc.H, 12)
+    kw = dict(seed=4, n_paths=1 << 9, max_depth=4, filter=1)
+    g = oracle.gradient(hsc, dI, attached=1, **kw)
+    h0 = hsc.heights.copy()
+    for k in np.argsort(-np.abs(g["d_heights"]))[:3]:
+        e = 1e-5
+        hp, hm = h0.copy(), h0.copy()
+        hp[k] += e
+        hm[k] -= e
+        p0 = (hsc.albedo, hsc.Le, h0)
+        fd = (_loss_fd(oracle, hsc, dI, p0, (hsc.albedo, hsc.Le, hp), **kw)
+              - _loss_fd(oracle, hsc, dI, p0, (hsc.albedo, hsc.Le, hm), **kw)) / (2 * e)
+        assert g["d_heights"][k] == pytest.approx(fd, rel=2e-5, abs=1e-12)
+
+
 # ------------------------------------------------------------------ learned target MLP
 def _mlp_params(seed=0):
     rng = np.random.default_rng(seed)
