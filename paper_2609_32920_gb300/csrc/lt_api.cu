@@ -341,13 +341,15 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   return k;
 }
 
-// Gradients accumulate per block in shared memory when both parameter arrays fit in the
-// default 48 KB shared-memory limit (46 KB, leaving room for static shared memory).
+// Gradients accumulate per block in shared memory for each parameter array that fits in
+// the default 48 KB shared-memory limit (46 KB, leaving room for static shared memory):
+// the albedo array first (usually small and hit by every diffuse vertex), then the
+// heights if room remains; an array that does not fit goes to global memory directly.
 void set_privatization(const lt_scene* s, const lt_grads* g, KParams& kp) {
-  kp.n_alb = s->n_albedo;
-  kp.n_h = s->n_heights;
-  int n = (g && g->d_albedo ? s->n_albedo : 0) + (g && g->d_heights ? s->n_heights : 0);
-  kp.priv_n = (n > 0 && (size_t)(s->n_albedo + s->n_heights) * sizeof(float) <= 46 * 1024) ? s->n_albedo + s->n_heights : 0;
+  const int budget = (46 * 1024) / (int)sizeof(float);
+  kp.n_alb = (g && g->d_albedo && s->n_albedo > 0 && s->n_albedo <= budget) ? s->n_albedo : 0;
+  kp.n_h = (g && g->d_heights && s->n_heights > 0 && s->n_heights <= budget - kp.n_alb) ? s->n_heights : 0;
+  kp.priv_n = kp.n_alb + kp.n_h;
 }
 
 lt_status prep_grads(const lt_scene* s, const lt_grads* g, cudaStream_t st, GradPtrs& gp) {

@@ -229,10 +229,11 @@ __device__ __forceinline__ void block_add3(float* dst, float3 v) {
   }
 }
 
-// Gradient sink of a block: when the parameter arrays fit in shared memory each block
-// accumulates its gradients there (shared-memory atomics) and adds them to the global
-// arrays once at the end; the albedo and height arrays are small and every path touches
-// them, so global atomics on them contend heavily.
+// Gradient sink of a block: each parameter array that fits in shared memory (the host
+// decides per array) is accumulated there by the block (shared-memory atomics) and added to
+// the global array once at the end; the albedo and height arrays are small and every path
+// touches them, so global atomics on them contend heavily (a one-texel albedo would send
+// every vertex's gradient to the same three addresses).
 struct Sink {
   float* alb;
   float* h;
@@ -244,8 +245,8 @@ __device__ __forceinline__ Sink sink_begin(const KParams& kp, const GradPtrs& g,
   if (kp.priv_n > 0) {
     for (int i = threadIdx.x; i < kp.priv_n; i += blockDim.x) sh[i] = 0.0f;
     __syncthreads();
-    if (g.d_albedo) s.alb = sh;
-    if (g.d_heights) s.h = sh + kp.n_alb;
+    if (g.d_albedo && kp.n_alb > 0) s.alb = sh;
+    if (g.d_heights && kp.n_h > 0) s.h = sh + kp.n_alb;
   }
   return s;
 }

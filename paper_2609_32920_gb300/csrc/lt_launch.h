@@ -21,8 +21,9 @@ struct KParams {
   float* dbg;                // DEVICE [n_paths][4] or null
   size_t tape_offset;        // naive tape: bytes before the first record
   unsigned long long* census;  // DEVICE [5] or null: rays, box tests, primitive tests, vertices, connections
-  int n_alb, n_h;              // parameter counts
-  int priv_n;                  // > 0: gradients accumulate in n_alb + n_h floats of shared memory per block
+  int n_alb, n_h;              // albedo / height gradients accumulated in shared memory per block
+                               // (array lengths, or 0: that array goes to global memory directly)
+  int priv_n;                  // n_alb + n_h: floats of dynamic shared memory per block
   const float* mlp;            // learned reservoir target parameters (DEVICE) or null (luminance)
   void* vstate;                // plain primal: LRB-3 per-path state that receives each path's
                                // connection-validity mask (or null)
