@@ -849,6 +849,10 @@ struct lt_batch {
   int64_t n_chunks[4] = {};   // whole batch
   int64_t split[4] = {};      // first chunk of the chain group
   unsigned long long* d_ticket = nullptr;  // [4 passes][3 launches]
+  // pass-3 spans of the lean and the specular-chain group, and the gradient-sink size
+  BatchSpan* d_spans[2] = {};
+  int n_spans[2] = {};
+  size_t span_smem = 0;
   cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams (main, second branch)
   cudaEvent_t fork = nullptr, join = nullptr;
   lt_batch_config cfg{128, 4, 0, 4};
@@ -872,6 +876,7 @@ void free_batch(lt_batch* b) {
   if (!b) return;
   drop_graphs(b);
   for (auto* j : b->d_jobs) cudaFree(j);
+  for (auto* sp : b->d_spans) cudaFree(sp);
   cudaFree(b->d_ticket);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->cap2) cudaStreamDestroy(b->cap2);
@@ -896,8 +901,9 @@ int kernel_pass(int pass) {
          : pass == LT_PASS_LRB3 ? BPASS_LRB3 : BPASS_RESLRB;
 }
 
-// One persistent launch over the items [j0, j1) of the table: kernel `kpass` (BatchPass),
-// queue ticket `slot` of its pass.
+// One persistent launch over the items [j0, j1) of the table: kernel `kpass` (BatchPass,
+// or kSpanPass: pass 3 over the group's spans), queue ticket `slot` of its pass.
+constexpr int kSpanPass = 100;
 struct GroupLaunch {
   int j0 = 0, j1 = 0;
   int64_t c0 = 0, c1 = 0;  // chunk range
@@ -917,8 +923,8 @@ std::vector<GroupLaunch> plan_pass(const lt_batch* b, int pass) {
   } else if (pass == LT_PASS_LRB3 && b->all_state) {
     const int p2 = b->mask_ready ? BPASS_LRB3_P2_MASK : BPASS_LRB3_P2;
     out.push_back(GroupLaunch{0, n, 0, b->n_chunks[slot], false, false, p2, 2, 0});
-    out.push_back(GroupLaunch{0, b->n_lean, 0, b->split[slot], b->att_lean, false, BPASS_LRB3_P3, 0, 0});
-    out.push_back(GroupLaunch{b->n_lean, n, b->split[slot], b->n_chunks[slot], true, true, BPASS_LRB3_P3, 1, 0});
+    out.push_back(GroupLaunch{0, b->n_lean, 0, b->n_spans[0], b->att_lean, false, kSpanPass, 0, 0});
+    out.push_back(GroupLaunch{b->n_lean, n, 0, b->n_spans[1], true, true, kSpanPass, 1, 0});
   } else {
     out.push_back(GroupLaunch{0, b->n_lean, 0, b->split[slot], b->att_lean, false, kp, 0, 0});
     out.push_back(GroupLaunch{b->n_lean, n, b->split[slot], b->n_chunks[slot], true, true, kp, 1, 0});
@@ -926,8 +932,9 @@ std::vector<GroupLaunch> plan_pass(const lt_batch* b, int pass) {
   std::vector<GroupLaunch> keep;
   for (GroupLaunch& g : out) {
     if (g.c1 <= g.c0) continue;
-    g.per_sm = b->cfg.blocks_per_sm > 0
-                   ? b->cfg.blocks_per_sm
+    g.per_sm = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm
+               : g.kpass == kSpanPass
+                   ? batch_spans_occupancy(b->cfg.bvh_width, g.att, g.chains, b->cfg.block_size, b->span_smem)
                    : batch_occupancy(b->cfg.bvh_width, g.kpass, g.att, g.chains, b->cfg.block_size);
     keep.push_back(g);
   }
@@ -938,6 +945,15 @@ lt_status launch_group(lt_batch* b, int pass, const GroupLaunch& g, cudaStream_t
   unsigned long long* ticket = b->d_ticket + 3 * pass + g.slot;
   LT_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st));
   const int block = b->cfg.block_size;
+  if (g.kpass == kSpanPass) {
+    // a resident grid, but no more blocks than spans
+    const int64_t grid = std::min<int64_t>((int64_t)b->sms * g.per_sm, g.c1);
+    cudaError_t e = launch_batch_spans(b->cfg.bvh_width, g.att, g.chains, b->d_jobs[table_of(b->cfg)],
+                                       b->d_spans[g.slot], (int)g.c1, ticket, block,
+                                       (int)std::max<int64_t>(grid, 1), b->span_smem, st);
+    if (e) return fail(LT_ERR_CUDA, std::string("batched pass 3: ") + cudaGetErrorString(e));
+    return LT_OK;
+  }
   // a resident grid, but no more warps than chunks
   const int64_t nch = g.c1 - g.c0;
   const int64_t warps_per_block = block / 32;
@@ -1084,6 +1100,8 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     J.rec = it.records;
     J.state = it.opts.lrb3_state;
     J.kp.vstate = it.opts.lrb3_state;  // the batched plain primal stores validity masks there
+    set_privatization(it.scene, &it.grads, J.kp);  // used by pass 3 over spans only
+    b->span_smem = std::max(b->span_smem, sizeof(float) * (size_t)J.kp.priv_n);
     J.att = it.opts.attached != 0;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -1108,6 +1126,22 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
     }
   }
   LT_CUDA(cudaMalloc(&b->d_ticket, 12 * sizeof(unsigned long long)));
+  // pass-3 spans: each group's items cut into spans of at most kSpan paths
+  const int64_t kSpan = 16384;
+  for (int grp = 0; grp < 2; ++grp) {
+    std::vector<BatchSpan> spans;
+    const int j0 = grp == 0 ? 0 : b->n_lean, j1 = grp == 0 ? b->n_lean : n;
+    for (int j = j0; j < j1; ++j)
+      for (int64_t a = 0; a < jobs[j].kp.n_paths; a += kSpan)
+        spans.push_back(BatchSpan{j, a, std::min<int64_t>(a + kSpan, jobs[j].kp.n_paths)});
+    b->n_spans[grp] = (int)spans.size();
+    if (!spans.empty()) {
+      LT_CUDA(cudaMalloc(&b->d_spans[grp], sizeof(BatchSpan) * spans.size()));
+      LT_CUDA(cudaMemcpyAsync(b->d_spans[grp], spans.data(), sizeof(BatchSpan) * spans.size(),
+                              cudaMemcpyHostToDevice, st));
+      LT_CUDA(cudaStreamSynchronize(st));
+    }
+  }
   LT_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   LT_CUDA(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
   LT_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));

@@ -36,6 +36,14 @@ struct BatchArgs {
   unsigned long long* ticket;
 };
 
+// A span of one item's paths [start, end), handed to one block at a time (LRB-3 pass 3 of a
+// batch: the block accumulates the item's parameter gradients in shared memory as the
+// single-scene kernels do, and adds them to the item's arrays when the span is done).
+struct BatchSpan {
+  int job;
+  int64_t start, end;
+};
+
 // Kernel of a batched launch: the fused LRB-3 kernel, or its two-kernel form (pass 2,
 // with or without the primal's validity masks, then pass 3).
 enum BatchPass {
@@ -54,12 +62,21 @@ enum BatchPass {
   cudaError_t launch_batch(int pass, bool att, bool chains, const BatchArgs& a, int block, int grid,       \
                            cudaStream_t st);                                                               \
   /* resident blocks per SM of the pass's kernel at `block` threads (0 on error) */                        \
-  int batch_occupancy(int pass, bool att, bool chains, int block);
+  int batch_occupancy(int pass, bool att, bool chains, int block);                                         \
+  /* LRB-3 pass 3 over spans (see BatchSpan), `smem` bytes of gradient sink per block */                   \
+  cudaError_t launch_batch_spans(bool att, bool chains, const BatchJob* jobs, const BatchSpan* spans,      \
+                                 int n_spans, unsigned long long* ticket, int block, int grid, size_t smem, \
+                                 cudaStream_t st);                                                         \
+  int batch_spans_occupancy(bool att, bool chains, int block, size_t smem);
 namespace w2 { LT_BATCH_LAUNCHERS }
 namespace w4 { LT_BATCH_LAUNCHERS }
 namespace w8 { LT_BATCH_LAUNCHERS }
 cudaError_t launch_batch(int width, int pass, bool att, bool chains, const BatchArgs& a, int block, int grid,
                          cudaStream_t st);
 int batch_occupancy(int width, int pass, bool att, bool chains, int block);
+cudaError_t launch_batch_spans(int width, bool att, bool chains, const BatchJob* jobs, const BatchSpan* spans,
+                               int n_spans, unsigned long long* ticket, int block, int grid, size_t smem,
+                               cudaStream_t st);
+int batch_spans_occupancy(int width, bool att, bool chains, int block, size_t smem);
 
 }  // namespace lt

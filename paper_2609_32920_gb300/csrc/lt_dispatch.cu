@@ -56,4 +56,14 @@ int batch_occupancy(int width, int pass, bool att, bool chains, int block) {
   return LT_BY_WIDTH(width, batch_occupancy(pass, att, chains, block));
 }
 
+cudaError_t launch_batch_spans(int width, bool att, bool chains, const BatchJob* jobs, const BatchSpan* spans,
+                               int n_spans, unsigned long long* ticket, int block, int grid, size_t smem,
+                               cudaStream_t st) {
+  return LT_BY_WIDTH(width, launch_batch_spans(att, chains, jobs, spans, n_spans, ticket, block, grid, smem, st));
+}
+
+int batch_spans_occupancy(int width, bool att, bool chains, int block, size_t smem) {
+  return LT_BY_WIDTH(width, batch_spans_occupancy(att, chains, block, smem));
+}
+
 }  // namespace lt

@@ -692,6 +692,14 @@ struct Dispenser {
     next = min(wid * per, n_paths);
     end = min(next + per, n_paths);
   }
+  // The block alone works on [0, n_paths): contiguous ranges of its warps.
+  __device__ __forceinline__ void init_local(int64_t n_paths) {
+    const int64_t warps = blockDim.x >> 5;
+    const int64_t wid = threadIdx.x >> 5;
+    const int64_t per = (n_paths + warps - 1) / warps;
+    next = min(wid * per, n_paths);
+    end = min(next + per, n_paths);
+  }
   // Lanes with `want` receive a path index, or -1 when the warp's range is exhausted.
   __device__ __forceinline__ int64_t take(bool want) {
     const unsigned m = __ballot_sync(0xffffffffu, want);
@@ -954,7 +962,8 @@ __global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
 // pass 3 only, starting from that state (paths without a valid connection are skipped).
 // MK (MODE 1): the primal stored each path's validity mask in xrec/xhi, so pass 2 takes
 // connection validity from it and traces no visibility rays.
-template <bool ATT, bool ST, bool CH, bool BATCH, int MODE = 0, bool MK = false>
+// LOCAL: the calling block alone works on the path range (a span of a batch item).
+template <bool ATT, bool ST, bool CH, bool BATCH, int MODE = 0, bool MK = false, bool LOCAL = false>
 __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0, const float* __restrict__ dI0,
                                           const GradPtrs& g0, const BatchArgs& ba, float4* xrec = nullptr,
                                           uint32_t* xhi = nullptr) {
@@ -971,7 +980,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   uint32_t nverts = 0, nconns = 0;
   Dispenser disp;
   BatchDispenser bdisp;
-  if (BATCH) bdisp.init(); else disp.init(kp0.n_paths);
+  if (BATCH) bdisp.init(); else if (LOCAL) disp.init_local(kp0.n_paths); else disp.init(kp0.n_paths);
   int jb = 0;
   enum { IDLE = 0, PASS2 = 1, PASS3 = 2 };
   int phase = IDLE, k = 0, last = 0, nconn = 0;
@@ -1177,6 +1186,37 @@ __global__ void __launch_bounds__(256) k_lrb3_p2_batch(BatchArgs ba) {
 template <bool ATT, bool CH>
 __global__ void __launch_bounds__(256) k_lrb3_p3_batch(BatchArgs ba) {
   lrb3_body<ATT, false, CH, true, 2>(ba.jobs[0].S, ba.jobs[0].kp, nullptr, ba.jobs[0].g, ba);
+}
+
+// Batched pass 3 by spans: a block takes the next span (one atomic by its first thread),
+// runs the single-scene pass-3 body over it with the item's shared-memory gradient sink,
+// and flushes the sink into the item's arrays at the end of the span.
+template <bool ATT, bool CH>
+__global__ void __launch_bounds__(256) k_lrb3_p3_spans(const BatchJob* __restrict__ jobs,
+                                                       const BatchSpan* __restrict__ spans, int n_spans,
+                                                       unsigned long long* ticket) {
+  __shared__ int s_span;
+  while (true) {
+    if (threadIdx.x == 0) s_span = (int)atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int sp = s_span;
+    __syncthreads();
+    if (sp >= n_spans) break;
+    const BatchSpan span = spans[sp];
+    const BatchJob& J = jobs[span.job];
+    KParams kp = J.kp;
+    kp.path_offset += span.start;
+    kp.n_paths = span.end - span.start;
+    if (kp.mask) kp.mask += span.start;
+    if (kp.dbg) kp.dbg += 4 * span.start;
+    float4* xr = (float4*)J.state + span.start;
+    uint32_t* xh = (uint32_t*)((char*)J.state + lrb3_state_split(J.kp.n_paths)) + span.start;
+    GradPtrs g = J.g;
+    g.d_Le = nullptr;  // pass 2 added the emitted-radiance gradient
+    const bool att = ATT && J.att;
+    if (att) lrb3_body<ATT, false, CH, false, 2, false, true>(J.S, kp, J.dI, g, BatchArgs{}, xr, xh);
+    else lrb3_body<false, false, false, false, 2, false, true>(J.S, kp, J.dI, g, BatchArgs{}, xr, xh);
+  }
 }
 
 template <bool ATT, bool CH>
@@ -1594,6 +1634,23 @@ cudaError_t launch_batch(int pass, bool att, bool chains, const BatchArgs& a, in
   LT_BATCH_DISPATCH(LT_LAUNCH_ONE)
 #undef LT_LAUNCH_ONE
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_spans(bool att, bool chains, const BatchJob* jobs, const BatchSpan* spans, int n_spans,
+                               unsigned long long* ticket, int block, int grid, size_t smem, cudaStream_t st) {
+  if (att && chains) k_lrb3_p3_spans<true, true><<<grid, block, smem, st>>>(jobs, spans, n_spans, ticket);
+  else if (att) k_lrb3_p3_spans<true, false><<<grid, block, smem, st>>>(jobs, spans, n_spans, ticket);
+  else k_lrb3_p3_spans<false, false><<<grid, block, smem, st>>>(jobs, spans, n_spans, ticket);
+  return cudaGetLastError();
+}
+
+int batch_spans_occupancy(bool att, bool chains, int block, size_t smem) {
+  int n = 0;
+  cudaError_t e;
+  if (att && chains) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lrb3_p3_spans<true, true>, block, smem);
+  else if (att) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lrb3_p3_spans<true, false>, block, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lrb3_p3_spans<false, false>, block, smem);
+  return e == cudaSuccess ? n : 0;
 }
 
 int batch_occupancy(int pass, bool att, bool chains, int block) {
