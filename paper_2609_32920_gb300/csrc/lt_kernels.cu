@@ -375,6 +375,54 @@ struct ChainState {
   bool refl;
 };
 
+// Vertex states of the chains the forward walk has just passed through, so that a chain's
+// reverse sweep reads them instead of replaying the chain (its traces run on the few lanes
+// that finish a chain at that step).  Two records, the current chain and the one before
+// (a position adjoint continues into it when the current chain's anchor ends it), of at
+// most kChainCache vertices each; a longer or older chain is replayed as before.  The
+// states are the ones the replay would compute, from the same arithmetic.
+constexpr int kChainCache = 4;
+struct ChainRec {
+  ChainInfo info;
+  int len;  // recorded specular vertices info.ka .. info.ka+len-1; -1: not usable
+  int prim[kChainCache];
+  float3 x[kChainCache], din[kChainCache];
+  unsigned refl;  // bit i: vertex info.ka+i took the reflected branch
+};
+struct ChainCache {
+  ChainRec r[2];
+  int cur;
+  __device__ __forceinline__ void reset() {
+    r[0].len = r[1].len = -1;
+    cur = 0;
+  }
+  // Specular vertex k reached along din (before scattering); an attached one starts `chain`.
+  __device__ __forceinline__ void record(const ChainInfo& chain, int k, const Vtx& v, float3 din) {
+    if (v.attached) {
+      cur ^= 1;
+      r[cur].info = chain;
+      r[cur].len = 0;
+      r[cur].refl = 0u;
+    }
+    ChainRec& c = r[cur];
+    if (c.len < 0) return;
+    if (c.len >= kChainCache || c.info.ka + c.len != k) {
+      c.len = -1;
+      return;
+    }
+    c.prim[c.len] = v.prim;
+    c.x[c.len] = v.x;
+    c.din[c.len] = din;
+  }
+  // Its branch, once the walk has scattered.
+  __device__ __forceinline__ void record_branch(bool refl) {
+    ChainRec& c = r[cur];
+    if (c.len < 0 || c.len >= kChainCache) return;
+    c.refl |= (refl ? 1u : 0u) << c.len;
+    ++c.len;
+  }
+};
+
 // Replay the chain from its start to vertex j (a <= j) and trace the ray leaving j.  The
 // chain's first direction is the one the walk sampled at the anchor (the emitter's
 // cosine sample, or the diffuse anchor's, on the side of its normal that faces the chain
@@ -465,13 +513,31 @@ __device__ __forceinline__ void spec_adjoint(const ChainState& s, float3 gdout, 
 // contributions of every primitive the chain touches and returns the adjoint of the
 // anchor position (through the chain start's incoming direction).
 __device__ __noinline__ float3 chain_reverse(const DevScene& S, const KParams& kp, uint64_t n, const ChainInfo& c,
-                                             int kt, float3 gx_t, float* dh) {
+                                             int kt, float3 gx_t, float* dh, const ChainCache* cc, int prim_t) {
+  const ChainRec* rec = nullptr;
+  if (cc)
+    for (int b = 0; b < 2; ++b)
+      if (cc->r[b].len > 0 && cc->r[b].info.ka == c.ka && cc->r[b].info.ka + cc->r[b].len == kt) rec = &cc->r[b];
   float3 gx = gx_t, gd = f3(0, 0, 0);
   for (int j = kt - 1; j >= c.ka; --j) {
     ChainState s;
-    HitRec h;
-    if (!chain_replay(S, kp, n, c, j, s, h)) { set_err(S, ERR_BOUNDS); return f3(0, 0, 0); }
-    Prim Q = load_prim(S, h.prim);
+    int hprim;
+    if (rec) {
+      const int i = j - c.ka;
+      s.prim = rec->prim[i];
+      s.x = rec->x[i];
+      s.din = rec->din[i];
+      const Prim P = load_prim(S, s.prim);
+      s.nraw = cross(P.e1, P.e2);
+      s.D = dielectric(s.din, normalize(s.nraw), __ldg(S.mat_ior + P.mat));
+      s.refl = (rec->refl >> i) & 1u;
+      hprim = j + 1 < kt ? rec->prim[i + 1] : prim_t;
+    } else {
+      HitRec h;
+      if (!chain_replay(S, kp, n, c, j, s, h)) { set_err(S, ERR_BOUNDS); return f3(0, 0, 0); }
+      hprim = h.prim;
+    }
+    Prim Q = load_prim(S, hprim);
     float3 m = cross(Q.e1, Q.e2);
     float3 dout = s.refl ? s.D.refl : s.D.refr;
     // x_{j+1} = x_j + tau d_out, tau = ((o' - x_j).m) / (d_out.m)
@@ -484,7 +550,7 @@ __device__ __noinline__ float3 chain_reverse(const DevScene& S, const KParams& k
     float3 go = m * ga;
     float3 gm = (Q.o - s.x) * ga + dout * gb;
     gdout = gdout + m * gb;
-    scatter_heights(S, dh, h.prim, 0.0f, 0.0f, go, gm);  // plane of the next primitive
+    scatter_heights(S, dh, hprim, 0.0f, 0.0f, go, gm);  // plane of the next primitive
     float3 gdin, gnraw;
     spec_adjoint(s, gdout, c.lam, gdin, gnraw);
     if (j > c.ka) {
@@ -539,16 +605,24 @@ __device__ __noinline__ bool replay_chain_of(const DevScene& S, const KParams& k
 // continuing through earlier chains while the anchor is itself sliding (those chains'
 // Fresnel factors were already counted, so they are re-traversed with zero weight).
 __device__ __noinline__ void propagate_sliding(const DevScene& S, const KParams& kp, uint64_t n, ChainInfo c, int kt,
-                                               float3 gx, float* dh) {
+                                               float3 gx, float* dh, const ChainCache* cc, int prim_t) {
   for (int guard = 0; guard < kMaxDepth; ++guard) {
-    float3 g_anchor = chain_reverse(S, kp, n, c, kt, gx, dh);
+    float3 g_anchor = chain_reverse(S, kp, n, c, kt, gx, dh, cc, prim_t);
     if (c.kanchor < 0) return;  // the emitter does not move
     if (!c.anchor_sliding) {
       scatter_heights(S, dh, c.prim_p, c.bp1, c.bp2, g_anchor, f3(0, 0, 0));
       return;
     }
     ChainInfo prev;
-    if (!replay_chain_of(S, kp, n, c.kanchor, prev)) { set_err(S, ERR_BOUNDS); return; }
+    bool found = false;
+    if (cc)
+      for (int b = 0; b < 2; ++b)
+        if (cc->r[b].len > 0 && cc->r[b].info.ka < c.ka && cc->r[b].info.ka + cc->r[b].len == c.kanchor) {
+          prev = cc->r[b].info;
+          found = true;
+        }
+    if (!found && !replay_chain_of(S, kp, n, c.kanchor, prev)) { set_err(S, ERR_BOUNDS); return; }
+    prim_t = c.prim_p;
     kt = c.kanchor;
     gx = g_anchor;
     c = prev;
@@ -582,13 +656,13 @@ __device__ __forceinline__ float3 tex_pos_adjoint(const float* albedo, int4 m, c
 // coordinates, sliding ones run the chain's reverse sweep (their normal is explicit).
 template <bool CH>
 __device__ __forceinline__ void pend_flush(const DevScene& S, const KParams& kp, uint64_t n, const PendAdj& p,
-                                           float* dh) {
+                                           float* dh, const ChainCache* cc) {
   if (!dh || p.prim < 0) return;
   if (!CH || !p.sliding) {
     scatter_heights(S, dh, p.prim, p.b1, p.b2, p.gx, p.gn);
   } else {
     scatter_heights(S, dh, p.prim, 0.0f, 0.0f, f3(0, 0, 0), p.gn);
-    propagate_sliding(S, kp, n, p.chain, p.k, p.gx, dh);
+    propagate_sliding(S, kp, n, p.chain, p.k, p.gx, dh, cc, p.prim);
   }
 }
 
@@ -600,12 +674,12 @@ __device__ __forceinline__ void pend_flush(const DevScene& S, const KParams& kp,
 template <bool CH>
 __device__ __forceinline__ void att_enter(const DevScene& S, const KParams& kp, uint64_t n, int k, const Vtx& v,
                                           float lam_seg, float lam_chain, PendAdj& pv, ChainInfo& chain,
-                                          float* dh) {
+                                          float* dh, const ChainCache* cc) {
   if (!CH || v.attached) {
     PendAdj cur;
     pend_init(cur, v.prim, k, v.b1, v.b2, v.x, v.nraw);
     seg_adjoint(pv.x, pv.nr, v.x, v.nraw, lam_seg, pv.gx, pv.gn, cur.gx, cur.gn);
-    pend_flush<CH>(S, kp, n, pv, dh);
+    pend_flush<CH>(S, kp, n, pv, dh, cc);
     if (CH && !v.diffuse) {
       chain = chain_at(pv, k, v, lam_chain);
       scatter_heights(S, dh, v.prim, v.b1, v.b2, cur.gx, cur.gn);
@@ -993,6 +1067,8 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   ChainInfo chain;
   chain.ka = -1;
   pv.prim = -1;
+  ChainCache cc;
+  cc.reset();
   while (true) {
     const bool want = more && phase == IDLE;
     int jnew = jb;
@@ -1029,6 +1105,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
           valid = vm;
           pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
           chain.ka = -1;
+          if (CH) cc.reset();
           last = 63 - __clzll((long long)valid);
           k = 0;
           phase = PASS3;
@@ -1085,6 +1162,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
           rem = dtot;
           pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
           chain.ka = -1;
+          if (CH) cc.reset();
           last = 63 - __clzll((long long)valid);
           k = 0;
           phase = PASS3;
@@ -1112,7 +1190,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       ++k;
     } else if (MODE != 1) {
       if (!alive) {
-        if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights);
+        if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights, &cc);
         phase = IDLE;
         continue;
       }
@@ -1120,7 +1198,9 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
       // attached segment weight and chain bookkeeping: every connection from here on
       // carries this vertex's factors, so they weigh the remaining adjoint before Eq. 16
-      if (att) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights);
+      if (att) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights, &cc);
+      const bool rec_chain = CH && att && !v.diffuse;
+      if (rec_chain) cc.record(chain, k, v, w.dir);
       float3 rho = f3(0, 0, 0);
       if (v.diffuse) {
         TexFoot foot;
@@ -1139,7 +1219,8 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         if (att && CH && !v.attached)
           pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
       }
-      walk_scatter(S, w, v, ns, rho, r);
+      const bool refl = walk_scatter(S, w, v, ns, rho, r);
+      if (rec_chain) cc.record_branch(refl);
       walk_rr(kp, n, k, w);
       ++k;
     }
@@ -1252,11 +1333,15 @@ __device__ __forceinline__ void reslrb_path(const DevScene& S, const KParams& kp
   pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
   ChainInfo chain;
   chain.ka = -1;
+  ChainCache cc;
+  cc.reset();
   for (int k = 0; k <= R; ++k) {
     Vtx v;
     if (!walk_hit(S, w, v)) { set_err(S, ERR_BOUNDS); break; }
     float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
-    if (att) att_enter<CH>(S, kp, n, k, v, lam, lam, pv, chain, g.d_heights);
+    if (att) att_enter<CH>(S, kp, n, k, v, lam, lam, pv, chain, g.d_heights, &cc);
+    const bool rec_chain = CH && att && !v.diffuse;
+    if (rec_chain) cc.record(chain, k, v, w.dir);
     float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
     if (v.diffuse) {
       ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
@@ -1268,10 +1353,11 @@ __device__ __forceinline__ void reslrb_path(const DevScene& S, const KParams& kp
         if (CH && !v.attached) pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, P, rho);
       }
     }
-    walk_scatter(S, w, v, ns, rho, r);
+    const bool refl = walk_scatter(S, w, v, ns, rho, r);
+    if (rec_chain) cc.record_branch(refl);
     walk_rr(kp, n, k, w);
   }
-  if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights);
+  if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights, &cc);
 }
 
 template <bool ATT, bool CH>
@@ -1440,7 +1526,7 @@ __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const flo
             c.anchor_sliding = !((((uint32_t)__float_as_int(sp.x)) >> 24) & 16u);
           }
           scatter_heights(S, g.d_heights, prim, 0.0f, 0.0f, f3(0, 0, 0), gn);
-          propagate_sliding(S, kp, n, c, k, gx, g.d_heights);
+          propagate_sliding(S, kp, n, c, k, gx, g.d_heights, nullptr, prim);
         }
       }
       acc = acc + P3;
