@@ -335,6 +335,96 @@ __device__ __forceinline__ void sort_children(float k[W], int c[W]) {
 // current hit are dropped when popped.  Leaves are tested in a separate loop (while-while
 // form) so that a warp tests its lanes' pending leaves together.  A stack overflow (a
 // tree deeper than the stack allows) drops the entry and sets ERR_BOUNDS.
+//
+// The traversal is resumable: its state (hit so far, next entry, stack depth; the stack in
+// caller-owned local arrays) survives between calls, and a call stops after `budget` node
+// and leaf visits.  A path kernel gives each lane a fixed budget per step of its main loop,
+// so a warp's step no longer waits for the lane with the longest ray: that lane resumes in
+// the next step while the others shade and start their next rays (the few rays that graze
+// a height field visit several times more nodes than the average ray).  Split or not, the
+// visits and their order are the same, and so is the hit.
+struct TravState {
+  HitRec h;
+  int best_orig;  // original id of the current hit (ties go to the smaller)
+  int next;       // entry to visit next: an inner node (>= 0), a leaf (< -1) or kCodeDone
+  int sp;         // entries on the stack
+};
+
+template <bool ST = false>
+__device__ __forceinline__ void trav_begin(const DevScene& S, float3 org, float3 dir, int skip, TravState& T,
+                                           Census* cs = nullptr) {
+  if (ST) cs->rays++;
+  T.h.prim = -1; T.h.t = 3.0e38f; T.h.b1 = 0; T.h.b2 = 0;
+  T.best_orig = 0x7fffffff;
+  for (int k = 0; k < S.n_direct; ++k) {
+    if (k == skip) continue;
+    if (ST) cs->prims++;
+    const Prim p = load_prim(S, k);
+    float t, u, v;
+    if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
+        (t < T.h.t || (t == T.h.t && p.orig < T.best_orig))) {
+      T.h.prim = k; T.h.t = t; T.h.b1 = u; T.h.b2 = v; T.best_orig = p.orig;
+    }
+  }
+  T.next = S.n_wnodes == 0 ? kCodeDone : 0;  // the root
+  T.sp = 0;
+}
+
+// Continue a traversal for at most `budget` visits (a leaf found within the budget is tested
+// in the same call); true when it has finished and T.h holds the closest hit.
+template <int W, bool ST = false>
+__device__ __forceinline__ bool trav_resume(const DevScene& S, float3 org, float3 dir, int skip, TravState& T,
+                                            int* st_code, float* st_t, int budget, Census* cs = nullptr) {
+  int next = T.next, sp = T.sp;
+  if (next == kCodeDone) return true;
+  const float3 inv = safe_inv(dir);
+  const float3 oi = f3(org.x * inv.x, org.y * inv.y, org.z * inv.z);
+  while (next != kCodeDone && budget > 0) {
+    while (next >= 0 && budget > 0) {
+      --budget;
+      float tn[W];
+      int code[W];
+      if (ST) cs->nodes += W;
+      wide_boxes<W>(S, next, inv, oi, T.h.t, tn, code);
+      sort_children<W>(tn, code);
+#pragma unroll
+      for (int c = W - 1; c >= 0; --c) {
+        if (tn[c] <= T.h.t) {
+          if (sp < kWideStack) { st_code[sp] = code[c]; st_t[sp] = tn[c]; ++sp; }
+          else atomicOr(S.err, ERR_BOUNDS);
+        }
+      }
+      next = kCodeDone;
+      while (sp > 0) {
+        --sp;
+        if (st_t[sp] <= T.h.t) { next = st_code[sp]; break; }
+      }
+    }
+    if (next >= 0 || next == kCodeDone) break;  // out of budget at an inner node, or finished
+    --budget;
+    const int first = (next & 0x7fffffff) >> 4, cnt = next & 15;
+    for (int k = first; k < first + cnt; ++k) {
+      if (k == skip) continue;
+      if (ST) cs->prims++;
+      const Prim p = load_prim(S, k);
+      float t, u, v;
+      if (hit_prim(p.o, p.e1, p.e2, p.is_tri, org, dir, t, u, v) && t > kTMin &&
+          (t < T.h.t || (t == T.h.t && p.orig < T.best_orig))) {
+        T.h.prim = k; T.h.t = t; T.h.b1 = u; T.h.b2 = v; T.best_orig = p.orig;
+      }
+    }
+    next = kCodeDone;
+    while (sp > 0) {
+      --sp;
+      if (st_t[sp] <= T.h.t) { next = st_code[sp]; break; }
+    }
+  }
+  T.next = next;
+  T.sp = sp;
+  return next == kCodeDone;
+}
+
+// The same traversal in one call, with its state in registers and a local stack.
 template <int W, bool ST = false>
 __device__ __forceinline__ HitRec trace_closest_w(const DevScene& S, float3 org, float3 dir, int skip,
                                                   Census* cs = nullptr) {
@@ -466,6 +556,30 @@ __device__ __forceinline__ HitRec trace_closest(const DevScene& S, float3 org, f
   return trace_closest2<ST>(S, org, dir, skip, cs);
 #else
   return trace_closest_w<LT_BVH_WIDTH, ST>(S, org, dir, skip, cs);
+#endif
+}
+// Resumable closest hit (see TravState): the binary BVH finishes in the first call.
+#ifndef LT_TRACE_BUDGET
+#define LT_TRACE_BUDGET 5
+#endif
+constexpr int kTraceBudget = LT_TRACE_BUDGET;  // node and leaf visits per lane per step
+template <bool ST = false>
+__device__ __forceinline__ void trace_begin(const DevScene& S, float3 org, float3 dir, int skip, TravState& T,
+                                            Census* cs = nullptr) {
+#if LT_BVH_WIDTH == 2
+  T.h = trace_closest2<ST>(S, org, dir, skip, cs);
+  T.next = kCodeDone;
+#else
+  trav_begin<ST>(S, org, dir, skip, T, cs);
+#endif
+}
+template <bool ST = false>
+__device__ __forceinline__ bool trace_resume(const DevScene& S, float3 org, float3 dir, int skip, TravState& T,
+                                             int* st_code, float* st_t, Census* cs = nullptr) {
+#if LT_BVH_WIDTH == 2
+  return true;
+#else
+  return trav_resume<LT_BVH_WIDTH, ST>(S, org, dir, skip, T, st_code, st_t, kTraceBudget, cs);
 #endif
 }
 template <bool ST = false>

@@ -880,6 +880,10 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
   float Om = 0.0f, wR = 0.0f, Rux = 0.0f, Ruy = 0.0f;
   float3 LR = f3(0, 0, 0);
   int R = -1;
+  TravState ts;  // the lane's ray in flight (see TravState)
+  int st_code[kWideStack];
+  float st_t[kWideStack];
+  bool inflight = false;
   while (true) {
     const bool want = more && !busy;
     int jnew = jb;
@@ -912,9 +916,15 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
     const bool trav = busy && k < kp.max_depth && !w.dead;
     HitRec h;
     h.prim = -1;
-    if (trav) h = trace_closest(S, w.org, w.dir, w.skip);
+    bool pending = false;  // the ray has visits left: the lane resumes it in the next step
+    if (trav) {
+      if (!inflight) trace_begin(S, w.org, w.dir, w.skip, ts);
+      inflight = !trace_resume(S, w.org, w.dir, w.skip, ts, st_code, st_t);
+      pending = inflight;
+      h = ts.h;
+    }
     Vtx v;
-    const bool alive = trav && walk_finish(S, w, h, v);
+    const bool alive = trav && !pending && walk_finish(S, w, h, v);
     float3 ns = f3(0, 0, 0);
     Conn c;
     c.valid = false; c.ux = c.uy = 0.0f;
@@ -939,7 +949,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
         yhat = mlp_warp_infer(mlp, f, ftile);
       }
     }
-    if (!busy) continue;
+    if (!busy || pending) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
     if (!alive) {
       // end of the path: reservoir record / tape length / per-path outputs
@@ -1069,6 +1079,10 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   pv.prim = -1;
   ChainCache cc;
   cc.reset();
+  TravState ts;  // the lane's ray in flight (see TravState)
+  int st_code[kWideStack];
+  float st_t[kWideStack];
+  bool inflight = false;
   while (true) {
     const bool want = more && phase == IDLE;
     int jnew = jb;
@@ -1128,9 +1142,19 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     const bool trav = phase != IDLE && k < kmax && !w.dead;
     HitRec h;
     h.prim = -1;
-    if (trav) h = trace_closest<ST>(S, w.org, w.dir, w.skip, &cs);
+    bool pending = false;  // the ray has visits left: the lane resumes it in the next step
+    if constexpr (CH) {
+      // the specular-chain variants keep whole traversals: the resumable state would
+      // push them past the register budget that their chain transport needs
+      if (trav) h = trace_closest<ST>(S, w.org, w.dir, w.skip, &cs);
+    } else if (trav) {
+      if (!inflight) trace_begin<ST>(S, w.org, w.dir, w.skip, ts, &cs);
+      inflight = !trace_resume<ST>(S, w.org, w.dir, w.skip, ts, st_code, st_t, &cs);
+      pending = inflight;
+      h = ts.h;
+    }
     Vtx v;
-    const bool alive = trav && walk_finish(S, w, h, v);
+    const bool alive = trav && !pending && walk_finish(S, w, h, v);
     float3 ns = f3(0, 0, 0);
     Conn c;
     c.valid = false; c.ux = c.uy = 0.0f;
@@ -1146,7 +1170,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       const bool vis = phase == PASS2 && c.valid;
       if (vis && occluded<ST>(S, v.x, c.wc, c.dist, v.prim, &cs)) c.valid = false;
     }
-    if (phase == IDLE) continue;
+    if (phase == IDLE || pending) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
     if (MODE != 2 && phase == PASS2) {
       if (!alive) {
