@@ -382,6 +382,7 @@ struct ChainState {
 // most kChainCache vertices each; a longer or older chain is replayed as before.  The
 // states are the ones the replay would compute, from the same arithmetic.
 constexpr int kChainCache = 4;
+constexpr int kDraws = 4;  // path draws per lane and step of the LRB-3 loop
 struct ChainRec {
   ChainInfo info;
   int len;  // recorded specular vertices info.ka .. info.ka+len-1; -1: not usable
@@ -1083,14 +1084,69 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   int st_code[kWideStack];
   float st_t[kWideStack];
   bool inflight = false;
+  // Start path `got` (-1: the lane's range is exhausted) on the lane, or pass over it.
+  auto start = [&](int64_t got) {
+    const DevScene& S = BATCH ? ba.jobs[jb].S : S0;
+    const KParams& kp = BATCH ? ba.jobs[jb].kp : kp0;
+    float4* xr = xrec;
+    uint32_t* xh = xhi;
+    if (BATCH && MODE != 0) {
+      xr = (float4*)ba.jobs[jb].state;
+      xh = (uint32_t*)((char*)ba.jobs[jb].state + lrb3_state_split(kp.n_paths));
+    }
+    if (got < 0) {
+      more = false;
+    } else if (MODE == 2) {
+      const float4 a = xr[got];
+      const uint64_t vm = (uint64_t)__float_as_uint(a.w) | ((uint64_t)xh[got] << 32);
+      if (vm && (!kp.mask || kp.mask[got])) {
+        p = got;
+        if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+        float3 x0;
+        walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
+        rem = f3(a.x, a.y, a.z);
+        valid = vm;
+        pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+        chain.ka = -1;
+        if (CH) cc.reset();
+        last = 63 - __clzll((long long)valid);
+        k = 0;
+        phase = PASS3;
+      }
+    } else if (!kp.mask || kp.mask[got]) {
+      if (MK) known = (uint64_t)__float_as_uint(xr[got].w) | ((uint64_t)xh[got] << 32);
+      if (MK && !known) {  // no valid connection: delta_total = 0, the stored state stands
+        if (kp.dbg) ((float4*)kp.dbg)[got] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+      }
+      p = got;
+      if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+      float3 x0;
+      walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
+      dtot = f3(0, 0, 0);
+      valid = 0;
+      if (MK) last = 63 - __clzll((long long)known);
+      nconn = 0;
+      k = 0;
+      phase = PASS2;
+    }
+  };
   while (true) {
-    const bool want = more && phase == IDLE;
-    int jnew = jb;
-    const int64_t got = BATCH ? bdisp.take(ba, want, jnew) : disp.take(want);
-    if (BATCH && jnew != jb) {
-      add3(ba.jobs[jb].g.d_Le, gLe);  // emitted-radiance gradient of the lane's previous item
-      gLe = f3(0, 0, 0);
-      jb = jnew;
+    // A lane that draws a path without a valid connection (pass 3, and pass 2 once the
+    // primal's masks are known) has nothing to trace for it: it draws again, up to kDraws
+    // times per step, instead of idling through the step.
+    bool want = more && phase == IDLE;
+    for (int draw = 0;; ++draw) {
+      int jnew = jb;
+      const int64_t got = BATCH ? bdisp.take(ba, want, jnew) : disp.take(want);
+      if (BATCH && jnew != jb) {
+        add3(ba.jobs[jb].g.d_Le, gLe);  // emitted-radiance gradient of the lane's previous item
+        gLe = f3(0, 0, 0);
+        jb = jnew;
+      }
+      if (want) start(got);
+      want = want && more && phase == IDLE;
+      if (draw + 1 == kDraws || !__any_sync(0xffffffffu, want)) break;
     }
     const DevScene& S = BATCH ? ba.jobs[jb].S : S0;
     const KParams& kp = BATCH ? ba.jobs[jb].kp : kp0;
@@ -1104,41 +1160,9 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       xr = (float4*)ba.jobs[jb].state;
       xh = (uint32_t*)((char*)ba.jobs[jb].state + lrb3_state_split(kp.n_paths));
     }
-    if (want) {
-      if (got < 0) {
-        more = false;
-      } else if (MODE == 2) {
-        const float4 a = xr[got];
-        const uint64_t vm = (uint64_t)__float_as_uint(a.w) | ((uint64_t)xh[got] << 32);
-        if (vm && (!kp.mask || kp.mask[got])) {
-          p = got;
-          if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
-          float3 x0;
-          walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
-          rem = f3(a.x, a.y, a.z);
-          valid = vm;
-          pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
-          chain.ka = -1;
-          if (CH) cc.reset();
-          last = 63 - __clzll((long long)valid);
-          k = 0;
-          phase = PASS3;
-        }
-      } else if (!kp.mask || kp.mask[got]) {
-        p = got;
-        if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
-        float3 x0;
-        walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
-        dtot = f3(0, 0, 0);
-        valid = 0;
-        if (MK) known = (uint64_t)__float_as_uint(xr[p].w) | ((uint64_t)xh[p] << 32);
-        nconn = 0;
-        k = 0;
-        phase = PASS2;
-      }
-    }
     if (!__any_sync(0xffffffffu, phase != IDLE || more)) break;
-    const int kmax = phase == PASS2 ? kp.max_depth : last + 1;
+    // pass 2 with known masks also stops after the path's last valid connection
+    const int kmax = phase == PASS2 && !MK ? kp.max_depth : last + 1;
     const bool trav = phase != IDLE && k < kmax && !w.dead;
     HitRec h;
     h.prim = -1;
@@ -1173,7 +1197,30 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     if (phase == IDLE || pending) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
     if (MODE != 2 && phase == PASS2) {
-      if (!alive) {
+      // the path ends at a miss, at the depth limit, or (known masks) once its last valid
+      // connection is done, in the same step, so that the lane draws its next path at once
+      bool fin = !alive;
+      if (alive) {
+        if (ST) ++nverts;
+        float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+        float3 rho = f3(0, 0, 0);
+        if (v.diffuse) {
+          rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
+          if (c.valid) {
+            if (ST) ++nconns;
+            valid |= 1ull << k;
+            ++nconn;
+            float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
+            float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, nullptr, kp.filter);
+            dtot = dtot + mul(Lb, L);
+          }
+        }
+        walk_scatter(S, w, v, ns, rho, r);
+        walk_rr(kp, n, k, w);
+        ++k;
+        fin = MK && k > last;
+      }
+      if (fin) {
         if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4(dtot.x, dtot.y, dtot.z, (float)nconn);
         gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);  // emitted factor, weight delta_total
         if (MODE == 1) {
@@ -1193,60 +1240,45 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         } else {
           phase = IDLE;
         }
-        continue;
       }
-      if (ST) ++nverts;
-      float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
-      float3 rho = f3(0, 0, 0);
-      if (v.diffuse) {
-        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
-        if (c.valid) {
-          if (ST) ++nconns;
-          valid |= 1ull << k;
-          ++nconn;
-          float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
-          float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, nullptr, kp.filter);
-          dtot = dtot + mul(Lb, L);
-        }
-      }
-      walk_scatter(S, w, v, ns, rho, r);
-      walk_rr(kp, n, k, w);
-      ++k;
     } else if (MODE != 1) {
-      if (!alive) {
+      bool fin = !alive;  // a miss, or the path's last valid connection is done
+      if (alive) {
+        if (ST) ++nverts;
+        float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+        // attached segment weight and chain bookkeeping: every connection from here on
+        // carries this vertex's factors, so they weigh the remaining adjoint before Eq. 16
+        if (att) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights, &cc);
+        const bool rec_chain = CH && att && !v.diffuse;
+        if (rec_chain) cc.record(chain, k, v, w.dir);
+        float3 rho = f3(0, 0, 0);
+        if (v.diffuse) {
+          TexFoot foot;
+          rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
+          float3 wsplat = f3(0, 0, 0);
+          if ((valid >> k) & 1ull) {
+            float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
+            float2 q;
+            float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, att ? &q : nullptr, kp.filter);
+            float3 P = mul(Lb, L);
+            wsplat = P;           // splat factor rho_k / pi (Eq. 15)
+            rem = rem - P;        // Eq. 16
+            if (att) conn_adjoint(S, v.x, v.nraw, hsum(P), q, pv.gx, pv.gn);
+          }
+          scatter_albedo(g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor rho_k (Eq. 17)
+          if (att && CH && !v.attached)
+            pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
+        }
+        const bool refl = walk_scatter(S, w, v, ns, rho, r);
+        if (rec_chain) cc.record_branch(refl);
+        walk_rr(kp, n, k, w);
+        ++k;
+        fin = k > last;
+      }
+      if (fin) {
         if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights, &cc);
         phase = IDLE;
-        continue;
       }
-      if (ST) ++nverts;
-      float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
-      // attached segment weight and chain bookkeeping: every connection from here on
-      // carries this vertex's factors, so they weigh the remaining adjoint before Eq. 16
-      if (att) att_enter<CH>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights, &cc);
-      const bool rec_chain = CH && att && !v.diffuse;
-      if (rec_chain) cc.record(chain, k, v, w.dir);
-      float3 rho = f3(0, 0, 0);
-      if (v.diffuse) {
-        TexFoot foot;
-        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
-        float3 wsplat = f3(0, 0, 0);
-        if ((valid >> k) & 1ull) {
-          float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
-          float2 q;
-          float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, att ? &q : nullptr, kp.filter);
-          float3 P = mul(Lb, L);
-          wsplat = P;           // splat factor rho_k / pi (Eq. 15)
-          rem = rem - P;        // Eq. 16
-          if (att) conn_adjoint(S, v.x, v.nraw, hsum(P), q, pv.gx, pv.gn);
-        }
-        scatter_albedo(g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor rho_k (Eq. 17)
-        if (att && CH && !v.attached)
-          pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
-      }
-      const bool refl = walk_scatter(S, w, v, ns, rho, r);
-      if (rec_chain) cc.record_branch(refl);
-      walk_rr(kp, n, k, w);
-      ++k;
     }
   }
   if (BATCH) {
