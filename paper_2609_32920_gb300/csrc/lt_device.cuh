@@ -337,12 +337,21 @@ __device__ __forceinline__ void sort_children(float k[W], int c[W]) {
 // tree deeper than the stack allows) drops the entry and sets ERR_BOUNDS.
 //
 // The traversal is resumable: its state (hit so far, next entry, stack depth; the stack in
-// caller-owned local arrays) survives between calls, and a call stops after `budget` node
+// a caller-owned LocalStack) survives between calls, and a call stops after `budget` node
 // and leaf visits.  A path kernel gives each lane a fixed budget per step of its main loop,
 // so a warp's step no longer waits for the lane with the longest ray: that lane resumes in
 // the next step while the others shade and start their next rays (the few rays that graze
 // a height field visit several times more nodes than the average ray).  Split or not, the
 // visits and their order are the same, and so is the hit.
+// Traversal stack of (entry code, entry distance) pairs, one 8-byte word per entry, in the
+// thread's local memory.
+struct LocalStack {
+  static constexpr int kCap = kWideStack;
+  int2 e[kWideStack];
+  __device__ __forceinline__ void put(int i, int code, float t) { e[i] = make_int2(code, __float_as_int(t)); }
+  __device__ __forceinline__ int2 get(int i) const { return e[i]; }
+};
+
 struct TravState {
   HitRec h;
   int best_orig;  // original id of the current hit (ties go to the smaller)
@@ -372,9 +381,9 @@ __device__ __forceinline__ void trav_begin(const DevScene& S, float3 org, float3
 
 // Continue a traversal for at most `budget` visits (a leaf found within the budget is tested
 // in the same call); true when it has finished and T.h holds the closest hit.
-template <int W, bool ST = false>
+template <int W, bool ST = false, class STK>
 __device__ __forceinline__ bool trav_resume(const DevScene& S, float3 org, float3 dir, int skip, TravState& T,
-                                            int* st_code, float* st_t, int budget, Census* cs = nullptr) {
+                                            STK& stk, int budget, Census* cs = nullptr) {
   int next = T.next, sp = T.sp;
   if (next == kCodeDone) return true;
   const float3 inv = safe_inv(dir);
@@ -390,14 +399,15 @@ __device__ __forceinline__ bool trav_resume(const DevScene& S, float3 org, float
 #pragma unroll
       for (int c = W - 1; c >= 0; --c) {
         if (tn[c] <= T.h.t) {
-          if (sp < kWideStack) { st_code[sp] = code[c]; st_t[sp] = tn[c]; ++sp; }
+          if (sp < STK::kCap) { stk.put(sp, code[c], tn[c]); ++sp; }
           else atomicOr(S.err, ERR_BOUNDS);
         }
       }
       next = kCodeDone;
       while (sp > 0) {
         --sp;
-        if (st_t[sp] <= T.h.t) { next = st_code[sp]; break; }
+        const int2 e = stk.get(sp);
+        if (__int_as_float(e.y) <= T.h.t) { next = e.x; break; }
       }
     }
     if (next >= 0 || next == kCodeDone) break;  // out of budget at an inner node, or finished
@@ -416,7 +426,8 @@ __device__ __forceinline__ bool trav_resume(const DevScene& S, float3 org, float
     next = kCodeDone;
     while (sp > 0) {
       --sp;
-      if (st_t[sp] <= T.h.t) { next = st_code[sp]; break; }
+      const int2 e = stk.get(sp);
+      if (__int_as_float(e.y) <= T.h.t) { next = e.x; break; }
     }
   }
   T.next = next;
@@ -573,13 +584,13 @@ __device__ __forceinline__ void trace_begin(const DevScene& S, float3 org, float
   trav_begin<ST>(S, org, dir, skip, T, cs);
 #endif
 }
-template <bool ST = false>
+template <bool ST = false, class STK>
 __device__ __forceinline__ bool trace_resume(const DevScene& S, float3 org, float3 dir, int skip, TravState& T,
-                                             int* st_code, float* st_t, Census* cs = nullptr) {
+                                             STK& stk, Census* cs = nullptr) {
 #if LT_BVH_WIDTH == 2
   return true;
 #else
-  return trav_resume<LT_BVH_WIDTH, ST>(S, org, dir, skip, T, st_code, st_t, kTraceBudget, cs);
+  return trav_resume<LT_BVH_WIDTH, ST>(S, org, dir, skip, T, stk, kTraceBudget, cs);
 #endif
 }
 template <bool ST = false>

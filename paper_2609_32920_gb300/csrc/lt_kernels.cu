@@ -882,8 +882,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
   float3 LR = f3(0, 0, 0);
   int R = -1;
   TravState ts;  // the lane's ray in flight (see TravState)
-  int st_code[kWideStack];
-  float st_t[kWideStack];
+  LocalStack stk;
   bool inflight = false;
   while (true) {
     const bool want = more && !busy;
@@ -920,7 +919,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
     bool pending = false;  // the ray has visits left: the lane resumes it in the next step
     if (trav) {
       if (!inflight) trace_begin(S, w.org, w.dir, w.skip, ts);
-      inflight = !trace_resume(S, w.org, w.dir, w.skip, ts, st_code, st_t);
+      inflight = !trace_resume(S, w.org, w.dir, w.skip, ts, stk);
       pending = inflight;
       h = ts.h;
     }
@@ -1081,8 +1080,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   ChainCache cc;
   cc.reset();
   TravState ts;  // the lane's ray in flight (see TravState)
-  int st_code[kWideStack];
-  float st_t[kWideStack];
+  LocalStack stk;
   bool inflight = false;
   // Start path `got` (-1: the lane's range is exhausted) on the lane, or pass over it.
   auto start = [&](int64_t got) {
@@ -1173,7 +1171,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       if (trav) h = trace_closest<ST>(S, w.org, w.dir, w.skip, &cs);
     } else if (trav) {
       if (!inflight) trace_begin<ST>(S, w.org, w.dir, w.skip, ts, &cs);
-      inflight = !trace_resume<ST>(S, w.org, w.dir, w.skip, ts, st_code, st_t, &cs);
+      inflight = !trace_resume<ST>(S, w.org, w.dir, w.skip, ts, stk, &cs);
       pending = inflight;
       h = ts.h;
     }
