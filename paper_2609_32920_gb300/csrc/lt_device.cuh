@@ -343,6 +343,7 @@ __device__ __forceinline__ void sort_children(float k[W], int c[W]) {
 // the next step while the others shade and start their next rays (the few rays that graze
 // a height field visit several times more nodes than the average ray).  Split or not, the
 // visits and their order are the same, and so is the hit.
+
 // Traversal stack of (entry code, entry distance) pairs, one 8-byte word per entry, in the
 // thread's local memory.
 struct LocalStack {

@@ -1362,37 +1362,112 @@ __global__ void __launch_bounds__(256) k_lrb3_batch(BatchArgs ba) {
 // ======================================================================= ResLRB backward
 // Replay to the selected vertex R and apply the log-derivative identity with weight
 // Lbar_R * S to every factor of L_R (Eq. 11); attached adds the positional channel.
-// One path of the ResLRB backward pass; `att` selects the attached formulation (ATT gates
-// its code at compile time).  gLe accumulates the emitted-radiance gradient.
-template <bool ATT, bool CH>
-__device__ __forceinline__ void reslrb_path(const DevScene& S, const KParams& kp, const float* __restrict__ dI,
-                                            const float4* __restrict__ rec, const GradPtrs& g, int64_t p, bool att,
-                                            float3 Le, float3& gLe) {
-  if (kp.mask && !kp.mask[p]) return;
-  float4 r0 = rec[2 * p], r1 = rec[2 * p + 1];
-  int R = __float_as_int(r0.x);
-  if (R < 0) return;
-  if (R >= kp.max_depth) { set_err(S, ERR_BOUNDS); return; }
-  const uint64_t n = (uint64_t)(kp.path_offset + p);
-  float3 Sh = f3(r1.x, r1.y, r1.z);
-  float2 q;
-  float3 Lb = adjoint_read_f(dI, S.W, S.H, r0.z, r0.w, Sh, att ? &q : nullptr, kp.filter);
-  float3 P = mul(Lb, Sh);
-  float lam = hsum(P);
-  gLe = gLe + f3(P.x / Le.x, P.y / Le.y, P.z / Le.z);
+// The ResLRB backward pass as a per-lane state machine, like the LRB-3 passes: a lane replays
+// one path to its selected vertex R, draws its next path in the same step as it finishes,
+// draws again over paths without a selected connection, and (scenes without dielectrics)
+// resumes long traversals over several steps.  `att` (per item in a batch) selects the
+// attached formulation; ATT gates its code at compile time.
+template <bool ATT, bool CH, bool BATCH>
+__device__ __forceinline__ void reslrb_body(const DevScene& S0, const KParams& kp0, const float* __restrict__ dI0,
+                                            const float4* __restrict__ rec0, const GradPtrs& g0, const BatchArgs& ba) {
+  extern __shared__ float sgrad[];
+  GradPtrs gs = g0;
+  if (!BATCH) {
+    const Sink sink = sink_begin(kp0, g0, sgrad);
+    gs.d_albedo = sink.alb;
+    gs.d_heights = sink.h;
+  }
+  float3 Le = BATCH ? f3(0, 0, 0) : f3(kp0.Le[0], kp0.Le[1], kp0.Le[2]);
+  float3 gLe = f3(0, 0, 0);
+  Dispenser disp;
+  BatchDispenser bdisp;
+  if (BATCH) bdisp.init(); else disp.init(kp0.n_paths);
+  int jb = 0;
+  bool busy = false, more = true;
+  int64_t p = 0;
+  int k = 0, R = 0;
+  float3 P = f3(0, 0, 0);  // Lbar_R * S: the weight of every factor of L_R
+  float lam = 0.0f;
+  float2 q = make_float2(0.0f, 0.0f);
   Walk w;
-  float3 x0;
-  walk_start(S, kp.seed, n, Le, w, x0);
   PendAdj pv;
-  pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
   ChainInfo chain;
   chain.ka = -1;
+  pv.prim = -1;
   ChainCache cc;
   cc.reset();
-  for (int k = 0; k <= R; ++k) {
+  TravState ts;
+  LocalStack stk;
+  bool inflight = false;
+  auto start = [&](int64_t got) {
+    if (got < 0) { more = false; return; }
+    const DevScene& S = BATCH ? ba.jobs[jb].S : S0;
+    const KParams& kp = BATCH ? ba.jobs[jb].kp : kp0;
+    const float* dI = BATCH ? ba.jobs[jb].dI : dI0;
+    const float4* rec = BATCH ? (const float4*)ba.jobs[jb].rec : rec0;
+    const bool att = ATT && (!BATCH || ba.jobs[jb].att);
+    if (kp.mask && !kp.mask[got]) return;
+    const float4 r0 = rec[2 * got], r1 = rec[2 * got + 1];
+    const int Rr = __float_as_int(r0.x);
+    if (Rr < 0) return;
+    if (Rr >= kp.max_depth) { set_err(S, ERR_BOUNDS); return; }
+    p = got;
+    R = Rr;
+    if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+    const float3 Sh = f3(r1.x, r1.y, r1.z);
+    const float3 Lb = adjoint_read_f(dI, S.W, S.H, r0.z, r0.w, Sh, att ? &q : nullptr, kp.filter);
+    P = mul(Lb, Sh);
+    lam = hsum(P);
+    gLe = gLe + f3(P.x / Le.x, P.y / Le.y, P.z / Le.z);
+    float3 x0;
+    walk_start(S, kp.seed, (uint64_t)(kp.path_offset + p), Le, w, x0);
+    pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+    chain.ka = -1;
+    if (CH) cc.reset();
+    k = 0;
+    busy = true;
+  };
+  while (true) {
+    bool want = more && !busy;
+    for (int draw = 0;; ++draw) {
+      int jnew = jb;
+      const int64_t got = BATCH ? bdisp.take(ba, want, jnew) : disp.take(want);
+      if (BATCH && jnew != jb) {
+        add3(ba.jobs[jb].g.d_Le, gLe);  // emitted-radiance gradient of the lane's previous item
+        gLe = f3(0, 0, 0);
+        jb = jnew;
+      }
+      if (want) start(got);
+      want = want && more && !busy;
+      if (draw + 1 == kDraws || !__any_sync(0xffffffffu, want)) break;
+    }
+    if (!__any_sync(0xffffffffu, busy || more)) break;
+    const DevScene& S = BATCH ? ba.jobs[jb].S : S0;
+    const KParams& kp = BATCH ? ba.jobs[jb].kp : kp0;
+    const GradPtrs& g = BATCH ? ba.jobs[jb].g : gs;
+    const bool att = ATT && (!BATCH || ba.jobs[jb].att);
+    const bool trav = busy && !w.dead;
+    HitRec h;
+    h.prim = -1;
+    bool pending = false;
+    if constexpr (CH) {
+      if (trav) h = trace_closest(S, w.org, w.dir, w.skip);
+    } else if (trav) {
+      if (!inflight) trace_begin(S, w.org, w.dir, w.skip, ts);
+      inflight = !trace_resume(S, w.org, w.dir, w.skip, ts, stk);
+      pending = inflight;
+      h = ts.h;
+    }
     Vtx v;
-    if (!walk_hit(S, w, v)) { set_err(S, ERR_BOUNDS); break; }
-    float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+    const bool alive = trav && !pending && walk_finish(S, w, h, v);
+    if (!busy || pending) continue;
+    const uint64_t n = (uint64_t)(kp.path_offset + p);
+    if (!alive) {  // the replay must reach the vertex the primal selected
+      set_err(S, ERR_BOUNDS);
+      busy = false;
+      continue;
+    }
+    const float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
     if (att) att_enter<CH>(S, kp, n, k, v, lam, lam, pv, chain, g.d_heights, &cc);
     const bool rec_chain = CH && att && !v.diffuse;
     if (rec_chain) cc.record(chain, k, v, w.dir);
@@ -1410,49 +1485,29 @@ __device__ __forceinline__ void reslrb_path(const DevScene& S, const KParams& kp
     const bool refl = walk_scatter(S, w, v, ns, rho, r);
     if (rec_chain) cc.record_branch(refl);
     walk_rr(kp, n, k, w);
+    if (++k > R) {
+      if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights, &cc);
+      busy = false;
+    }
   }
-  if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights, &cc);
+  if (BATCH) {
+    add3(ba.jobs[jb].g.d_Le, gLe);
+    return;
+  }
+  sink_end(kp0, g0, sgrad);
+  block_add3(g0.d_Le, gLe);
 }
 
 template <bool ATT, bool CH>
 __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const float* __restrict__ dI,
                                                 const float4* __restrict__ rec, GradPtrs g0) {
-  extern __shared__ float sgrad[];
-  const Sink sink = sink_begin(kp, g0, sgrad);
-  GradPtrs g = g0;
-  g.d_albedo = sink.alb;
-  g.d_heights = sink.h;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
-  float3 gLe = f3(0, 0, 0);
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride)
-    reslrb_path<ATT, CH>(S, kp, dI, rec, g, p, ATT, Le, gLe);
-  sink_end(kp, g0, sgrad);
-  block_add3(g.d_Le, gLe);
+  reslrb_body<ATT, CH, false>(S, kp, dI, rec, g0, BatchArgs{});
 }
 
-// Batched ResLRB backward: lanes take paths from the batch queue (one path each per turn).
+// Batched ResLRB backward: lanes take paths from the batch queue.
 template <bool ATT, bool CH>
 __global__ void __launch_bounds__(256) k_reslrb_batch(BatchArgs ba) {
-  BatchDispenser bdisp;
-  bdisp.init();
-  int jb = 0;
-  float3 gLe = f3(0, 0, 0);
-  while (true) {
-    int jnew = jb;
-    const int64_t p = bdisp.take(ba, true, jnew);
-    if (jnew != jb) {
-      add3(ba.jobs[jb].g.d_Le, gLe);
-      gLe = f3(0, 0, 0);
-      jb = jnew;
-    }
-    if (!__any_sync(0xffffffffu, p >= 0)) break;
-    if (p < 0) continue;
-    const BatchJob& J = ba.jobs[jb];
-    const float3 Le = f3(J.kp.Le[0], J.kp.Le[1], J.kp.Le[2]);
-    reslrb_path<ATT, CH>(J.S, J.kp, J.dI, (const float4*)J.rec, J.g, p, ATT && J.att, Le, gLe);
-  }
-  add3(ba.jobs[jb].g.d_Le, gLe);
+  reslrb_body<ATT, CH, true>(ba.jobs[0].S, ba.jobs[0].kp, nullptr, nullptr, GradPtrs{}, ba);
 }
 
 // ======================================================================= buffered two-pass
