@@ -853,15 +853,21 @@ __device__ __forceinline__ void add3(float* d, float3 v) {
 // loop performs one vertex of the lane's current path.
 // BATCH: the lane's scene, parameters and outputs are those of the batch item its path
 // belongs to (BatchDispenser); S0, kp0, image0 and aux0 are not used.
-template <int EST, bool BATCH>
+// LEARN compiles the learned reservoir target (ResLRB only); plain ResLRB does not carry its
+// registers.
+template <int EST, bool BATCH, bool LEARN = false>
 __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& kp0, float* __restrict__ image0,
                                             void* aux0, const BatchArgs& ba) {
-  // learned reservoir target: network image and one 32x16 feature tile per warp
+  // learned reservoir target: network image, one 32x16 feature tile per warp, and two
+  // feature slots per lane (see below)
   extern __shared__ __align__(16) unsigned char psmem[];
   MlpSmem& mlp = *reinterpret_cast<MlpSmem*>(psmem);
-  __nv_bfloat16* ftile = reinterpret_cast<__nv_bfloat16*>(psmem + ((sizeof(MlpSmem) + 15) & ~size_t(15))) +
-                         (threadIdx.x >> 5) * 32 * kMlpIn;
-  const bool learned = !BATCH && EST == 1 && kp0.mlp != nullptr;
+  const size_t tile_at = (sizeof(MlpSmem) + 15) & ~size_t(15);
+  __nv_bfloat16* ftile = reinterpret_cast<__nv_bfloat16*>(psmem + tile_at) + (threadIdx.x >> 5) * 32 * kMlpIn;
+  // feature i of slot q of this lane at fstash[(q * kMlpIn + i) * blockDim.x] (no bank conflicts)
+  float* fstash = reinterpret_cast<float*>(psmem + tile_at + sizeof(__nv_bfloat16) * 32 * kMlpIn * (blockDim.x >> 5)) +
+                  threadIdx.x;
+  const bool learned = LEARN && !BATCH && EST == 1 && kp0.mlp != nullptr;
   if (learned) {
     mlp_load_smem(mlp, kp0.mlp);
     __syncthreads();
@@ -881,6 +887,8 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
   float Om = 0.0f, wR = 0.0f, Rux = 0.0f, Ruy = 0.0f;
   float3 LR = f3(0, 0, 0);
   int R = -1;
+  int ncand = 0;       // candidates so far (learned target)
+  float lum1 = 0.0f;   // luminance of the first one
   TravState ts;  // the lane's ray in flight (see TravState)
   LocalStack stk;
   bool inflight = false;
@@ -909,6 +917,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
         Om = wR = Rux = Ruy = 0.0f;
         LR = f3(0, 0, 0);
         R = -1;
+        ncand = 0;
         busy = true;
       }
     }
@@ -933,20 +942,47 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
       c = connect_pre(S, v.x, ns);
     }
     if (c.valid && occluded(S, v.x, c.wc, c.dist, v.prim)) c.valid = false;
-    // learned reservoir target: one warp-wide tensor-core evaluation for the lanes that
-    // have a connection at this step (all 32 lanes take part)
-    float yhat = 0.0f;
+    // Learned reservoir target: warp-wide tensor-core evaluations (all 32 lanes take part).
+    // The first candidate of a path is kept whatever its weight (acceptance probability
+    // w_1 / Omega = 1), so its weight is only needed once a second candidate arrives: its
+    // features wait in shared memory and both are evaluated then.  A path with one
+    // candidate (most caustic paths) costs no evaluation; the weights, and so every
+    // decision and record, are the same as with eager evaluation.  The rows a step needs are
+    // packed into one tile, so a step costs one evaluation of up to 32 rows, and one m16
+    // tile when 16 rows or fewer are needed.
+    float yhat = 0.0f, yfirst = 0.0f;
     if (learned) {
-      const bool need = busy && alive && c.valid && active;
-      if (__any_sync(0xffffffffu, need)) {
-        float f[16];
-        if (need) {
-          conn_features(S, v.x, ns, w.dir, w.beta, k, kp.max_depth, c, kp.inv_n, f);
-        } else {
+      bool cand = busy && alive && c.valid && active;
+      float f[16];
+      if (cand) {
+        const float3 Lc = mul(w.beta, tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr)) * (c.geo * kp.inv_n);
+        cand = luminance(Lc) > 0.0f;  // a zero-weight connection is no candidate
+      }
+      if (cand) {
+        // slot 0 keeps the first candidate's features, slot 1 takes this step's
+        conn_features(S, v.x, ns, w.dir, w.beta, k, kp.max_depth, c, kp.inv_n, f);
+        float* dst = fstash + (ncand == 0 ? 0 : kMlpIn * blockDim.x);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) f[i] = mlp.mean[i];
-        }
-        yhat = mlp_warp_infer(mlp, f, ftile);
+        for (int i = 0; i < 16; ++i) dst[i * blockDim.x] = f[i];
+      }
+      // the evaluations the warp needs at this step, packed into consecutive tile rows:
+      // this step's candidates first, then the stashed first candidates
+      const bool need = cand && ncand >= 1, need1 = cand && ncand == 1;
+      const unsigned b0 = __ballot_sync(0xffffffffu, need), b1 = __ballot_sync(0xffffffffu, need1);
+      const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
+      const int n0 = __popc(b0), total = n0 + __popc(b1);
+      const int r0 = __popc(b0 & below), r1 = n0 + __popc(b1 & below);
+      for (int base = 0; base < total; base += 32) {
+        const bool s0 = need && r0 >= base && r0 < base + 32, s1 = need1 && r1 >= base && r1 < base + 32;
+        if (s0) mlp_stage_row(mlp, fstash + kMlpIn * blockDim.x, blockDim.x, ftile, r0 - base);
+        if (s1) mlp_stage_row(mlp, fstash, blockDim.x, ftile, r1 - base);
+        __syncwarp();
+        const float out = mlp_warp_infer_rows(mlp, ftile, min(32, total - base));
+        const float o0 = __shfl_sync(0xffffffffu, out, (r0 - base) & 31);
+        const float o1 = __shfl_sync(0xffffffffu, out, (r1 - base) & 31);
+        if (s0) yhat = o0;
+        if (s1) yfirst = o1;
+        __syncwarp();
       }
     }
     if (!busy || pending) continue;
@@ -990,7 +1026,19 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
             float om = luminance(L);
             // learned target: lum(L) (exp(sigma * yhat) + eps); any positive weight keeps the
             // estimator unbiased (Eq. 10)
-            if (learned) om *= __expf(fminf(fmaxf(mlp.tscale * yhat, -30.0f), 30.0f)) + 1e-3f;
+            if (learned && om > 0.0f) {
+              if (ncand == 0) {
+                // first candidate: accepted; Om / wR = 1 until a second one arrives
+                lum1 = om;
+                Om = wR = 1.0f;
+                R = k; LR = L; Rux = c.ux; Ruy = c.uy;
+                om = 0.0f;
+              } else if (ncand == 1) {
+                Om = wR = lum1 * (__expf(fminf(fmaxf(mlp.tscale * yfirst, -30.0f), 30.0f)) + 1e-3f);
+              }
+              ++ncand;
+              if (om > 0.0f) om *= __expf(fminf(fmaxf(mlp.tscale * yhat, -30.0f), 30.0f)) + 1e-3f;
+            }
             if (om > 0.0f) {
               Om += om;
               if (r.w < om / Om) { R = k; wR = om; LR = L; Rux = c.ux; Ruy = c.uy; }
@@ -1026,6 +1074,11 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
 template <int EST>
 __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
   primal_body<EST, false>(S, kp, image, aux, BatchArgs{});
+}
+// ResLRB primal with the learned reservoir target, held to four blocks per SM
+__global__ void __launch_bounds__(128, 4) k_primal_learned(DevScene S, KParams kp, float* __restrict__ image,
+                                                           void* aux) {
+  primal_body<1, false, true>(S, kp, image, aux, BatchArgs{});
 }
 
 template <int EST>
@@ -1698,12 +1751,16 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
 cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux, const LaunchCfg& L,
                           cudaStream_t st) {
   int grid = grid_for(L, kp.n_paths);
-  const size_t smem = (est == 1 && kp.mlp)
-                          ? ((sizeof(MlpSmem) + 15) & ~size_t(15)) + sizeof(__nv_bfloat16) * 32 * kMlpIn * (L.block / 32)
-                          : 0;
+  const size_t smem = (est == 1 && kp.mlp) ? ((sizeof(MlpSmem) + 15) & ~size_t(15)) +
+                                                sizeof(__nv_bfloat16) * 32 * kMlpIn * (L.block / 32) +
+                                                sizeof(float) * 2 * kMlpIn * L.block
+                                          : 0;
   switch (est) {
     case 0: k_primal<0><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
-    case 1: k_primal<1><<<grid, L.block, smem, st>>>(S, kp, image, aux); break;
+    case 1:
+      if (kp.mlp) k_primal_learned<<<grid, L.block, smem, st>>>(S, kp, image, aux);
+      else k_primal<1><<<grid, L.block, 0, st>>>(S, kp, image, aux);
+      break;
     case 2: k_primal<2><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
     default: k_primal<3><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
   }

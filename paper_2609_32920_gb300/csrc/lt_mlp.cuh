@@ -161,6 +161,34 @@ __device__ __forceinline__ void afrag_from_tile(const __nv_bfloat16* tile, int m
   a[3] = *reinterpret_cast<const uint32_t*>(r8 + 2 * t + 8);
 }
 
+// Standardize 16 raw features (src[i * stride]) and stage them (BF16) as row `row` of the
+// warp's 32x16 tile.
+__device__ __forceinline__ void mlp_stage_row(const MlpSmem& m, const float* src, int stride, __nv_bfloat16* tile,
+                                              int row) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) tile[row * 16 + i] = __float2bfloat16_rn((src[i * stride] - m.mean[i]) * m.inv_std[i]);
+}
+
+// Whole-warp inference of the first `rows` (1..32, the same on every lane) rows of a staged
+// tile: lane r receives the output of row r.  Up to 16 rows take one m16 tile.
+__device__ __forceinline__ float mlp_warp_infer_rows(const MlpSmem& m, const __nv_bfloat16* tile, int rows) {
+  const int lane = threadIdx.x & 31;
+  float out = 0.0f;
+  for (int mt = 0; mt < (rows > 16 ? 2 : 1); ++mt) {
+    uint32_t a[4];
+    afrag_from_tile(tile, mt, a);
+    Hid z1, z2;
+    float yg, yg8;
+    mlp_tile_forward(m, a, z1, z2, yg, yg8);
+    // the output of row r of this tile sits on lane 4(r mod 8)
+    const int r = lane - 16 * mt;
+    const int src = 4 * (r & 7);
+    const float a0 = __shfl_sync(0xffffffffu, yg, src), a8 = __shfl_sync(0xffffffffu, yg8, src);
+    if (r >= 0 && r < 16) out = (r < 8) ? a0 : a8;
+  }
+  return out;
+}
+
 // Whole-warp inference: every lane passes its raw features, every lane receives its own
 // network output (must be called by all 32 lanes together).
 __device__ __forceinline__ float mlp_warp_infer(const MlpSmem& m, const float f[16], __nv_bfloat16* tile) {
