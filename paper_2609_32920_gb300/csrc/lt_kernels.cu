@@ -1,9 +1,12 @@
 // lt_kernels.cu -- CUDA kernels of the light tracer and its adjoints (sm_103a).
 //
-// One thread carries one light path through all of its vertices (grid-stride over the
-// path range, persistent grid sized to the SM count).  Every pass regenerates the path
-// from its Philox counter; nothing per vertex is stored except by the naive baseline.
+// One lane carries one light path at a time through its vertices and draws the next path
+// of its warp's share when it finishes (one wave of resident blocks).  Every pass
+// regenerates the path from its Philox counter; nothing per vertex is stored except by the
+// naive baseline and the buffered two-pass form.
 #include <cuda_runtime.h>
+
+#include <utility>
 
 #include "lt_device.cuh"
 #include "lt_batch.h"
@@ -1722,11 +1725,22 @@ __global__ void k_film_l2(const float* __restrict__ I, const float* __restrict__
 }
 
 // ======================================================================= launchers
-static int grid_for(const LaunchCfg& L, int64_t work) {
-  int64_t want = (work + L.block - 1) / L.block;
-  int64_t cap = (int64_t)L.sms * L.blocks_per_sm;
-  if (want > cap) want = cap;
-  return (int)(want < 1 ? 1 : want);
+// Launch a path kernel over `work` paths: at most L.blocks_per_sm blocks per SM, and no more
+// than the kernel's occupancy lets an SM hold at once.  The path kernels split their paths
+// statically over the warps of the grid, so a grid of more blocks than fit would run in
+// waves whose last one leaves SMs idle.
+template <typename... P, typename... A>
+static void launch_paths(void (*kern)(P...), const LaunchCfg& L, int64_t work, size_t smem, cudaStream_t st,
+                         A&&... args) {
+  int per_sm = L.blocks_per_sm, occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, L.block, smem) == cudaSuccess && occ > 0 &&
+      occ < per_sm)
+    per_sm = occ;
+  int64_t grid = (work + L.block - 1) / L.block;
+  const int64_t cap = (int64_t)L.sms * per_sm;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  kern<<<(int)grid, L.block, smem, st>>>(std::forward<A>(args)...);
 }
 
 cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
@@ -1750,26 +1764,24 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
 
 cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* image, void* aux, const LaunchCfg& L,
                           cudaStream_t st) {
-  int grid = grid_for(L, kp.n_paths);
   const size_t smem = (est == 1 && kp.mlp) ? ((sizeof(MlpSmem) + 15) & ~size_t(15)) +
                                                 sizeof(__nv_bfloat16) * 32 * kMlpIn * (L.block / 32) +
                                                 sizeof(float) * 2 * kMlpIn * L.block
                                           : 0;
   switch (est) {
-    case 0: k_primal<0><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
+    case 0: launch_paths(k_primal<0>, L, kp.n_paths, 0, st, S, kp, image, aux); break;
     case 1:
-      if (kp.mlp) k_primal_learned<<<grid, L.block, smem, st>>>(S, kp, image, aux);
-      else k_primal<1><<<grid, L.block, 0, st>>>(S, kp, image, aux);
+      if (kp.mlp) launch_paths(k_primal_learned, L, kp.n_paths, smem, st, S, kp, image, aux);
+      else launch_paths(k_primal<1>, L, kp.n_paths, 0, st, S, kp, image, aux);
       break;
-    case 2: k_primal<2><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
-    default: k_primal<3><<<grid, L.block, 0, st>>>(S, kp, image, aux); break;
+    case 2: launch_paths(k_primal<2>, L, kp.n_paths, 0, st, S, kp, image, aux); break;
+    default: launch_paths(k_primal<3>, L, kp.n_paths, 0, st, S, kp, image, aux); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                         const GradPtrs& g, void* state, bool mask_ready, const LaunchCfg& L, cudaStream_t st) {
-  int grid = grid_for(L, kp.n_paths);
   const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
   if (state) {
     float4* xrec = (float4*)state;
@@ -1779,74 +1791,70 @@ cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool cha
     GradPtrs g3 = g;
     g3.d_Le = nullptr;  // pass 3 writes no emitted-radiance gradient
     if (kp.census) {
-      if (mask_ready) k_lrb3_p2<true, true><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
-      else k_lrb3_p2<true, false><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+      if (mask_ready) launch_paths(k_lrb3_p2<true, true>, L, kp.n_paths, 0, st, S, k2, dI, g, xrec, xhi);
+      else launch_paths(k_lrb3_p2<true, false>, L, kp.n_paths, 0, st, S, k2, dI, g, xrec, xhi);
     } else {
-      if (mask_ready) k_lrb3_p2<false, true><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
-      else k_lrb3_p2<false, false><<<grid, L.block, 0, st>>>(S, k2, dI, g, xrec, xhi);
+      if (mask_ready) launch_paths(k_lrb3_p2<false, true>, L, kp.n_paths, 0, st, S, k2, dI, g, xrec, xhi);
+      else launch_paths(k_lrb3_p2<false, false>, L, kp.n_paths, 0, st, S, k2, dI, g, xrec, xhi);
     }
     if (kp.census) {
-      if (att && chains) k_lrb3_p3<true, true, true><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
-      else if (att) k_lrb3_p3<true, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
-      else k_lrb3_p3<false, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+      if (att && chains) launch_paths(k_lrb3_p3<true, true, true>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
+      else if (att) launch_paths(k_lrb3_p3<true, true, false>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
+      else launch_paths(k_lrb3_p3<false, true, false>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
     } else {
-      if (att && chains) k_lrb3_p3<true, false, true><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
-      else if (att) k_lrb3_p3<true, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
-      else k_lrb3_p3<false, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+      if (att && chains) launch_paths(k_lrb3_p3<true, false, true>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
+      else if (att) launch_paths(k_lrb3_p3<true, false, false>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
+      else launch_paths(k_lrb3_p3<false, false, false>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
     }
     return cudaGetLastError();
   }
   if (kp.census) {
-    if (att && chains) k_lrb3<true, true, true><<<grid, L.block, smem, st>>>(S, kp, dI, g);
-    else if (att) k_lrb3<true, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
-    else k_lrb3<false, true, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
+    if (att && chains) launch_paths(k_lrb3<true, true, true>, L, kp.n_paths, smem, st, S, kp, dI, g);
+    else if (att) launch_paths(k_lrb3<true, true, false>, L, kp.n_paths, smem, st, S, kp, dI, g);
+    else launch_paths(k_lrb3<false, true, false>, L, kp.n_paths, smem, st, S, kp, dI, g);
   } else {
-    if (att && chains) k_lrb3<true, false, true><<<grid, L.block, smem, st>>>(S, kp, dI, g);
-    else if (att) k_lrb3<true, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
-    else k_lrb3<false, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g);
+    if (att && chains) launch_paths(k_lrb3<true, false, true>, L, kp.n_paths, smem, st, S, kp, dI, g);
+    else if (att) launch_paths(k_lrb3<true, false, false>, L, kp.n_paths, smem, st, S, kp, dI, g);
+    else launch_paths(k_lrb3<false, false, false>, L, kp.n_paths, smem, st, S, kp, dI, g);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_reslrb(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                           const void* rec, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
-  int grid = grid_for(L, kp.n_paths);
   const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
-  if (att && chains) k_reslrb<true, true><<<grid, L.block, smem, st>>>(S, kp, dI, (const float4*)rec, g);
-  else if (att) k_reslrb<true, false><<<grid, L.block, smem, st>>>(S, kp, dI, (const float4*)rec, g);
-  else k_reslrb<false, false><<<grid, L.block, smem, st>>>(S, kp, dI, (const float4*)rec, g);
+  if (att && chains) launch_paths(k_reslrb<true, true>, L, kp.n_paths, smem, st, S, kp, dI, (const float4*)rec, g);
+  else if (att) launch_paths(k_reslrb<true, false>, L, kp.n_paths, smem, st, S, kp, dI, (const float4*)rec, g);
+  else launch_paths(k_reslrb<false, false>, L, kp.n_paths, smem, st, S, kp, dI, (const float4*)rec, g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_naive(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI,
                          const void* ws, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
-  int grid = grid_for(L, kp.n_paths);
   const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
-  if (att && chains) k_naive<true, true><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
-  else if (att) k_naive<true, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
-  else k_naive<false, false><<<grid, L.block, smem, st>>>(S, kp, dI, ws, g);
+  if (att && chains) launch_paths(k_naive<true, true>, L, kp.n_paths, smem, st, S, kp, dI, ws, g);
+  else if (att) launch_paths(k_naive<true, false>, L, kp.n_paths, smem, st, S, kp, dI, ws, g);
+  else launch_paths(k_naive<false, false>, L, kp.n_paths, smem, st, S, kp, dI, ws, g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lrb2(const DevScene& S, const KParams& kp, bool att, bool chains, const float* dI, void* buf,
                         const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
-  int grid = grid_for(L, kp.n_paths);
-  k_lrb2_reduce<<<grid, L.block, 0, st>>>(S, kp, dI, buf, g.d_Le);
+  launch_paths(k_lrb2_reduce, L, kp.n_paths, 0, st, S, kp, dI, buf, g.d_Le);
   float4* xrec = (float4*)buf;
   uint32_t* xhi = (uint32_t*)((char*)buf + lrb3_state_split(kp.n_paths));
   const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
   GradPtrs g3 = g;
   g3.d_Le = nullptr;  // added by the reduction
-  if (att && chains) k_lrb3_p3<true, false, true><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
-  else if (att) k_lrb3_p3<true, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
-  else k_lrb3_p3<false, false, false><<<grid, L.block, smem, st>>>(S, kp, dI, g3, xrec, xhi);
+  if (att && chains) launch_paths(k_lrb3_p3<true, false, true>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
+  else if (att) launch_paths(k_lrb3_p3<true, false, false>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
+  else launch_paths(k_lrb3_p3<false, false, false>, L, kp.n_paths, smem, st, S, kp, dI, g3, xrec, xhi);
   return cudaGetLastError();
 }
 
 cudaError_t launch_collect(const DevScene& S, const KParams& kp, const float* dI, float tfloor, float* feats,
                            float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L, cudaStream_t st) {
-  int grid = grid_for(L, kp.n_paths);
-  k_collect<<<grid, L.block, 0, st>>>(S, kp, dI, tfloor, feats, targets, cap, count);
+  launch_paths(k_collect, L, kp.n_paths, 0, st, S, kp, dI, tfloor, feats, targets, cap, count);
   return cudaGetLastError();
 }
 
