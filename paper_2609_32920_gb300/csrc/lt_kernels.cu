@@ -1351,7 +1351,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
 }
 
 template <bool ATT, bool ST, bool CH>
-__global__ void __launch_bounds__(128) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0) {
+__global__ void __launch_bounds__(128, 4) k_lrb3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0) {
   lrb3_body<ATT, ST, CH, false>(S, kp, dI, g0, BatchArgs{});
 }
 
