@@ -35,12 +35,14 @@ def agree_mask(S, sc, seed, n, D, path_offset=0, n_norm=0, max_divergent=1e-3):
     return same.astype(np.uint8)
 
 
-def primal_close(a, b, rtol=1e-4, mass=None, W=None):
+def primal_close(a, b, rtol=1e-4, mass=None, W=None, depth=1):
     """Per pixel |a-b| <= rtol * max(|b|, 1e-3 mean|b|) + eps_u * mass.
 
     The second term is the FP32 rounding of film positions: u = W/2 (1 + p_x / tan_x) comes
     from the hit point through about ten FP32 operations, so |du| <= 16 * 2^-24 * max(W, H)
-    pixels; a tent tap's weight moves by at most |du|, so a pixel moves by at
+    pixels per vertex; each vertex is found from its predecessor (the ray leaves the previous
+    vertex, Eq. 2), so the position error can grow along the path, at worst linearly in its
+    length `depth`.  A tent tap's weight moves by at most |du|, so a pixel moves by at
     most |du| times its tap mass (sum of |L| over splats touching it, from the oracle).  A
     splat within rounding of a pixel-centre line may use a tap set shifted by one pixel
     (with a near-zero weight there), so the mass is dilated over each pixel's 3x3
@@ -52,5 +54,5 @@ def primal_close(a, b, rtol=1e-4, mass=None, W=None):
         m = np.asarray(mass)
         pad = np.pad(m, ((1, 1), (1, 1), (0, 0)))
         dil = np.max([pad[i:i + m.shape[0], j:j + m.shape[1]] for i in range(3) for j in range(3)], axis=0)
-        tol = tol + 16.0 * 2.0 ** -24 * float(W) * dil
+        tol = tol + 16.0 * 2.0 ** -24 * float(W) * float(depth) * dil
     return np.abs(a - b) <= tol

@@ -81,7 +81,7 @@ def test_caustic_height_field_optimisation_reduces_loss(method):
         loss = ((img - target) ** 2).mean()
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     S.sync_status()
     first, last = np.mean(losses[:5]), np.mean(losses[-5:])
     assert last < 0.7 * first, (first, last)

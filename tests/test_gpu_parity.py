@@ -447,3 +447,83 @@ def test_gaussian_filter_matches_oracle(boxhm, slab, method):
         S.sync_status()
         assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
         assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+
+
+def test_bench_size_sampled_paths_match_oracle():
+    """The bench workload in the bench's launch configuration: box 256x256 with the 32x32
+    height field, 2^22 paths, depth 16, attached; the primal stores the validity masks and
+    LRB-3 runs as two kernels that reuse them; ResLRB with its 32-byte records.  Every path
+    index of the full range is launched; a path mask keeps the paths of nine blocks spread
+    over the range (the last one ends at the last path), which the oracle computes one by
+    one with the full-size normalisation 1/2^22.  Paths whose FP32 and FP64 decisions differ
+    are masked out on both sides.
+
+    Along depth-16 paths the FP32 vertex positions drift from the FP64 ones (each vertex is
+    found from its predecessor and grazing intersections amplify the rounding: film positions
+    differ by up to a few 1e-3 pixels, splat values by about 1e-4 relative through the
+    texture lookups), so the image is held to 1e-4 relative L2 and to the per-pixel bound
+    (with the film-position term scaled by the depth) on 99.9 % of its lit pixels, and the
+    reservoir weights to 1e-3; the gradients keep the 1e-3 relative L2 of the small cases."""
+    sc = I.box_scene(256, heightmap=32)
+    S = lt.Scene(sc)
+    N, D, seed, blk = 1 << 22, 16, 1, 500
+    rng = np.random.default_rng(11)
+    offs = sorted(int(x) for x in rng.choice(N - blk, 8, replace=False)) + [N - blk]
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 61)
+    dI = t32(dI_np)
+    # decision hashes over the full launch, compared on the sampled blocks
+    h = torch.zeros(N, dtype=torch.int32, device="cuda")
+    S.primal(S.opts(seed=seed, n_paths=N, max_depth=D, hash_out=h))
+    g_hash = h.cpu().numpy().view(np.uint32)
+    mask = np.zeros(N, dtype=np.uint8)
+    agree = {}
+    for o in offs:
+        _, oh = O.render(sc, seed=seed, n_paths=blk, max_depth=D, path_begin=o, n_norm=N, want_hash=True)
+        agree[o] = (g_hash[o:o + blk] == oh).astype(np.uint8)
+        mask[o:o + blk] = agree[o]
+    assert mask.sum() >= 0.998 * blk * len(offs), "too many paths took different discrete decisions"
+    m_dev = _dev_mask(mask)
+
+    # primal (plain estimator, storing the LRB-3 validity masks) and LRB-3 backward
+    state = S.new_lrb3_state(N)
+    o_p = S.opts(seed=seed, n_paths=N, max_depth=D, mask=m_dev, lrb3_state=state)
+    img = S.primal(o_p).cpu().numpy()
+    o_b = S.opts(seed=seed, n_paths=N, max_depth=D, attached=1, mask=m_dev, lrb3_state=state, lrb3_mask_ready=1)
+    gA, gL, gH = S.backward_lrb3(o_b, dI)
+    ref_img = np.zeros_like(img, dtype=np.float64)
+    mass = np.zeros_like(ref_img)
+    ref = None
+    for o in offs:
+        kw = dict(seed=seed, n_paths=blk, max_depth=D, path_begin=o, n_norm=N, mask=agree[o])
+        ref_img += O.render(sc, **kw)
+        mass += O.render(sc, estimator=2, **kw)
+        r = O.gradient(sc, dI_np, attached=1, **kw)
+        ref = r if ref is None else {k: ref[k] + r[k] for k in ("d_albedo", "d_Le", "d_heights")}
+    assert rel_l2(img, ref_img) < 1e-4
+    lit = ref_img != 0
+    close = primal_close(img, ref_img, mass=mass, W=max(sc.W, sc.H), depth=D)
+    assert close[lit].mean() >= 0.999 and close[~lit].all()
+    assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+    assert rel_l2(gA.cpu().numpy(), ref["d_albedo"]) < 1e-3
+
+    # ResLRB: reservoir winners bit-exact on the sampled paths, then its gradient
+    rec = torch.zeros((N, 8), device="cuda")
+    o_r = S.opts(seed=seed, n_paths=N, max_depth=D, attached=1, mask=m_dev)
+    S.primal(o_r, estimator=lt.EST_RESLRB, aux=rec)
+    gA, gL, gH = S.backward_reslrb(o_r, dI, rec)
+    r_all = rec.cpu().numpy()
+    ref = None
+    for o in offs:
+        kw = dict(seed=seed, n_paths=blk, max_depth=D, path_begin=o, n_norm=N, mask=agree[o])
+        _, rr = O.render(sc, estimator=1, want_records=True, **kw)
+        m = agree[o].astype(bool)
+        R = r_all[o:o + blk, 0].view(np.int32)
+        assert np.array_equal(R[m], rr[m, 0].astype(np.int32)), "reservoir winners differ"
+        sel = m & (R >= 0)
+        assert np.allclose(r_all[o:o + blk][sel, 1], rr[sel, 1], rtol=1e-3)
+        g = O.gradient(sc, dI_np, attached=1, method=O.RESLRB_AD, **kw)
+        ref = g if ref is None else {k: ref[k] + g[k] for k in ("d_albedo", "d_Le", "d_heights")}
+    assert rel_l2(gH.cpu().numpy(), ref["d_heights"]) < 1e-3
+    assert rel_l2(gL.cpu().numpy(), ref["d_Le"]) < 1e-3
+    assert rel_l2(gA.cpu().numpy(), ref["d_albedo"]) < 1e-3
