@@ -776,8 +776,13 @@ int or_intersect(const or_scene* s, const or_params* p, const double* org, const
 
 // Light-traced image (Sec. 3.1).  estimator 0 splats every connection; estimator 1 splats
 // only the reservoir winner reweighted by Omega/omega_R (Eq. 9, the ResLRB primal);
-// estimator 2 returns the tap-mass image used to bound film-position rounding.  image [H][W][3] is overwritten.  Optional per-path outputs: hashes [n_paths],
-// records [n_paths][8] = (R vertex index or -1, Omega/omega_R, u_x, u_y, S_rgb, n_conn).
+// estimator 2 returns the tap-mass image used to bound film-position rounding; estimator 3
+// splats every connection like 0 and reports per path the smallest distance (pixels) of a
+// film coordinate of its connections to a pixel centre, where the tent filter's derivative
+// jumps (Eq. 21; 1e9 without connections).  image [H][W][3] is overwritten.  Optional
+// per-path outputs: hashes [n_paths], records [n_paths][8] = (R vertex index or -1,
+// Omega/omega_R, u_x, u_y, S_rgb, n_conn); estimator 3: records [n_paths][8] with the
+// distance in slot 0.
 int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const uint8_t* mask, double* image,
                  uint32_t* hashes, int estimator, double* records) {
   Scene sc{s, p};
@@ -801,8 +806,14 @@ int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const
         r[0] = -1;
         r[7] = (double)cs.size();
       }
+      if (estimator == 3 && records) {
+        double dmin = 1e9;
+        for (auto& c : cs)
+          for (double u : {c.ux, c.uy}) dmin = std::min(dmin, std::fabs((u - 0.5) - std::round(u - 0.5)));
+        records[8 * i] = dmin;
+      }
       if (mask && !mask[i]) continue;
-      if (estimator == 0) {
+      if (estimator == 0 || estimator == 3) {
         for (auto& c : cs) splat(sc, A.img.data(), c.L, c.ux, c.uy, run->filter);
       } else if (estimator == 2) {
         // tap mass: |L| added with weight one to every on-film tap of each splat (bounds

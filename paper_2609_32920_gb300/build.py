@@ -14,11 +14,16 @@ OUT = os.path.join(PKG, "liblt.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
-# (source, object, extra flags): the kernels are compiled once per BVH width
+# (source, object, extra flags): the kernels are compiled once per BVH width.  They are
+# compiled without multiply-add contraction: every pass of a method replays the same path
+# and must take the same discrete decisions (a ray through a shared triangle edge, a
+# connection at the film border), but the compiler would otherwise fuse the same source
+# expression differently in each kernel it is inlined into.  Explicit fmaf() calls stay fused.
+KERNEL_FLAGS = ["-fmad=false"]
 UNITS = [("lt_api.cu", "lt_api.o", []), ("lt_dispatch.cu", "lt_dispatch.o", []), ("lt_mlp.cu", "lt_mlp.o", []),
-         ("lt_kernels.cu", "lt_kernels_w2.o", ["-DLT_BVH_WIDTH=2"]),
-         ("lt_kernels.cu", "lt_kernels_w4.o", ["-DLT_BVH_WIDTH=4"]),
-         ("lt_kernels.cu", "lt_kernels_w8.o", ["-DLT_BVH_WIDTH=8"])]
+         ("lt_kernels.cu", "lt_kernels_w2.o", ["-DLT_BVH_WIDTH=2", *KERNEL_FLAGS]),
+         ("lt_kernels.cu", "lt_kernels_w4.o", ["-DLT_BVH_WIDTH=4", *KERNEL_FLAGS]),
+         ("lt_kernels.cu", "lt_kernels_w8.o", ["-DLT_BVH_WIDTH=8", *KERNEL_FLAGS])]
 SOURCES = sorted({u[0] for u in UNITS})
 
 

@@ -28,19 +28,26 @@ namespace lt {
 namespace LT_KNS {
 
 // ======================================================================= refit
-// Triangle geometry from base vertex positions plus heights (y), leaf order.
+// Triangle geometry from base vertex positions plus heights (y), leaf order.  The edges
+// take the base edges plus the height differences, not differences of the displaced
+// absolute positions: a height field's neighbouring heights differ by far less than the
+// FP32 spacing of its absolute coordinates allows to resolve, and the edges set the
+// normals that refraction and the height gradients depend on.
 __global__ void k_update_tris(float4* prim, const int4* prim_h, const float4* tri_base, const float* heights,
                               int n_prims) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_prims) return;
   int4 ph = prim_h[i];
   if (ph.x < 0 && ph.y < 0 && ph.z < 0) return;
-  float3 v0 = xyz(tri_base[3 * i]), v1 = xyz(tri_base[3 * i + 1]), v2 = xyz(tri_base[3 * i + 2]);
-  if (ph.x >= 0) v0.y += heights[ph.x];
-  if (ph.y >= 0) v1.y += heights[ph.y];
-  if (ph.z >= 0) v2.y += heights[ph.z];
+  const float3 b0 = xyz(tri_base[3 * i]), b1 = xyz(tri_base[3 * i + 1]), b2 = xyz(tri_base[3 * i + 2]);
+  const float h0 = ph.x >= 0 ? heights[ph.x] : 0.0f, h1 = ph.y >= 0 ? heights[ph.y] : 0.0f,
+              h2 = ph.z >= 0 ? heights[ph.z] : 0.0f;
+  float3 e1 = b1 - b0, e2 = b2 - b0;
+  e1.y += h1 - h0;
+  e2.y += h2 - h0;
+  float3 v0 = b0;
+  v0.y += h0;
   float4 a = prim[3 * i], b = prim[3 * i + 1], c = prim[3 * i + 2];
-  float3 e1 = v1 - v0, e2 = v2 - v0;
   prim[3 * i] = make_float4(v0.x, v0.y, v0.z, a.w);
   prim[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, b.w);
   prim[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, c.w);
