@@ -36,6 +36,19 @@ def test_built_for_sm_103a():
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
 
 
+def test_kernels_compiled_replay_exact():
+    """Every pass of a method must take the same discrete decisions for a path (the replay
+    regenerates it from its seed): the path kernels are compiled without multiply-add
+    contraction, so an expression rounds the same in every kernel it is inlined into."""
+    from paper_2609_32920_gb300 import build
+    kernels = [u for u in build.UNITS if u[0] == "lt_kernels.cu"]
+    assert len(kernels) == 3
+    for _, _, extra in kernels:
+        assert "-fmad=false" in extra
+        assert not any(f.startswith("--use_fast_math") or f.startswith("-use_fast_math") for f in extra)
+    assert not any("fast_math" in f for f in build.FLAGS)
+
+
 def test_host_only_calls(liblt):
     from paper_2609_32920_gb300 import lt
     liblt.lt_version.restype = C.c_char_p
