@@ -519,10 +519,11 @@ __device__ __forceinline__ void spec_adjoint(const ChainState& s, float3 gdout, 
 
 
 // Reverse-mode sweep back through a chain ending at sliding vertex kt whose position
-// adjoint is gx_t: vertex states are replayed from the chain start (constant memory,
-// c(c+1)/2 traces for c specular vertices).  Scatters into the height gradient the
-// contributions of every primitive the chain touches and returns the adjoint of the
-// anchor position (through the chain start's incoming direction).
+// adjoint is gx_t: vertex states come from the forward walk's chain cache when it holds the
+// chain, else they are replayed from the chain start (constant memory, c(c+1)/2 traces for
+// c specular vertices).  Scatters into the height gradient the contributions of every
+// primitive the chain touches and returns the adjoint of the anchor position (through the
+// chain start's incoming direction).
 __device__ __noinline__ float3 chain_reverse(const DevScene& S, const KParams& kp, uint64_t n, const ChainInfo& c,
                                              int kt, float3 gx_t, float* dh, const ChainCache* cc, int prim_t) {
   const ChainRec* rec = nullptr;
@@ -630,6 +631,7 @@ __device__ __noinline__ void propagate_sliding(const DevScene& S, const KParams&
       for (int b = 0; b < 2; ++b)
         if (cc->r[b].len > 0 && cc->r[b].info.ka < c.ka && cc->r[b].info.ka + cc->r[b].len == c.kanchor) {
           prev = cc->r[b].info;
+          prev.lam = 0.0f;  // geometry only, as in the replay: its Fresnel factors are counted
           found = true;
         }
     if (!found && !replay_chain_of(S, kp, n, c.kanchor, prev)) { set_err(S, ERR_BOUNDS); return; }

@@ -548,3 +548,32 @@ def test_caustic_full_size_sampled_paths_match_oracle():
     receiver, 512x512, 2^24 paths, depth 8, attached (specular chains), as the bench's
     caustic study launches it."""
     _sampled_full_size_check(I.slab_scene(512, n=128, seed=0), 1 << 24, 8, 3, 4000, 62)
+
+
+# Paths of the caustic workload (slab512_hm128, seed 3) whose first specular chain reflects
+# and ends at a sliding diffuse vertex that anchors a second chain ending in a connection:
+# found by scanning the FP64 oracle's paths.
+SECOND_GENERATION_PATHS = [3369, 10344, 13028, 13605, 16623, 20825, 24369, 29502, 29615, 43839, 44944, 49760,
+                           49840, 54435, 54953, 58738, 63040, 70633, 74762, 78854]
+
+
+def test_chain_cache_matches_replay_on_second_generation_chains():
+    """The attached LRB-3 pass 3 reads chain vertex states from the forward walk's cache; the
+    naive baseline replays them.  On paths whose second chain's anchor adjoint continues
+    through an earlier, reflecting chain (geometry only: that chain's Fresnel factors are
+    counted once) both must give the same per-path height gradient, and the oracle's."""
+    sc = I.slab_scene(512, n=128, seed=0)
+    S = lt.Scene(sc)
+    N, D, seed = 1 << 24, 8, 3
+    dI_np = I.smooth_adjoint(sc.W, sc.H, 62)
+    dI = t32(dI_np)
+    for p in SECOND_GENERATION_PATHS:
+        kw = dict(seed=seed, n_paths=1, path_offset=p, n_norm=N, max_depth=D, attached=1)
+        g = S.backward_lrb3(S.opts(lrb3_state=S.new_lrb3_state(1), **kw), dI)[2].cpu().numpy()
+        o = S.opts(**kw)
+        ws = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device="cuda")
+        S.primal(o, estimator=lt.EST_NAIVE, aux=ws)
+        gn = S.backward_naive(o, dI, ws)[2].cpu().numpy()
+        ref = O.gradient(sc, dI_np, seed=seed, n_paths=1, max_depth=D, attached=1, path_begin=p, n_norm=N)
+        assert rel_l2(g, gn) < 1e-5, f"path {p}: cached and replayed chains differ"
+        assert rel_l2(g, ref["d_heights"]) < 1e-3, f"path {p}: differs from the oracle"
