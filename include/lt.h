@@ -120,7 +120,10 @@ typedef struct {
                            path's connection-validity mask there.  Set 1 in the opts of
                            lt_backward_lrb3 when that primal ran with the same seed,
                            paths, depth and scene geometry: pass 2 then takes validity
-                           from the mask and traces no visibility rays.            */
+                           from the mask, traces no visibility rays, stops each path
+                           after its last valid connection and skips the paths
+                           without one (their delta_total is zero; their stored
+                           colour words are left as they are and not read).     */
   int rr_depth;         /* Russian roulette: after each vertex of depth >= rr_depth a
                            path continues with probability rr_prob (Philox stream 2
                            of that depth) and its throughput is divided by rr_prob;
