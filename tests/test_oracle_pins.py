@@ -453,3 +453,24 @@ def test_mlp_oracle_bf16_rounding():
     rel = np.abs(a - b) / np.abs(b).mean()
     assert np.median(rel) < 1e-2 and np.max(rel) < 5e-2
     assert not np.allclose(a, b, rtol=1e-6)
+
+
+def test_filter_kink_distance_query(oracle):
+    """The per-path distance to the nearest pixel centre (where the tent filter's derivative
+    jumps) equals, for a path with exactly one connection, the distance of that connection's
+    film coordinates read from the reservoir records (which then hold the only candidate);
+    paths without a connection report 1e9, and the image equals the plain estimator's."""
+    sc = I.box_scene(24)
+    kw = dict(seed=5, n_paths=1 << 11, max_depth=3)
+    img3, kr = oracle.render(sc, estimator=3, want_records=True, **kw)
+    img0 = oracle.render(sc, **kw)
+    assert np.array_equal(img3, img0)
+    _, rr = oracle.render(sc, estimator=1, want_records=True, **kw)
+    n_conn = rr[:, 7]
+    one = (n_conn == 1) & (rr[:, 0] >= 0)
+    assert one.sum() > 100
+    u = rr[one, 2:4]
+    d = np.abs((u - 0.5) - np.round(u - 0.5)).min(axis=1)
+    assert np.allclose(kr[one, 0], d, rtol=0, atol=1e-12)
+    assert np.all(kr[n_conn == 0, 0] == 1e9)
+    assert np.all((kr[n_conn > 0, 0] >= 0) & (kr[n_conn > 0, 0] <= 0.5))
