@@ -43,21 +43,35 @@ KERNEL_SOURCES = ("lt_kernels.cu", "lt_device.cuh", "lt_launch.h", "lt_batch.h",
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "traffic_box256_hm32_2p22.md")
 
 
+def kernel_fingerprint():
+    """16 hex digits identifying the compiled kernels: the kernel sources with comments and
+    layout removed, and the kernel compiler flags (a comment edit keeps it, a code or flag
+    change does not)."""
+    import hashlib
+    import re
+
+    from paper_2609_32920_gb300 import build as B
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        src = open(os.path.join(ROOT, "paper_2609_32920_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
+    h.update(" ".join(B.ARCH + B.FLAGS + B.KERNEL_FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the LRB-3 backward pair from the committed ncu summary, or
-    None when the kernel sources have changed since that capture."""
-    import hashlib
+    None when the compiled kernels have changed since that capture."""
     import re
     try:
         text = open(TRAFFIC_PROFILE).read()
-        h = hashlib.sha256()
-        for f in KERNEL_SOURCES:
-            h.update(open(os.path.join(ROOT, "paper_2609_32920_gb300", "csrc", f), "rb").read())
-        fp = re.search(r"kernel_sources_sha256_16: (\w+)", text).group(1)
+        fp = re.search(r"kernel_fingerprint: (\w+)", text).group(1)
         tb = int(re.search(r"traffic_bytes_lrb3_backward_per_launch: (\d+)", text).group(1))
     except (OSError, AttributeError, ValueError):
         return None
-    return tb if fp == h.hexdigest()[:16] else None
+    return tb if fp == kernel_fingerprint() else None
 
 
 def workload_config(n_paths):

@@ -1101,8 +1101,10 @@ __global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
 // ======================================================================= LRB-3-pass
 // Pass 2 (accumulate delta_total, Eq. 14) and pass 3 (backpropagate, Eq. 15-17) per path,
 // run as a per-lane state machine: every iteration of the step loop performs one vertex
-// step (one closest-hit traversal) of whichever pass the lane is in, and a lane that
-// finishes a path takes the next one from its warp's range.  The connection-validity bits
+// step of whichever pass the lane is in (a closest-hit traversal of at most kTraceBudget
+// visits, resumed in the next step if the ray needs more), and a lane that finishes a
+// path takes the next one from its warp's range, in the same step as its last needed
+// vertex, drawing again over paths with nothing to trace.  The connection-validity bits
 // found in pass 2 are kept in a register mask so pass 3 traces no visibility rays.
 // BATCH: per-lane item (BatchDispenser), global gradient atomics, per-item attached flag;
 // S0, kp0, dI0 and g0 are not used.
@@ -1110,7 +1112,8 @@ __global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
 // validity mask of path p in xrec[p] (rgb, bits 0-31) and xhi[p] (bits 32-63).  MODE 2:
 // pass 3 only, starting from that state (paths without a valid connection are skipped).
 // MK (MODE 1): the primal stored each path's validity mask in xrec/xhi, so pass 2 takes
-// connection validity from it and traces no visibility rays.
+// connection validity from it, traces no visibility rays, stops after the last valid
+// connection and skips paths without one.
 // LOCAL: the calling block alone works on the path range (a span of a batch item).
 template <bool ATT, bool ST, bool CH, bool BATCH, int MODE = 0, bool MK = false, bool LOCAL = false>
 __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0, const float* __restrict__ dI0,
