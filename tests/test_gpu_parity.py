@@ -577,3 +577,37 @@ def test_chain_cache_matches_replay_on_second_generation_chains():
         ref = O.gradient(sc, dI_np, seed=seed, n_paths=1, max_depth=D, attached=1, path_begin=p, n_norm=N)
         assert rel_l2(g, gn) < 1e-5, f"path {p}: cached and replayed chains differ"
         assert rel_l2(g, ref["d_heights"]) < 1e-3, f"path {p}: differs from the oracle"
+
+
+@pytest.mark.parametrize("attached", [0, 1])
+def test_reslrb_matches_naive_in_expectation_over_256_seeds(boxhm, attached):
+    """Eq. 10: ResLRB is unbiased for the gradient; over 256 seeds its mean matches naive AD
+    (here LRB-3, which equals naive AD per seed).  Paired per seed to cancel path noise: a
+    random projection of the whole gradient's mean difference within 3 standard errors;
+    per parameter (those that receive a gradient) at most 1 % (at least one) of the
+    z-scores beyond 3.5 and their mean square near 1 (a bias of half a standard deviation
+    would put it near 64)."""
+    sc, S = boxhm
+    n, D, seeds = 1 << 12, 6, 256
+    dI = t32(I.smooth_adjoint(sc.W, sc.H, 91))
+    gi = 2 if attached else 0  # heights (attached) or albedo (detached)
+    diffs = []
+    for s in range(seeds):
+        o = S.opts(seed=5000 + s, n_paths=n, max_depth=D, attached=attached)
+        ref = S.backward_lrb3(o, dI)
+        rec = torch.zeros((n, 8), device="cuda")
+        S.primal(o, estimator=lt.EST_RESLRB, aux=rec)
+        res = S.backward_reslrb(o, dI, rec)
+        diffs.append(np.concatenate([(res[gi] - ref[gi]).cpu().numpy(), (res[1] - ref[1]).cpu().numpy()]))
+    S.sync_status()
+    d = np.array(diffs, dtype=np.float64)
+    sd = d.std(axis=0, ddof=1)
+    ok = sd > 0
+    assert ok.sum() >= 10
+    z = d.mean(axis=0)[ok] / (sd[ok] / np.sqrt(seeds))
+    assert np.sum(np.abs(z) > 3.5) <= max(1, int(np.ceil(0.01 * z.size))), np.sort(np.abs(z))[-5:]
+    assert 0.5 < np.mean(z * z) < 2.0, np.mean(z * z)
+    proj = np.random.default_rng(7).normal(size=d.shape[1]) * ok
+    p = d @ proj
+    zp = p.mean() / (p.std(ddof=1) / np.sqrt(seeds))
+    assert abs(zp) < 3.0, zp
