@@ -32,15 +32,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "box256_hm32"
-N_PATHS = 1 << 22
-DEPTH = 16
+# The headline workload: the largest single-GPU configuration, the caustic slab (a
+# dielectric slab with a 128x128 height-field top over a diffuse receiver, 512x512 film,
+# 2^24 light paths per step at depth 8, attached height gradients).  The box with a 32x32
+# diffuse height field (2^22 paths at depth 16) is timed alongside as a study.
+WORKLOADS = {
+    "slab512_hm128": dict(paths_log2=24, depth=8, resolution="512x512",
+                          geometry="dielectric slab, 128x128 height-field top (32258 + 1016 + 2 triangles) "
+                                   "over a 2x2 m diffuse receiver",
+                          params="16384 heights (+ Le)"),
+    "box256_hm32": dict(paths_log2=22, depth=16, resolution="256x256",
+                        geometry="open box of 5 textured walls + 32x32 diffuse height field (1922 triangles)",
+                        params="Le (3) + 1024 heights (+ albedo textures)"),
+}
+WORKLOAD = "slab512_hm128"
+N_PATHS = 1 << WORKLOADS[WORKLOAD]["paths_log2"]
+DEPTH = WORKLOADS[WORKLOAD]["depth"]
 METRIC = "adjoint light paths/s (LRB-3-pass attached: refit + primal + film + backward)"
 FLOPS_PER = {"node": 24, "prim": 30, "vertex": 150, "conn": 100}
 
 
 KERNEL_SOURCES = ("lt_kernels.cu", "lt_device.cuh", "lt_launch.h", "lt_batch.h", "lt_mlp.cuh")
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "traffic_box256_hm32_2p22.md")
+
+
+def traffic_profile(workload):
+    return os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
 
 
 def kernel_fingerprint():
@@ -61,24 +77,42 @@ def kernel_fingerprint():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the LRB-3 backward pair from the committed ncu summary, or
-    None when the compiled kernels have changed since that capture."""
+def profiled_traffic(workload, key):
+    """DRAM bytes per launch of kernel `key` (primal, lrb3_backward) from the committed ncu
+    summary of the workload, or None when the compiled kernels have changed since that
+    capture (or there is none)."""
     import re
     try:
-        text = open(TRAFFIC_PROFILE).read()
+        text = open(traffic_profile(workload)).read()
         fp = re.search(r"kernel_fingerprint: (\w+)", text).group(1)
-        tb = int(re.search(r"traffic_bytes_lrb3_backward_per_launch: (\d+)", text).group(1))
+        tb = int(re.search(r"traffic_bytes_%s_per_launch: (\d+)" % key, text).group(1))
     except (OSError, AttributeError, ValueError):
         return None
     return tb if fp == kernel_fingerprint() else None
 
 
-def workload_config(n_paths):
+def workload_config(n_paths, workload=None):
     """The `config` object of the JSON line (both arms)."""
-    return {"workload": WORKLOAD, "resolution": "256x256", "heightmap": "32x32 (1922 triangles)",
-            "paths_per_gpu": n_paths, "max_depth": DEPTH, "attached": True,
-            "params": "Le (3) + 1024 heights (+ albedo textures)", "l2": "flushed between steps"}
+    wl = workload or WORKLOAD
+    w = WORKLOADS[wl]
+    return {"workload": wl, "resolution": w["resolution"], "geometry": w["geometry"], "paths_per_gpu": n_paths,
+            "max_depth": w["depth"], "attached": True, "params": w["params"],
+            "l2": "flushed between steps (256 MB write outside the timed interval)"}
+
+
+def make_workload(name):
+    """(scene, target scene, paths, depth) of a named workload.  Targets: the caustic of
+    another height field (seed 1) for the slab; perturbed albedo and halved heights for the
+    box."""
+    from paper_2609_32920_gb300 import inputs as I
+    w = WORKLOADS[name]
+    if name == "slab512_hm128":
+        sc = I.slab_scene(512, n=128, seed=0)
+        tgt = I.slab_scene(512, n=128, seed=1)
+    else:
+        sc = I.box_scene(256, heightmap=32)
+        tgt = sc.with_params(albedo=I.perturbed_albedo(sc, 0.05, 1), heights=sc.heights * 0.5)
+    return sc, tgt, 1 << w["paths_log2"], w["depth"]
 
 
 def parse():
@@ -87,14 +121,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-sweep", action="store_true", help="skip the per-method and memory-vs-depth sweep")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="timed workload (profiling runs may pick the box)")
+    ap.add_argument("--paths-log2", type=int, default=0, help="paths per GPU per step (0: the workload's; "
+                                                               "profiling uses fewer)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-method and memory-vs-depth sweeps")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-oracle sample time")
-    ap.add_argument("--paths-log2", type=int, default=22, help="paths per GPU per step (profiling uses fewer)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-target study")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched many-scene study")
     ap.add_argument("--no-inverse", action="store_true", help="skip the caustic inverse-rendering study")
     ap.add_argument("--profile", action="store_true",
-                    help="profiling run: only warm-up and timed steps (no e2e, census, sweep or CPU baseline)")
+                    help="profiling run: only warm-up and timed steps (no e2e, census, studies or CPU baseline)")
     return ap.parse_args()
 
 
@@ -155,18 +192,18 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def oracle_sample(sc, dI, seconds: float, attached: int = 1):
+def oracle_sample(sc, dI, seconds: float, n_norm: int, depth: int, attached: int = 1):
     """Time the FP64 oracle (naive tape AD) on a bounded sample of the workload's paths."""
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
-    n = 64
+    n = 32
     t0 = time.perf_counter()
-    O.gradient(sc, dI, seed=0, n_paths=n, max_depth=DEPTH, attached=attached, n_norm=N_PATHS, n_threads=cores)
+    O.gradient(sc, dI, seed=0, n_paths=n, max_depth=depth, attached=attached, n_norm=n_norm, n_threads=cores)
     dt = max(time.perf_counter() - t0, 1e-3)
     n = int(min(1 << 16, max(256, n * seconds / dt)))
     t0 = time.perf_counter()
-    O.gradient(sc, dI, seed=0, n_paths=n, max_depth=DEPTH, attached=attached, n_norm=N_PATHS, n_threads=cores)
+    O.gradient(sc, dI, seed=0, n_paths=n, max_depth=depth, attached=attached, n_norm=n_norm, n_threads=cores)
     dt = time.perf_counter() - t0
     return n, dt, cores
 
@@ -175,19 +212,17 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
-
+    from oracle import oracle as O
     from paper_2609_32920_gb300 import inputs as I
-    sc = I.box_scene(256, heightmap=32)
+    sc, _, n_wl, depth = make_workload(args.workload)
     dI = I.smooth_adjoint(sc.W, sc.H, 1)
     # size one step's sample so that the whole warmup + steps run stays within a few minutes
     per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
-    n, dt, cores = oracle_sample(sc, dI, per_step)
-    from oracle import oracle as O
+    n, dt, cores = oracle_sample(sc, dI, per_step, n_wl, depth)
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        O.gradient(sc, dI, seed=i, n_paths=n, max_depth=DEPTH, attached=1, n_norm=N_PATHS, n_threads=cores)
+        O.gradient(sc, dI, seed=i, n_paths=n, max_depth=depth, attached=1, n_norm=n_wl, n_threads=cores)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     mean = sum(times) / len(times)
@@ -195,9 +230,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(N_PATHS),
+            "config": workload_config(n_wl, args.workload),
             "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{n} of the workload's {N_PATHS} paths per step (the same scene, depth and "
+                             "sample": f"{n} of the workload's {n_wl} paths per step (the same scene, depth and "
                                        f"attached gradient), naive tape reverse-mode AD in FP64 on the host cores"},
             "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -205,11 +240,106 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+class Step:
+    """One pass of the hot path on a workload: refit the height field (update_tris,
+    refit_nodes, refit_wide<4>, refit_wide<8>: every width stays current), primal light
+    tracing storing the paths' connection-validity masks (1 kernel), film L2 loss and
+    image adjoint (1), LRB-3-pass backward in its three-pass form, attached (pass 2 and
+    pass 3: 2 kernels).  Events around the primal and the backward pair time them on the
+    launching stream."""
+
+    LAUNCHES = 8
+
+    def __init__(self, name, dev, path_offset=0, n_norm=0, n_paths=0):
+        import torch
+
+        from paper_2609_32920_gb300 import lt
+        self.lt = lt
+        sc, tgt, n_wl, depth = make_workload(name)
+        self.name, self.sc, self.depth = name, sc, depth
+        self.n = n_paths or n_wl
+        self.S = S = lt.Scene(sc)
+        T_S = lt.Scene(tgt)
+        self.target = T_S.primal(T_S.opts(seed=12345, n_paths=self.n, max_depth=depth))
+        del T_S
+        self.heights = S.heights.clone()
+        self.state = S.new_lrb3_state(self.n)
+        self.path_offset, self.n_norm = path_offset, n_norm or self.n
+        kw = dict(seed=1, n_paths=self.n, max_depth=depth, path_offset=path_offset, n_norm=self.n_norm,
+                  lrb3_state=self.state)
+        self.o_plain = S.opts(**kw)
+        self.o_att = S.opts(attached=1, lrb3_mask_ready=1, **kw)
+        self.img = S.new_image()
+        self.dI = torch.empty_like(self.img)
+        self.loss = torch.empty(1, device=dev)
+        self.grads = S.new_grads()
+        self.stream = torch.cuda.current_stream()
+
+    def __call__(self, ev=None):
+        """ev: optional [primal start, primal end, backward start, backward end] events."""
+        S, lt, st = self.S, self.lt, self.stream
+        S.refit(self.heights)
+        if ev:
+            ev[0].record(st)
+        S.primal(self.o_plain, image=self.img)
+        if ev:
+            ev[1].record(st)
+        lt.film_l2(self.img, self.target, d_image=self.dI, loss=self.loss)
+        if ev:
+            ev[2].record(st)
+        S.backward_lrb3(self.o_att, self.dI, grads=self.grads)
+        if ev:
+            ev[3].record(st)
+
+    def census(self):
+        """Work of one primal and one backward pair (counting kernel variants, untimed)."""
+        import torch
+        S = self.S
+        out = {}
+        for key in ("primal", "lrb3_backward"):
+            c = torch.zeros(5, dtype=torch.int64, device=self.img.device)
+            kw = dict(seed=1, n_paths=self.n, max_depth=self.depth, path_offset=self.path_offset,
+                      n_norm=self.n_norm, census=c, lrb3_state=self.state)
+            if key == "primal":
+                S.primal(S.opts(**kw), image=S.new_image())
+            else:
+                S.backward_lrb3(S.opts(attached=1, lrb3_mask_ready=1, **kw), self.dI, grads=S.new_grads())
+            torch.cuda.synchronize()
+            v = [int(x) for x in c.cpu()]
+            flops = (FLOPS_PER["node"] * v[1] + FLOPS_PER["prim"] * v[2] + FLOPS_PER["vertex"] * v[3] +
+                     FLOPS_PER["conn"] * v[4])
+            out[key] = {"rays": v[0], "box_tests": v[1], "prim_tests": v[2], "vertices": v[3], "connections": v[4],
+                        "flops": flops}
+        return out
+
+
+def timed_steps(step, steps, flush, barrier):
+    """Run `steps` timed steps (L2 flushed before each, outside the timed interval); returns
+    per-step, per-primal and per-backward milliseconds."""
+    import torch
+    st = step.stream
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ev = [(E(), E()) for _ in range(steps)]
+    kev = [[E(), E(), E(), E()] for _ in range(steps)]
+    barrier()
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(st)
+        step(kev[i])
+        ev[i][1].record(st)
+    barrier()
+    return ([a.elapsed_time(b) for a, b in ev], [k[0].elapsed_time(k[1]) for k in kev],
+            [k[2].elapsed_time(k[3]) for k in kev])
+
+
+def device_free_bytes():
+    import torch
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
 def run_ours(args):
     import torch
-
-    global N_PATHS
-    N_PATHS = 1 << args.paths_log2
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -222,46 +352,14 @@ def run_ours(args):
 
     from paper_2609_32920_gb300 import inputs as I
     from paper_2609_32920_gb300 import lt
-
     from paper_2609_32920_gb300.shard import max_over_ranks, path_shard
-    sc = I.box_scene(256, heightmap=32)
-    S = lt.Scene(sc)
-    W, H = sc.W, sc.H
-    # weak scaling: each rank traces its own 2^22 paths, no data-path collective
-    path_offset, _, n_norm = path_shard(rank, ws, N_PATHS)
-    # target image: the same scene with perturbed albedo and heights (rendered by liblt)
-    tgt_sc = sc.with_params(albedo=I.perturbed_albedo(sc, 0.05, 1), heights=sc.heights * 0.5)
-    T_S = lt.Scene(tgt_sc)
-    target = T_S.primal(T_S.opts(seed=12345, n_paths=N_PATHS, max_depth=DEPTH))
-    del T_S
-    heights = S.heights.clone()
-    # LRB-3 in the paper's three-pass form: passes 2 and 3 are two kernels that hand over
-    # delta_total and the connection-validity mask per path (20 B per path, flat in depth);
-    # the primal stores the masks there, so pass 2 traces no visibility rays
-    lrb3_state = S.new_lrb3_state(N_PATHS)
-    o_plain = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, path_offset=path_offset, n_norm=n_norm,
-                     lrb3_state=lrb3_state)
-    o_att = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset, n_norm=n_norm,
-                   lrb3_state=lrb3_state, lrb3_mask_ready=1)
-    img = S.new_image()
-    dI = torch.empty_like(img)
-    loss = torch.empty(1, device=dev)
-    grads = S.new_grads()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    stream = torch.cuda.current_stream()
-    # update_tris, refit_nodes, refit_wide<4>, refit_wide<8> (every width stays current), primal,
-    # film_l2, lrb3 pass 2, lrb3 pass 3 (as the ncu launch list of a step shows)
-    launches_per_step = 8
 
-    def step(bwd_events=None):
-        S.refit(heights)
-        S.primal(o_plain, image=img)
-        lt.film_l2(img, target, d_image=dI, loss=loss)
-        if bwd_events:
-            bwd_events[0].record(stream)
-        S.backward_lrb3(o_att, dI, grads=grads)
-        if bwd_events:
-            bwd_events[1].record(stream)
+    wl = args.workload
+    n_paths = (1 << args.paths_log2) if args.paths_log2 else (1 << WORKLOADS[wl]["paths_log2"])
+    # weak scaling: each rank traces its own paths, no data-path collective
+    path_offset, _, n_norm = path_shard(rank, ws, n_paths)
+    step = Step(wl, dev, path_offset, n_norm, n_paths)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def barrier():
         torch.cuda.synchronize()
@@ -271,50 +369,42 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         step()
-    S.sync_status()
+    step.S.sync_status()
     clocks = Clocks(torch.cuda.current_device())
-    barrier()
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(i & 0xff)  # evict L2 between timed steps (outside the timed interval)
-        ev[i][0].record(stream)
-        step(bev[i])
-        ev[i][1].record(stream)
-    barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    bwd_ms = [a.elapsed_time(b) for a, b in bev]
+    step_ms, primal_ms, bwd_ms = timed_steps(step, args.steps, flush, barrier)
     total_ms = max_over_ranks(sum(step_ms), dev)
-    if args.profile:
-        clocks.stop()
-        if rank == 0:
-            print(json.dumps({"profile": True, "paths": N_PATHS, "ms_per_step": total_ms / args.steps,
-                              "backward_ms": statistics.median(bwd_ms)}))
-        return 0
     ms_per_step = total_ms / args.steps
-    value = ws * N_PATHS / (ms_per_step * 1e-3)
-    S.sync_status()
+    if args.profile:
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"profile": True, "workload": wl, "paths": n_paths, "ms_per_step": ms_per_step,
+                              "primal_ms": statistics.median(primal_ms), "backward_ms": statistics.median(bwd_ms),
+                              "clocks": clk}))
+        return 0
+    value = ws * n_paths / (ms_per_step * 1e-3)
+    step.S.sync_status()
 
     # ---------------- end to end through the public API with host buffers
+    S = step.S
     alb_h = S.albedo.cpu().pin_memory()
     le_h = S.Le.cpu().pin_memory()
-    hts_h = heights.cpu().pin_memory()
-    tgt_h = target.cpu().pin_memory()
-    out_h = [torch.empty(g.numel(), dtype=torch.float32).pin_memory() for g in grads]
+    hts_h = step.heights.cpu().pin_memory()
+    tgt_h = step.target.cpu().pin_memory()
+    out_h = [torch.empty(g.numel(), dtype=torch.float32).pin_memory() for g in step.grads]
     loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
     h2d = (alb_h.numel() + le_h.numel() + hts_h.numel() + tgt_h.numel()) * 4
-    d2h = (sum(g.numel() for g in grads) + 1) * 4
+    d2h = (sum(g.numel() for g in step.grads) + 1) * 4
 
     def e2e_step():
         S.albedo.copy_(alb_h, non_blocking=True)
         S.Le.copy_(le_h, non_blocking=True)
-        heights.copy_(hts_h, non_blocking=True)
-        target.copy_(tgt_h, non_blocking=True)
+        step.heights.copy_(hts_h, non_blocking=True)
+        step.target.copy_(tgt_h, non_blocking=True)
         step()
-        for g, h in zip(grads, out_h):
+        for g, h in zip(step.grads, out_h):
             h.copy_(g, non_blocking=True)
-        loss_h.copy_(loss, non_blocking=True)
+        loss_h.copy_(step.loss, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -323,23 +413,15 @@ def run_ours(args):
             for _ in range(max(3, args.steps // 2))]
     for a, b in e_ev:
         flush.fill_(1)
-        a.record(stream)
+        a.record(step.stream)
         e2e_step()
-        b.record(stream)
+        b.record(step.stream)
     barrier()
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e_ev) / len(e_ev), dev)
-    e2e_value = ws * N_PATHS / (e2e_ms * 1e-3)
+    e2e_value = ws * n_paths / (e2e_ms * 1e-3)
 
-    # ---------------- algorithmic work of the dominant kernel (counting variant, untimed)
-    census = torch.zeros(5, dtype=torch.int64, device=dev)
-    o_cnt = S.opts(seed=1, n_paths=N_PATHS, max_depth=DEPTH, attached=1, path_offset=path_offset,
-                   n_norm=N_PATHS * ws, census=census, lrb3_state=lrb3_state, lrb3_mask_ready=1)
-    S.backward_lrb3(o_cnt, dI, grads=S.new_grads())
-    torch.cuda.synchronize()
-    c = [int(x) for x in census.cpu()]
-    flops = (FLOPS_PER["node"] * c[1] + FLOPS_PER["prim"] * c[2] + FLOPS_PER["vertex"] * c[3] +
-             FLOPS_PER["conn"] * c[4])
-    bwd_mean_s = (sum(bwd_ms) / len(bwd_ms)) * 1e-3
+    # ---------------- roofline of the dominant kernel (census from the counting variants)
+    census = step.census()
     sm_max = 2070.0
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -348,56 +430,63 @@ def run_ours(args):
         pass
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 x max SM clock
-    achieved = flops / bwd_mean_s / 1e12
-    roofline = {"bound": "alu", "kernel": "LRB-3-pass backward, attached: k_lrb3_p2 + k_lrb3_p3 (passes 2 and 3)",
-                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                "traffic": profiled_traffic(), "traffic_source": "profiles/traffic_box256_hm32_2p22.md",
-                "kernel_ms": 1e3 * bwd_mean_s,
-                "census": {"rays": c[0], "box_tests": c[1], "prim_tests": c[2], "vertices": c[3],
-                           "connections": c[4], "flops_per": FLOPS_PER}}
+    kernel_ms = {"primal": sum(primal_ms) / len(primal_ms), "lrb3_backward": sum(bwd_ms) / len(bwd_ms)}
+    names = {"primal": "k_primal<PLAIN> (primal light tracing, sensor connections, splats, validity masks)",
+             "lrb3_backward": "k_lrb3_p2 + k_lrb3_p3 (LRB-3 passes 2 and 3, attached)"}
+    rooflines = {}
+    for key in kernel_ms:
+        ach = census[key]["flops"] / (kernel_ms[key] * 1e-3) / 1e12
+        rooflines[key] = {"bound": "alu", "kernel": names[key], "achieved": ach, "peak": peak_tflops,
+                          "unit": "TFLOP/s", "frac": ach / peak_tflops,
+                          "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                          "traffic": profiled_traffic(wl, key),
+                          "traffic_source": os.path.relpath(traffic_profile(wl), ROOT),
+                          "kernel_ms": kernel_ms[key], "census": census[key], "flops_per": FLOPS_PER}
+    dom = max(kernel_ms, key=kernel_ms.get)
+    roofline = dict(rooflines[dom])
+    roofline["other"] = {k: {x: rooflines[k][x] for x in ("kernel", "achieved", "frac", "kernel_ms", "traffic")}
+                         for k in rooflines if k != dom}
 
-    # ---------------- other estimators + memory vs depth (outside the headline timing)
-    methods, memory, caustic, roulette = {}, {}, None, None
+    # ---------------- studies (outside the headline timing)
+    studies = {}
+    other = "box256_hm32" if wl == "slab512_hm128" else "slab512_hm128"
+    if rank == 0:
+        studies[other] = workload_study(other, dev, flush, barrier, args.steps)
     if not args.no_sweep:
-        methods, memory = method_sweep(S, sc, target, heights, dev, path_offset, ws, flush)
-        roulette = roulette_study(S, target, dev, path_offset, ws, flush)
+        studies["methods"], studies["memory_vs_depth"] = method_sweep(step, dev, flush)
         if rank == 0:
-            caustic = caustic_sweep(dev, flush)
-    learned = None
+            box = Step("box256_hm32", dev)
+            studies["box_methods"], studies["box_memory_vs_depth"] = method_sweep(box, dev, flush)
+            studies["russian_roulette"] = roulette_study(box, dev, flush)
+            del box
     if not args.no_learned and rank == 0:
-        learned = learned_target_study(dev)
-    batched = None
+        studies["learned_target"] = learned_target_study(dev)
     if not args.no_batch and rank == 0:
-        batched = batched_study(dev)
-    inverse = None
+        studies["batched"] = batched_study(dev)
     if not args.no_inverse and rank == 0:
-        # Adam moves every height by about the learning rate per step; the slab's heights
-        # are centimetres and the caustic overshoots beyond steps of about 1 mm, so the
-        # configured 1e-3 is reported beside a rate of the problem's scale
-        inverse = {"lr_1e-3": caustic_inverse_study(dev, lr=1e-3), "lr_3e-5": caustic_inverse_study(dev, lr=3e-5)}
+        studies["caustic_inverse"] = caustic_inverse_study(dev)
     clk = clocks.stop()
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N=1 only)
     cpu = None
     if rank == 0 and ws == 1:
-        n, dt, cores = oracle_sample(sc, I.smooth_adjoint(W, H, 1), args.cpu_seconds)
+        n, dt, cores = oracle_sample(step.sc, I.smooth_adjoint(step.sc.W, step.sc.H, 1), args.cpu_seconds,
+                                     n_paths, step.depth)
         cpu = {"value": n / dt, "unit": "paths/s", "cores": cores, "kind": "oracle",
-               "sample": f"{n} of {N_PATHS} paths, depth {DEPTH}, attached naive tape AD (FP64), one gradient pass"}
+               "sample": f"{n} of the workload's {n_paths} paths, depth {step.depth}, attached naive tape AD "
+                         f"(FP64), one gradient pass"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(N_PATHS),
+                "config": workload_config(n_paths, wl),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+                "gpu_launches": Step.LAUNCHES * args.steps, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
-                "backward_ms": statistics.median(bwd_ms), "methods": methods, "memory_vs_depth": memory, "caustic_memory_vs_depth": caustic,
-                "russian_roulette": roulette,
-                "learned_target": learned, "batched": batched, "caustic_inverse": inverse,
-                "lib": lt.version()}
+                "primal_ms": statistics.median(primal_ms), "backward_ms": statistics.median(bwd_ms),
+                "studies": studies, "lib": lt.version()}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.barrier()
@@ -405,14 +494,30 @@ def run_ours(args):
     return 0
 
 
+def workload_study(name, dev, flush, barrier, steps):
+    """The same step on another workload (untimed for the headline)."""
+    step = Step(name, dev)
+    for _ in range(3):
+        step()
+    step_ms, primal_ms, bwd_ms = timed_steps(step, max(5, steps // 2), flush, barrier)
+    step.S.sync_status()
+    ms = statistics.median(step_ms)
+    return {"config": workload_config(step.n, name), "ms_per_step": ms, "paths_per_s": step.n / (ms * 1e-3),
+            "primal_ms": statistics.median(primal_ms), "backward_ms": statistics.median(bwd_ms)}
+
+
 METHODS = ("lrb3", "lrb3_fused", "lrb2", "reslrb", "naive")
 
 
 def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
-    """run(method, D, reps) -> (median ms, peak extra device bytes) of one attached
+    """run(method, D, reps) -> (median ms, peak extra bytes, device bytes) of one attached
     gradient: primal + film L2 + backward.  lrb3 = two-kernel form with its per-path
     state; lrb3_fused = one fused backward kernel without per-path state; lrb2 = the
-    buffered two-pass baseline (per-vertex splat records, linear in depth)."""
+    buffered two-pass baseline (per-vertex splat records, linear in depth).  Peak extra
+    bytes: torch's peak allocation above the scene's; device bytes: the fall of the
+    device's free memory (cudaMemGetInfo) from before the method's buffers are allocated
+    to after its first gradient, which also sees what the driver reserves for the kernels
+    (local memory of traversal stacks and chain caches)."""
     import torch
 
     from paper_2609_32920_gb300 import lt
@@ -424,6 +529,8 @@ def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
 
     def run(method, D, timed_reps=3):
         torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free0 = device_free_bytes()
         base = torch.cuda.memory_allocated()
         torch.cuda.reset_peak_memory_stats()
         aux = None
@@ -457,6 +564,7 @@ def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
         once()
         torch.cuda.synchronize()
         peak = torch.cuda.max_memory_allocated() - base
+        dev_bytes = free0 - device_free_bytes()
         ms = []
         for _ in range(timed_reps):
             flush.fill_(2)
@@ -468,52 +576,55 @@ def _pipeline_runner(S, target, dev, n_paths, path_offset, n_norm, flush):
             ms.append(a.elapsed_time(b))
         del aux, state
         torch.cuda.empty_cache()
-        return statistics.median(ms), peak
+        return statistics.median(ms), peak, dev_bytes
 
     return run
 
 
-def method_sweep(S, sc, target, heights, dev, path_offset, ws, flush):
-    """Paths/s of each estimator (primal + backward, attached) at depth 16 and the peak
-    extra device memory of each estimator at depths 4..64 (box with the 32x32 height field)."""
-    run = _pipeline_runner(S, target, dev, N_PATHS, path_offset, N_PATHS * ws, flush)
-    methods = {}
+def method_sweep(step, dev, flush):
+    """Paths/s of each estimator (primal + film + backward, attached) at the workload's depth,
+    and the extra device memory of each estimator at depths 4..64 (torch's peak allocation
+    and the device's own free-memory drop)."""
+    S, n = step.S, step.n
+    run = _pipeline_runner(S, step.target, dev, n, step.path_offset, step.n_norm, flush)
+    methods = {"workload": f"{step.name}, 2^{n.bit_length() - 1} paths, depth {step.depth}, attached"}
     for m in METHODS:
-        ms, peak = run(m, DEPTH)
-        methods[m] = {"paths_per_s": N_PATHS / (ms * 1e-3), "ms": ms, "extra_bytes": peak}
-    memory = {}
+        ms, peak, dbytes = run(m, step.depth)
+        methods[m] = {"paths_per_s": n / (ms * 1e-3), "ms": ms, "extra_bytes": peak, "device_bytes": dbytes}
+    memory = {"workload": f"{step.name}, 2^{n.bit_length() - 1} paths, attached"}
     for D in (4, 8, 16, 32, 64):
         memory[str(D)] = {}
         for m in METHODS:
-            ms, peak = run(m, D, timed_reps=1)
-            memory[str(D)][m] = {"extra_bytes": peak, "ms": ms}
+            ms, peak, dbytes = run(m, D, timed_reps=1)
+            memory[str(D)][m] = {"extra_bytes": peak, "device_bytes": dbytes, "ms": ms}
+    S.sync_status()
     return methods, memory
 
 
-def roulette_study(S, target, dev, path_offset, ws, flush, rr_depth=4, rr_prob=0.8):
+def roulette_study(step, dev, flush, rr_depth=4, rr_prob=0.8):
     """Time of one attached LRB-3 gradient (primal + film + backward) on the box workload
     with Russian roulette (continue with probability 0.8 after depth 4) and without it,
     at depths 16 and 64."""
     import torch
 
     from paper_2609_32920_gb300 import lt
+    S, n = step.S, step.n
     stream = torch.cuda.current_stream()
     img = S.new_image()
     dI = torch.empty_like(img)
     loss = torch.empty(1, device=dev)
     grads = S.new_grads()
-    state = S.new_lrb3_state(N_PATHS)
+    state = S.new_lrb3_state(n)
     out = {"setting": "continue with probability %g after depth %d" % (rr_prob, rr_depth)}
     for D in (16, 64):
         row = {}
         for name, rr in (("off", {}), ("on", dict(rr_depth=rr_depth, rr_prob=rr_prob))):
-            kw = dict(seed=5, n_paths=N_PATHS, max_depth=D, attached=1, path_offset=path_offset,
-                      n_norm=N_PATHS * ws, lrb3_state=state, **rr)
+            kw = dict(seed=5, n_paths=n, max_depth=D, attached=1, lrb3_state=state, **rr)
             op, om = S.opts(**kw), S.opts(lrb3_mask_ready=1, **kw)
 
             def once():
                 S.primal(op, image=img)
-                lt.film_l2(img, target, d_image=dI, loss=loss)
+                lt.film_l2(img, step.target, d_image=dI, loss=loss)
                 S.backward_lrb3(om, dI, grads=grads)
             once()
             ms = []
@@ -525,33 +636,8 @@ def roulette_study(S, target, dev, path_offset, ws, flush, rr_depth=4, rr_prob=0
                 b.record(stream)
                 torch.cuda.synchronize()
                 ms.append(a.elapsed_time(b))
-            row[name] = {"ms": statistics.median(ms), "paths_per_s": N_PATHS / (statistics.median(ms) * 1e-3)}
+            row[name] = {"ms": statistics.median(ms), "paths_per_s": n / (statistics.median(ms) * 1e-3)}
         out[str(D)] = row
-    return out
-
-
-def caustic_sweep(dev, flush, paths_log2=24):
-    """The caustic workload: a 512x512 camera over a dielectric slab with a 128x128 height
-    field (32k triangles) above a diffuse receiver, 2^24 paths per gradient, attached
-    height gradients of an L2 loss against the caustic of another height field.  Time and
-    peak extra device memory of every estimator at depths 4..64."""
-    import torch
-
-    from paper_2609_32920_gb300 import inputs as I
-    from paper_2609_32920_gb300 import lt
-    n = 1 << paths_log2
-    S = lt.Scene(I.slab_scene(512, n=128, seed=0))
-    T_S = lt.Scene(I.slab_scene(512, n=128, seed=1))
-    target = T_S.primal(T_S.opts(seed=7, n_paths=n, max_depth=8))
-    del T_S
-    run = _pipeline_runner(S, target, dev, n, 0, n, flush)
-    out = {"workload": "slab512_hm128 (caustic), 2^%d paths, attached heights" % paths_log2}
-    for D in (4, 8, 16, 32, 64):
-        out[str(D)] = {}
-        for m in METHODS:
-            ms, peak = run(m, D, timed_reps=1)
-            out[str(D)][m] = {"extra_bytes": peak, "ms": ms, "paths_per_s": n / (ms * 1e-3)}
-    S.sync_status()
     return out
 
 

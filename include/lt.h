@@ -90,10 +90,14 @@ typedef struct {
   const float* Le;       /* [3]        */
 } lt_params;
 
+/* Largest n_paths and path_offset any call accepts (LT_ERR_INVALID_ARG beyond): every byte
+ * count derived from a path count then fits in size_t with room to spare. */
+#define LT_MAX_PATHS ((int64_t)1 << 40)
+
 typedef struct {
   uint64_t seed;        /* Philox key                                               */
   int64_t path_offset;  /* first path index (Philox counter) traced by this call    */
-  int64_t n_paths;      /* number of paths traced by this call                      */
+  int64_t n_paths;      /* number of paths traced by this call (<= LT_MAX_PATHS)    */
   int64_t n_norm;       /* N of the estimator's 1/N; 0 means n_paths                */
   int max_depth;        /* traced intersections x1..xD per path, 1..64              */
   int attached;         /* 0 detached, 1 attached (geometry derivatives)            */
@@ -104,26 +108,29 @@ typedef struct {
   const uint8_t* path_mask; /* DEVICE [n_paths] optional: 0 = skip path (testing)   */
   uint32_t* path_hash;  /* DEVICE [n_paths] optional out: decision hash per path    */
   float* path_dbg;      /* DEVICE [n_paths][4] optional out (see each call)         */
-  uint64_t* census;     /* DEVICE [5] optional out, lt_backward_lrb3 only: adds the
-                           work done (rays traced, BVH box tests, primitive tests,
-                           path vertices, valid connections) using a counting kernel
-                           variant; for measurement, not for timed runs           */
+  uint64_t* census;     /* DEVICE [5] optional out, lt_backward_lrb3 and
+                           lt_primal(LT_EST_PLAIN) only: adds the work done (rays
+                           traced, BVH box tests, primitive tests, path vertices,
+                           valid connections) using a counting kernel variant; for
+                           measurement, not for timed runs                        */
   void* lrb3_state;     /* DEVICE optional, for lt_backward_lrb3 (and written by a
                            plain lt_primal, see lrb3_mask_ready): per-path state of
                            lt_lrb3_state_bytes(opts) bytes.  Given, passes 2 and 3 run
                            as two kernels and pass 2 stores each path's delta_total
-                           and connection-validity mask there (20 B per path, the
-                           paper's three-pass form); NULL, one fused kernel keeps
-                           them in registers.  Same result either way.            */
+                           and connection-validity mask there (the paper's three-pass
+                           form; 24 B per path, flat in depth); NULL, one fused kernel
+                           keeps them in registers.  Same result either way.      */
   size_t lrb3_state_bytes; /* size of lrb3_state                                    */
   int lrb3_mask_ready;  /* lt_primal(LT_EST_PLAIN) given lrb3_state also stores each
-                           path's connection-validity mask there.  Set 1 in the opts of
+                           path's connection-validity mask there, and the list of the
+                           paths that have a valid connection.  Set 1 in the opts of
                            lt_backward_lrb3 when that primal ran with the same seed,
                            paths, depth and scene geometry: pass 2 then takes validity
                            from the mask, traces no visibility rays, stops each path
-                           after its last valid connection and skips the paths
-                           without one (their delta_total is zero; their stored
-                           colour words are left as they are and not read).     */
+                           after its last valid connection, and passes 2 and 3 visit
+                           only the listed paths (the others have delta_total zero;
+                           their stored colour words and path_dbg rows are left as
+                           they are and not read).                              */
   int rr_depth;         /* Russian roulette: after each vertex of depth >= rr_depth a
                            path continues with probability rr_prob (Philox stream 2
                            of that depth) and its throughput is divided by rr_prob;
@@ -223,8 +230,9 @@ lt_status lt_film_l2(const float* image, const float* target, int64_t n, float* 
 
 /* Training pairs from an LRB-3 pass-2 replay (Eq. 14): for every valid connection, its 16
  * features into feats [capacity][16] and its target log(|Lbar*L|_1 / lum(L) + floor) into
- * targets [capacity] (DEVICE).  *count (DEVICE int64, zeroed by this call) receives the
- * number of connections found; only the first `capacity` are written. */
+ * targets [capacity] (DEVICE), in no particular order (rows are claimed atomically).
+ * *count (DEVICE int64, zeroed by this call) receives the number of connections found;
+ * only the first `capacity` are written.  opts->path_mask skips paths. */
 lt_status lt_mlp_collect(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
                          const float* d_image, float target_floor, float* feats, float* targets,
                          int64_t capacity, int64_t* count, void* stream);
@@ -261,7 +269,10 @@ lt_status lt_mlp_forward(const float* mlp, const float* feats, int64_t n, float*
  *    rejected with LT_ERR_INVALID_ARG; nothing is launched.
  *  - The scene's device must be the current device.  The first call on a device looks up
  *    the scratch array's device address for that device (once, cached afterwards); make
- *    that first call before any stream capture on that device begins.
+ *    that first call before any stream capture on that device begins.  The cached address
+ *    belongs to the device's current context: after cudaDeviceReset (or any other teardown
+ *    of the primary context) the library may be loaded at another address, so do not call
+ *    this function again in that process after such a reset.
  *  - All calls on a device share the one array and it keeps whatever the last call left;
  *    each call writes every tape entry it later reads, so nothing needs clearing, but two
  *    calls whose work overlaps on the GPU (for example on two streams) race on the array
@@ -348,6 +359,52 @@ lt_status lt_batch_tune(lt_batch* batch, int pass, int reps, void* stream, lt_ba
 
 void lt_batch_destroy(lt_batch* batch);
 
+/* ---------------------------------------------------------------------------------
+ * Bidirectional estimator: the paper's light tracer combined with camera-side samples, the
+ * "combined bidirectional formulation" its discussion names as a next step ("Toward more
+ * complex integrators": path replay backpropagation on the camera side, LRB-3-pass on the
+ * light side).  Two strategies estimate the same paths x0 (on the emitter), x1..xk
+ * (diffuse) -> camera:
+ *   light: a light path and its sensor connection at xk (opts->n_paths paths, Sec. 3.1);
+ *   camera: a camera sample through a film position uniform over the film, traced to
+ *       xk = y1, x(k-1) = y2, ... by cosine sampling, with next-event estimation from
+ *       x1 = ym to a point x0 uniform on the emitter (n_cam samples, Philox stream 3:
+ *       counter (c, 0) the film position, (c, m) at camera vertex m the cosine direction
+ *       (u0, u1) and the emitter point (u2, u3)).
+ * They are combined with the balance heuristic: with Lambertian surfaces, cosine sampling
+ * and cosine emission a segment between two surfaces has the same area density in both
+ * directions, so the density ratio of the camera strategy to the light strategy is
+ * R = p_film(xk) / pf0 (the film's area density at xk over the light tracer's density of x1
+ * from x0, cos0 cos1 / (pi r01^2)), and a sample of either strategy splats
+ * N L / (N + M R) (L: the light tracer's splat value of the path, which carries 1/N;
+ * N = opts->n_norm or n_paths, M = n_cam).  Each camera sample splats the sum of its
+ * vertices' contributions at its film position.  Which strategy owns a path is thus a
+ * weight, not a choice: every path reaches the image through both, in proportions N : M R.
+ * Detached only (albedo, Le); scenes without dielectrics; no Russian roulette
+ * (LT_ERR_UNSUPPORTED otherwise).  The camera side's adjoint is path replay
+ * backpropagation: a camera sample contributes at one film position, so one adjoint read
+ * serves all its vertices; a first walk sums the contributions, a replay weights each
+ * vertex's albedo with the adjoint of the contributions from that vertex on.  The light
+ * side's adjoint is LRB-3-pass (Eq. 14-17) with the weights (constant in the parameters).
+ * Memory is constant in depth on both sides. */
+typedef struct {
+  int64_t n_cam;            /* camera samples M (0..LT_MAX_PATHS)                         */
+  const uint8_t* cam_mask;  /* DEVICE [n_cam] optional: 0 = skip the sample (testing)     */
+  uint32_t* cam_hash;       /* DEVICE [n_cam] optional out (lt_bidir_primal): decision hash
+                               of each camera sample (primitives hit, next-event validity) */
+} lt_bidir_opts;
+
+/* Bidirectional image: image DEVICE [H][W][3], overwritten.  opts->path_hash (optional)
+ * receives the light paths' decision hashes. */
+lt_status lt_bidir_primal(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                          const lt_bidir_opts* bidir, float* image, void* stream);
+
+/* Gradient of <d_image, I_bidir> (albedo and Le; d_heights, if given, is zeroed unless
+ * accumulate): LRB-3-pass on the light paths, path replay backpropagation on the camera
+ * samples, both with the same opts and bidir as the primal. */
+lt_status lt_bidir_backward(lt_scene* scene, const lt_params* params, const lt_render_opts* opts,
+                            const lt_bidir_opts* bidir, const float* d_image, const lt_grads* grads, void* stream);
+
 /* Buffered two-pass backward (the paper's lrb_2pass baseline, Sec. 4.1 and Sec. 6.2): the
  * primal lt_primal(LT_EST_BUFFERED) splats like LT_EST_PLAIN and also stores every traced
  * vertex's splat record (film position and contribution L_i, 20 B per vertex, memory
@@ -363,12 +420,13 @@ lt_status lt_backward_lrb2(lt_scene* scene, const lt_params* params, const lt_re
 size_t lt_lrb2_buffer_bytes(const lt_render_opts* opts);
 
 /* Bytes of the optional LRB-3 per-path state (opts->lrb3_state): 16 B (delta_total rgb,
- * validity bits 0-31) then 4 B (validity bits 32-63) per path, each array 256-B aligned. */
+ * validity bits 0-31), 4 B (validity bits 32-63) and 4 B (the list of paths with a valid
+ * connection) per path, each array 256-B aligned, then the list's length (8 B). */
 size_t lt_lrb3_state_bytes(const lt_render_opts* opts);
 
 /* Bytes of one ResLRB record (constant per path). */
 size_t lt_record_size(const lt_render_opts* opts);
-/* Bytes of the naive-AD tape for opts (n_paths * max_depth * record). */
+/* Bytes of the naive-AD tape for opts (n_paths * max_depth * record); 0 for invalid opts. */
 size_t lt_naive_workspace_bytes(const lt_render_opts* opts);
 
 /* Read and clear the scene's device error word (synchronises `stream`). */

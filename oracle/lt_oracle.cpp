@@ -20,8 +20,13 @@
 //                    method 3: ResLRB restated in its replay form, detached only (Eq. 11).
 //   * or_render_pt   a camera-side path tracer with next-event estimation, used only to
 //                    pin the light tracer's normalisation by reciprocity.
+//   * or_render_bidir, or_gradient_bidir  a bidirectional estimator: light-tracer sensor
+//                    connections and camera samples with next-event estimation, combined
+//                    with the balance heuristic, and naive tape AD of it (detached).
 //   * helpers exported for pinning tests: Philox, dielectric sampling, reservoir draw,
-//                    the frozen-decision loss (for finite differences).
+//                    the frozen-decision loss (for finite differences), and every sensor
+//                    connection's values (or_connections: the training pairs of the
+//                    learned reservoir target are built from them).
 //   * every method optionally applies Russian roulette with a fixed survival probability
 //     (see trace()), the path-termination rule the CUDA path replays identically, and
 //     either the tent or a wider truncated-Gaussian reconstruction filter (filter_taps).
@@ -558,6 +563,14 @@ template <class T> struct ConnOut {
   int vi;
   T L[3];
   T ux, uy;
+  // values at the connection, for the per-connection query (or_connections): position,
+  // arrival-side unit normal, arrival direction, throughput before the vertex's albedo and
+  // the connection weight (importance with the estimator's 1/N)
+  D3 x, ns, din;
+  double beta[3], geo;
+  // area density of the path's first vertex x1 as the light tracer samples it from x0
+  // (cosine emission): cos0 cos1 / (pi r01^2); used by the bidirectional weights
+  double pf0;
 };
 
 // Evaluate the frozen-decision path function: per valid sensor connection i, the splat
@@ -578,6 +591,7 @@ void eval_path(const Scene& sc, const Path& P, const AA& albedo, const AL& Le, c
   for (int c = 0; c < 3; ++c) beta[c] = Le[c] * T(A_L * PI);
   Vec<T> xprev = lift<T>(P.x0), nprev = lift<T>(P.n_light), dprev = mk<T>(0.0, 0.0, 0.0);
   const double K = (double)sc.s->W * (double)sc.s->H / (sc.A_img * N * PI);
+  double pf0 = 0.0;
   for (size_t k = 0; k < P.v.size(); ++k) {
     const Vtx& v = P.v[k];
     Vec<T> o, e1, e2;
@@ -594,6 +608,7 @@ void eval_path(const Scene& sc, const Path& P, const AA& albedo, const AL& Le, c
       T r2 = dot(w, w);
       din = w * (T(1.0) / sqrt(r2));
       T g = fabs(dot(nprev, din)) * fabs(dot(n, din)) * area / r2;
+      if (k == 0) pf0 = std::fabs(val(dot(nprev, din))) * std::fabs(val(dot(n, din))) / (PI * val(r2));
       if (fill) fill->v[k].g0 = val(g);
       T ratio = g / T(v.g0 > 0 ? v.g0 : val(g));
       for (int c = 0; c < 3; ++c) beta[c] = beta[c] * ratio;
@@ -623,6 +638,10 @@ void eval_path(const Scene& sc, const Path& P, const AA& albedo, const AL& Le, c
         T cc = zc / dist;
         T geo = cosc * T(K) / (dist2 * cc * cc * cc);
         for (int c = 0; c < 3; ++c) co.L[c] = beta[c] * rho[c] * geo;
+        co.x = vval(x); co.ns = vval(ns); co.din = vval(din);
+        for (int c = 0; c < 3; ++c) co.beta[c] = val(beta[c]);
+        co.geo = val(geo);
+        co.pf0 = pf0;
         out.push_back(co);
       }
       for (int c = 0; c < 3; ++c) beta[c] = beta[c] * rho[c];
@@ -721,6 +740,130 @@ void texel_weights(const Scene& sc, int m, double s, double t, int idx[4], doubl
   idx[1] = off + (ya * tw + xb) * 3; w[1] = fx * (1 - fy);
   idx[2] = off + (yb * tw + xa) * 3; w[2] = (1 - fx) * fy;
   idx[3] = off + (yb * tw + xb) * 3; w[3] = fx * fy;
+}
+
+// ---------------------------------------------------------------- bidirectional estimator
+// Two strategies for the same paths x0 (on the emitter), x1..xk (diffuse) -> camera, combined
+// with the balance heuristic (Veach's multiple importance sampling):
+//   L: a light path of the light tracer and its sensor connection at xk (N light paths);
+//   C: a camera sample through a film position u uniform over the film, traced to
+//      xk = y1, x_{k-1} = y2, ... by cosine sampling, with next-event estimation from
+//      x1 = ym to a point x0 uniform on the emitter (M camera samples).
+// With Lambertian surfaces, cosine sampling and cosine emission, the area densities of a
+// segment between two surfaces are the same in both directions (cos cos / (pi r^2)), so
+// the density ratio of C to L of a path reduces to
+//   R = p_film(xk) / pf0,   p_film(xk) = cos_c / (A_img cos^3(theta_c) r_c^2),
+//   pf0 = cos0 cos1 / (pi r01^2)  (x1 sampled from x0 by the light tracer),
+// and either strategy's sample contributes  N L / (N + M R)  where L is the light tracer's
+// splat value of the path (which carries 1/N): strategy L is weighted by N / (N + M R),
+// strategy C by M R / (N + M R).  Diffuse scenes, detached, no Russian roulette.
+struct CamVtx {
+  int prim;
+  double b1, b2;
+  D3 x, ns;       // position and the unit normal on the side the camera path arrives from
+  bool nee;       // valid next-event connection at this vertex
+  D3 xl;          // its emitter point
+};
+struct CamPath {
+  double ux, uy;
+  std::vector<CamVtx> v;
+  uint32_t hash = 2166136261u;
+};
+
+// Camera sample c: Philox stream 3, counter (c, 0) the film position, (c, m) at vertex m the
+// cosine direction (u0, u1) and the emitter point of the next-event connection (u2, u3).
+CamPath trace_cam(const Scene& sc, uint64_t seed, uint64_t c, int D) {
+  CamPath P;
+  const double* h = sc.p->heights;
+  D3 lo, le1, le2;
+  sc.prim<double>(sc.s->emitter_quad, h, lo, le1, le2);
+  const D3 nL = normalize(cross(le1, le2));
+  Rand4 r0 = rand4(seed, c, 0, 3);
+  P.ux = r0.u[0] * sc.s->W;
+  P.uy = r0.u[1] * sc.s->H;
+  double pxn = (2 * P.ux / sc.s->W - 1) * sc.tanx, pyn = (1 - 2 * P.uy / sc.s->H) * sc.tany;
+  D3 dir = normalize(sc.cf + sc.cr * pxn + sc.cu * pyn);
+  D3 org = sc.cpos;
+  int skip = -1;
+  for (int m = 1; m <= D; ++m) {
+    int prim;
+    double tt, su, sv;
+    if (!closest(sc, org, dir, skip, prim, tt, su, sv)) break;
+    if (sc.mtype(prim) != 0) break;  // the emitter absorbs (seen directly it is black)
+    CamVtx v;
+    v.prim = prim; v.b1 = su; v.b2 = sv;
+    D3 o, e1, e2;
+    sc.prim<double>(prim, h, o, e1, e2);
+    v.x = o + e1 * su + e2 * sv;
+    D3 nrm = normalize(cross(e1, e2));
+    v.ns = dot(nrm, dir) < 0 ? nrm : nrm * -1.0;
+    Rand4 r = rand4(seed, c, (uint32_t)m, 3);
+    v.xl = lo + le1 * r.u[2] + le2 * r.u[3];
+    D3 wl = v.xl - v.x;
+    double dist = norm(wl);
+    D3 wn = wl * (1.0 / dist);
+    v.nee = dot(v.ns, wn) > 0 && -dot(nL, wn) > 0 && !occluded(sc, v.x, wn, dist, prim);
+    fnv(P.hash, (uint32_t)prim);
+    fnv(P.hash, v.nee ? 1u : 0u);
+    P.v.push_back(v);
+    D3 ta, tb;
+    onb(v.ns, ta, tb);
+    double r1 = std::sqrt(r.u[0]), p1 = 2 * PI * r.u[1];
+    dir = ta * (r1 * std::cos(p1)) + tb * (r1 * std::sin(p1)) + v.ns * std::sqrt(std::max(0.0, 1 - r.u[0]));
+    org = v.x;
+    skip = prim;
+  }
+  return P;
+}
+
+// Contribution of a camera sample, summed over its valid next-event connections (all splat
+// at its film position): the connection at y_m closes the path x0 = xl, x1 = y_m, ...,
+// xk = y_1 (k = m), whose light-tracer value times N is
+//   Le A_L pi prod_{j=1..m} rho(y_j) geo(y_1),
+// geo = cos_c W H / (A_img pi r_c^2 cos^3 theta_c) (the sensor connection at y_1); the
+// sample adds it divided by (N + M R).  Values are evaluated with AD-capable albedo and Le.
+template <class T, class AA, class AL>
+void eval_cam(const Scene& sc, const CamPath& P, const AA& albedo, const AL& Le, double N, double M, T out[3]) {
+  for (int c = 0; c < 3; ++c) out[c] = T(0.0);
+  if (P.v.empty()) return;
+  D3 lo, le1, le2;
+  sc.prim<double>(sc.s->emitter_quad, sc.p->heights, lo, le1, le2);
+  const D3 nL = normalize(cross(le1, le2));
+  const double A_L = norm(cross(le1, le2));
+  const D3 d = P.v[0].x - sc.cpos;
+  const double dist = norm(d), cc = dot(d, sc.cf) / dist;
+  const double cosc = -dot(P.v[0].ns, d) / dist;
+  const double W = sc.s->W, H = sc.s->H;
+  const double geo1 = cosc * W * H / (sc.A_img * PI * dist * dist * cc * cc * cc);
+  const double pfilm = cosc / (sc.A_img * cc * cc * cc * dist * dist);
+  T thr[3] = {T(1.0), T(1.0), T(1.0)};
+  for (const CamVtx& v : P.v) {
+    T rho[3];
+    tex_lookup<T>(sc, sc.mat(v.prim), albedo, T(v.b1), T(v.b2), rho);
+    for (int c = 0; c < 3; ++c) thr[c] = thr[c] * rho[c];
+    if (!v.nee) continue;
+    const D3 wl = v.xl - v.x;
+    const double dl = norm(wl);
+    const D3 wn = wl * (1.0 / dl);
+    const double pf0 = dot(v.ns, wn) * -dot(nL, wn) / (PI * dl * dl);
+    const double wgt = A_L * PI * geo1 / (N + M * (pfilm / pf0));
+    for (int c = 0; c < 3; ++c) out[c] = out[c] + Le[c] * thr[c] * T(wgt);
+  }
+}
+
+// Balance-heuristic weight N / (N + M R) of a light-tracer connection (see above).
+double light_weight(const Scene& sc, const ConnOut<double>& c, double N, double M) {
+  if (M <= 0) return 1.0;
+  const double pfilm = c.geo * N * PI / ((double)sc.s->W * (double)sc.s->H);
+  return N / (N + M * (pfilm / c.pf0));
+}
+
+int bidir_check(const or_scene* s, const or_run* run) {
+  if (run->attached) return -1;
+  for (int m = 0; m < s->n_mats; ++m)
+    if (s->mat_type[m] == 1) return -2;
+  if (run->rr_depth > 0) return -3;
+  return 0;
 }
 
 }  // namespace
@@ -978,6 +1121,40 @@ int or_gradient(const or_scene* s, const or_params* p, const or_run* run, const 
   return 0;
 }
 
+// Every valid sensor connection of the paths (in path order, skipping masked paths), one
+// row of 24 doubles each: path index, vertex index k (depth k+1), position x[3], arrival-side
+// unit normal[3], unit arrival direction[3], throughput before the vertex's albedo[3], film
+// position u_x, u_y, connection weight (importance including the estimator's 1/N), the
+// splat L[3] (Eq. 1) and its filter-weighted adjoint read Lbar[3] (Eq. 21), 0.  At most
+// `cap` rows are written; returns the number of connections.
+int64_t or_connections(const or_scene* s, const or_params* p, const or_run* run, const double* dI,
+                       const uint8_t* mask, double* rows, int64_t cap) {
+  Scene sc{s, p};
+  sc.setup();
+  const double N = (double)(run->n_norm > 0 ? run->n_norm : run->n_paths);
+  std::vector<ConnOut<double>> cs;
+  int64_t count = 0;
+  for (int64_t i = 0; i < run->n_paths; ++i) {
+    if (mask && !mask[i]) continue;
+    uint64_t n = (uint64_t)(run->path_begin + i);
+    Path P = trace(sc, run->seed, n, run->max_depth, run->rr_depth, run->rr_q);
+    eval_path<double>(sc, P, Plain{p->albedo}, Plain{p->Le}, Plain{p->heights}, N, cs, &P);
+    for (auto& c : cs) {
+      if (count < cap) {
+        double* r = rows + 24 * count;
+        double Lb[3];
+        adjoint_read<double>(dI, s->W, s->H, c.ux, c.uy, Lb, run->filter);
+        const double v[24] = {(double)i, (double)c.vi, c.x.x, c.x.y, c.x.z, c.ns.x, c.ns.y, c.ns.z,
+                              c.din.x, c.din.y, c.din.z, c.beta[0], c.beta[1], c.beta[2], c.ux, c.uy, c.geo,
+                              c.L[0], c.L[1], c.L[2], Lb[0], Lb[1], Lb[2], 0.0};
+        for (int k = 0; k < 24; ++k) r[k] = v[k];
+      }
+      ++count;
+    }
+  }
+  return count;
+}
+
 // <dI, I_s> with every decision taken at parameters p0 and every value evaluated at p1
 // (the frozen-decision function whose derivative all methods compute).  method 0: all
 // connections; method 2: the ResLRB estimator (winner and weight frozen at p0).
@@ -1014,6 +1191,137 @@ double or_frozen_loss(const or_scene* s, const or_params* p0, const or_params* p
   double v = 0;
   for (double x : part) v += x;
   return v;
+}
+
+// Bidirectional estimator (light tracer + camera samples with next-event estimation,
+// balance heuristic; see above): image [H][W][3] overwritten.  N = run->n_norm (or
+// n_paths) light paths from run, n_cam camera samples (indices 0..n_cam-1).  Optional
+// per-sample decision hashes of the light paths (hashes [n_paths]) and camera samples
+// (cam_hashes [n_cam]); masks skip paths / samples.  Returns < 0 for unsupported requests
+// (attached, dielectrics, Russian roulette).
+int or_render_bidir(const or_scene* s, const or_params* p, const or_run* run, int64_t n_cam, const uint8_t* mask,
+                    const uint8_t* cam_mask, double* image, uint32_t* hashes, uint32_t* cam_hashes) {
+  const int bad = bidir_check(s, run);
+  if (bad) return bad;
+  Scene sc{s, p};
+  sc.setup();
+  const int64_t npx = (int64_t)s->W * s->H * 3;
+  const double N = (double)(run->n_norm > 0 ? run->n_norm : run->n_paths), M = (double)n_cam;
+  int nt = std::max(1, run->n_threads);
+  std::vector<Acc> acc(nt);
+  parallel_paths(nt, run->n_paths, [&](int tid, int64_t a, int64_t b) {
+    Acc& A = acc[tid];
+    A.img.assign(npx, 0.0);
+    std::vector<ConnOut<double>> cs;
+    for (int64_t i = a; i < b; ++i) {
+      uint64_t n = (uint64_t)(run->path_begin + i);
+      Path P = trace(sc, run->seed, n, run->max_depth, 0, 1.0);
+      if (hashes) hashes[i] = P.hash;
+      if (mask && !mask[i]) continue;
+      eval_path<double>(sc, P, Plain{p->albedo}, Plain{p->Le}, Plain{p->heights}, N > 0 ? N : 1.0, cs, &P);
+      for (auto& c : cs) {
+        const double w = light_weight(sc, c, N, M);
+        double L[3] = {c.L[0] * w, c.L[1] * w, c.L[2] * w};
+        splat(sc, A.img.data(), L, c.ux, c.uy, run->filter);
+      }
+    }
+  });
+  std::vector<Acc> cacc(nt);
+  parallel_paths(nt, n_cam, [&](int tid, int64_t a, int64_t b) {
+    Acc& A = cacc[tid];
+    A.img.assign(npx, 0.0);
+    for (int64_t c = a; c < b; ++c) {
+      CamPath P = trace_cam(sc, run->seed, (uint64_t)c, run->max_depth);
+      if (cam_hashes) cam_hashes[c] = P.hash;
+      if (cam_mask && !cam_mask[c]) continue;
+      double L[3];
+      eval_cam<double>(sc, P, Plain{p->albedo}, Plain{p->Le}, N, M, L);
+      splat(sc, A.img.data(), L, P.ux, P.uy, run->filter);
+    }
+  });
+  for (int64_t j = 0; j < npx; ++j) {
+    double v = 0;
+    for (int t = 0; t < nt; ++t) {
+      v += acc[t].img.size() ? acc[t].img[j] : 0.0;
+      v += cacc[t].img.size() ? cacc[t].img[j] : 0.0;
+    }
+    image[j] = v;
+  }
+  return 0;
+}
+
+// Naive reverse-mode AD (tape per light path and per camera sample) of <dI, I_bidir> for
+// the bidirectional estimator of or_render_bidir: albedo and Le gradients (detached; the
+// balance-heuristic weights depend on the geometry only).  Outputs are overwritten.
+int or_gradient_bidir(const or_scene* s, const or_params* p, const or_run* run, int64_t n_cam, const double* dI,
+                      const uint8_t* mask, const uint8_t* cam_mask, or_grads* out) {
+  const int bad = bidir_check(s, run);
+  if (bad) return bad;
+  Scene sc{s, p};
+  sc.setup();
+  const double N = (double)(run->n_norm > 0 ? run->n_norm : run->n_paths), M = (double)n_cam;
+  const int W = s->W, H = s->H;
+  int nt = std::max(1, run->n_threads);
+  std::vector<Acc> acc(nt);
+  auto body = [&](int tid, int64_t a, int64_t b, bool camera) {
+    Acc& A = acc[tid];
+    if (A.ga.empty()) A.ga.assign(p->n_albedo, 0.0);
+    Tape tape;
+    TP = &tape;
+    std::vector<int> node_a(p->n_albedo, -1), touch_a;
+    std::vector<ConnOut<double>> cs;
+    std::vector<ConnOut<V>> cv;
+    for (int64_t i = a; i < b; ++i) {
+      tape.clear();
+      touch_a.clear();
+      V Lev[3];
+      for (int c = 0; c < 3; ++c) Lev[c] = V(p->Le[c], tape.push(-1, 0, -1, 0));
+      Leaves la{p->albedo, &node_a, &touch_a};
+      V loss(0.0);
+      if (camera) {
+        if (cam_mask && !cam_mask[i]) continue;
+        CamPath P = trace_cam(sc, run->seed, (uint64_t)i, run->max_depth);
+        V L[3];
+        eval_cam<V>(sc, P, la, Lev, N, M, L);
+        double Lb[3];
+        adjoint_read<double>(dI, W, H, P.ux, P.uy, Lb, run->filter);
+        for (int c = 0; c < 3; ++c) loss = loss + L[c] * V(Lb[c]);
+      } else {
+        if (mask && !mask[i]) continue;
+        uint64_t n = (uint64_t)(run->path_begin + i);
+        Path P = trace(sc, run->seed, n, run->max_depth, 0, 1.0);
+        eval_path<double>(sc, P, Plain{p->albedo}, Plain{p->Le}, Plain{p->heights}, N > 0 ? N : 1.0, cs, &P);
+        eval_path<V>(sc, P, la, Lev, ConstV{p->heights}, N > 0 ? N : 1.0, cv);
+        for (size_t j = 0; j < cv.size(); ++j) {
+          const double w = light_weight(sc, cs[j], N, M);
+          V Lb[3];
+          adjoint_read<V>(dI, W, H, cv[j].ux, cv[j].uy, Lb, run->filter);
+          V term = cv[j].L[0] * Lb[0] + cv[j].L[1] * Lb[1] + cv[j].L[2] * Lb[2];
+          loss = loss + term * V(w);
+        }
+      }
+      A.loss += loss.v;
+      if (loss.i >= 0) {
+        tape.backward(loss.i);
+        for (int c = 0; c < 3; ++c) A.gL[c] += tape.adj[Lev[c].i];
+        for (int idx : touch_a) A.ga[idx] += tape.adj[node_a[idx]];
+      }
+      for (int idx : touch_a) node_a[idx] = -1;
+    }
+    TP = nullptr;
+  };
+  parallel_paths(nt, run->n_paths, [&](int tid, int64_t a, int64_t b) { body(tid, a, b, false); });
+  parallel_paths(nt, n_cam, [&](int tid, int64_t a, int64_t b) { body(tid, a, b, true); });
+  if (out->d_albedo)
+    for (int j = 0; j < p->n_albedo; ++j) {
+      double v = 0;
+      for (int t = 0; t < nt; ++t) if (acc[t].ga.size()) v += acc[t].ga[j];
+      out->d_albedo[j] = v;
+    }
+  if (out->d_heights) for (int j = 0; j < p->n_heights; ++j) out->d_heights[j] = 0.0;
+  if (out->d_Le) for (int c = 0; c < 3; ++c) { double v = 0; for (int t = 0; t < nt; ++t) v += acc[t].gL[c]; out->d_Le[c] = v; }
+  if (out->loss) { double v = 0; for (int t = 0; t < nt; ++t) v += acc[t].loss; out->loss[0] = v; }
+  return 0;
 }
 
 // Camera-side path tracer with next-event estimation to the area emitter (radiance

@@ -89,6 +89,13 @@ def lib():
             L.or_reservoir.restype = C.c_int
             L.or_intersect.argtypes = [P(or_scene), P(or_params), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
             L.or_intersect.restype = C.c_int
+            L.or_render_bidir.argtypes = [P(or_scene), P(or_params), P(or_run), C.c_int64, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]
+            L.or_gradient_bidir.argtypes = [P(or_scene), P(or_params), P(or_run), C.c_int64, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, P(or_grads)]
+            L.or_connections.argtypes = [P(or_scene), P(or_params), P(or_run), C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_int64]
+            L.or_connections.restype = C.c_int64
             L.or_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]
             L.or_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p]
             L.or_mlp_grad.restype = C.c_double
@@ -202,6 +209,61 @@ def gradient(scene, dI, seed=0, n_paths=1 << 12, max_depth=4, method=NAIVE, atta
     if want_dbg:
         out["dbg"] = dbg
     return out
+
+
+def connections(scene, dI, seed=0, n_paths=1 << 12, max_depth=4, path_begin=0, n_norm=0, mask=None, cap=1 << 20,
+                filter=0):
+    """Every valid sensor connection [n, 24]: path, vertex index k, x[3], arrival-side normal[3],
+    arrival direction[3], throughput before the albedo[3], u_x, u_y, connection weight,
+    L[3], Lbar[3], 0 (see or_connections)."""
+    b = _Bound(scene)
+    dI = np.ascontiguousarray(dI, dtype=np.float64)
+    run = or_run(seed, path_begin, n_paths, n_norm or n_paths, max_depth, 0, 0, 1, 0, 1.0, int(filter))
+    rows = np.zeros((cap, 24))
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    k = lib().or_connections(C.byref(b.sc), C.byref(b.params), C.byref(run), dI.ctypes.data, _ptr(m),
+                             rows.ctypes.data, cap)
+    return rows[: min(k, cap)]
+
+
+def render_bidir(scene, n_cam, seed=0, n_paths=1 << 12, max_depth=4, n_norm=0, mask=None, cam_mask=None,
+                 want_hash=False, n_threads=0, filter=0, albedo=None, Le=None):
+    """Bidirectional image [H, W, 3]: light-tracer connections of n_paths light paths and
+    n_cam camera samples with next-event estimation, balance heuristic (detached, diffuse
+    scenes).  want_hash: also (light path hashes, camera sample hashes)."""
+    b = _Bound(scene, albedo, Le)
+    img = np.zeros((scene.H, scene.W, 3))
+    run = or_run(seed, 0, n_paths, n_norm or n_paths, max_depth, 0, 0, _threads(n_threads), 0, 1.0, int(filter))
+    lh = np.zeros(max(1, n_paths), dtype=np.uint32)
+    ch = np.zeros(max(1, n_cam), dtype=np.uint32)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    cm = None if cam_mask is None else np.ascontiguousarray(cam_mask, dtype=np.uint8)
+    rc = lib().or_render_bidir(C.byref(b.sc), C.byref(b.params), C.byref(run), int(n_cam), _ptr(m), _ptr(cm),
+                               img.ctypes.data, lh.ctypes.data, ch.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle or_render_bidir refused (code {rc})")
+    return (img, lh[:n_paths], ch[:n_cam]) if want_hash else img
+
+
+def gradient_bidir(scene, dI, n_cam, seed=0, n_paths=1 << 12, max_depth=4, n_norm=0, mask=None, cam_mask=None,
+                   n_threads=0, filter=0, albedo=None, Le=None):
+    """dict(d_albedo, d_Le, loss) of <dI, I_bidir>: naive tape AD of the bidirectional
+    estimator of render_bidir."""
+    b = _Bound(scene, albedo, Le)
+    dI = np.ascontiguousarray(dI, dtype=np.float64)
+    ga = np.zeros(max(1, scene.albedo.size))
+    gl = np.zeros(3)
+    gh = np.zeros(max(1, scene.heights.size))
+    loss = np.zeros(1)
+    g = or_grads(_dp(ga), _dp(gl), _dp(gh), _dp(loss))
+    run = or_run(seed, 0, n_paths, n_norm or n_paths, max_depth, 0, 0, _threads(n_threads), 0, 1.0, int(filter))
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    cm = None if cam_mask is None else np.ascontiguousarray(cam_mask, dtype=np.uint8)
+    rc = lib().or_gradient_bidir(C.byref(b.sc), C.byref(b.params), C.byref(run), int(n_cam), dI.ctypes.data,
+                                 _ptr(m), _ptr(cm), C.byref(g))
+    if rc != 0:
+        raise ValueError(f"oracle or_gradient_bidir refused (code {rc})")
+    return dict(d_albedo=ga[:scene.albedo.size], d_Le=gl, loss=float(loss[0]))
 
 
 def frozen_loss(scene, dI, params0, params1, seed=0, n_paths=1 << 10, max_depth=4, method=NAIVE, path_begin=0,

@@ -4,7 +4,9 @@
 I(theta) [H, W, 3]; ``I.backward(dI)`` (or any loss built on I) produces gradients of
 albedo, Le and heights through liblt's constant-memory adjoints (LRB-3-pass or ResLRB) or
 the naive baseline.  The forward pass refits the height field, then runs the primal kernel
-of the chosen method; the backward pass replays the same paths (same seed and path range).
+of the chosen method; the backward pass refits the height field to the heights its forward
+pass saw (another render of the same scene may have moved it in between) and replays the
+same paths (same seed and path range).  The scene is left refitted to those heights.
 Methods: "lrb3" (LRB-3-pass), "reslrb" (ResLRB), "naive" (tape AD), "lrb2" (buffered
 two-pass).
 All work runs in liblt's CUDA kernels.
@@ -53,6 +55,10 @@ class _LightTrace(torch.autograd.Function):
     def backward(ctx, grad_image):
         albedo, Le, heights = ctx.saved_tensors
         S = ctx.scene
+        if S.n_heights:
+            # the attached adjoints replay the paths against the scene's current geometry:
+            # restore the geometry of this render's forward pass
+            S.refit(heights.detach())
         if ctx.method == "lrb3":
             o = S.opts(**ctx.opts_kw, lrb3_state=ctx.aux, lrb3_mask_ready=1)
         else:

@@ -305,6 +305,10 @@ lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts
   if (!o) return fail(LT_ERR_INVALID_ARG, "opts is NULL");
   if (o->max_depth < 1 || o->max_depth > kMaxDepth) return fail(LT_ERR_INVALID_ARG, "max_depth must be in 1..64");
   if (o->n_paths < 0 || o->path_offset < 0 || o->n_norm < 0) return fail(LT_ERR_INVALID_ARG, "negative path counts");
+  // every byte count derived from n_paths (records, states, tapes up to 64 vertices of
+  // 32 B) stays far inside size_t, and path indices inside the 64-bit Philox counter
+  if (o->n_paths > LT_MAX_PATHS || o->path_offset > LT_MAX_PATHS)
+    return fail(LT_ERR_INVALID_ARG, "n_paths and path_offset must be at most 2^40");
   if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 1024 || o->block_size % 32))
     return fail(LT_ERR_INVALID_ARG, "block_size must be a multiple of 32 in 32..1024 (or 0)");
   if (o->block_size > 128) return fail(LT_ERR_INVALID_ARG, "kernels are compiled for at most 128 threads per block");
@@ -338,6 +342,8 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.rr_depth = o->rr_depth;
   k.rr_q = o->rr_prob;
   k.filter = o->filter;
+  k.list = nullptr;
+  k.list_n = nullptr;
   return k;
 }
 
@@ -402,7 +408,10 @@ lt_status lt_naive_gradient_static(lt_scene* s, const lt_params* p, const lt_ren
   lt_status v = check_opts(s, p, o);
   if (v != LT_OK) return v;
   if (!dI || !image) return fail(LT_ERR_INVALID_ARG, "lt_naive_gradient_static: d_image or image is NULL");
-  const size_t need = lt_naive_workspace_bytes(o);
+  // bound the path count first (32 B per vertex) so that the size below cannot wrap
+  const size_t need = o->n_paths > (int64_t)(LT_NAIVE_STATIC_BYTES / (32u * (unsigned)o->max_depth))
+                          ? (size_t)-1
+                          : lt_naive_workspace_bytes(o);
   if (need > (size_t)LT_NAIVE_STATIC_BYTES)
     return fail(LT_ERR_INVALID_ARG, "lt_naive_gradient_static: the tape needs " + std::to_string(need) +
                                         " bytes, more than the fixed scratch of " +
@@ -630,17 +639,17 @@ void lt_scene_destroy(lt_scene* s) { free_scene(s); }
 size_t lt_record_size(const lt_render_opts*) { return 32; }
 
 size_t lt_lrb2_buffer_bytes(const lt_render_opts* o) {
-  if (!o || o->n_paths < 0 || o->max_depth < 1) return 0;
+  if (!o || o->n_paths < 0 || o->n_paths > LT_MAX_PATHS || o->max_depth < 1 || o->max_depth > kMaxDepth) return 0;
   return lrb2_layout(o->n_paths, o->max_depth).total;
 }
 
 size_t lt_lrb3_state_bytes(const lt_render_opts* o) {
-  if (!o || o->n_paths < 0) return 0;
+  if (!o || o->n_paths < 0 || o->n_paths > LT_MAX_PATHS) return 0;
   return lrb3_state_bytes(o->n_paths);
 }
 
 size_t lt_naive_workspace_bytes(const lt_render_opts* o) {
-  if (!o || o->n_paths < 0 || o->max_depth < 1) return 0;
+  if (!o || o->n_paths < 0 || o->n_paths > LT_MAX_PATHS || o->max_depth < 1 || o->max_depth > kMaxDepth) return 0;
   size_t head = ((size_t)o->n_paths * sizeof(int) + 255) & ~(size_t)255;
   return head + (size_t)o->n_paths * (size_t)o->max_depth * 32;
 }
@@ -663,7 +672,16 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
   LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
-  if (est == LT_EST_PLAIN) kp.vstate = o->lrb3_state;
+  if (est == LT_EST_PLAIN && o->lrb3_state) {
+    kp.vstate = o->lrb3_state;
+    if (o->n_paths <= kListMaxPaths) {
+      // the list of the paths with a valid connection, for LRB-3 passes 2 and 3
+      char* base = (char*)o->lrb3_state;
+      kp.list = (uint32_t*)(base + lrb3_state_list(o->n_paths));
+      kp.list_n = (unsigned long long*)(base + lrb3_state_count(o->n_paths));
+      LT_CUDA(cudaMemsetAsync(kp.list_n, 0, sizeof(unsigned long long), st));
+    }
+  }
   cudaError_t e = launch_primal(dev_for(s, o->bvh_width), kp, est, image, aux, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_primal: ") + cudaGetErrorString(e));
   return LT_OK;
@@ -683,6 +701,12 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
   set_privatization(s, g, kp);
+  if (o->lrb3_state && o->lrb3_mask_ready && o->n_paths <= kListMaxPaths) {
+    // the primal listed the paths with a valid connection: passes 2 and 3 visit only those
+    char* base = (char*)o->lrb3_state;
+    kp.list = (uint32_t*)(base + lrb3_state_list(o->n_paths));
+    kp.list_n = (unsigned long long*)(base + lrb3_state_count(o->n_paths));
+  }
   cudaError_t e = launch_lrb3(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, gp,
                               o->lrb3_state, o->lrb3_state && o->lrb3_mask_ready, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
@@ -742,6 +766,61 @@ lt_status lt_backward_naive(lt_scene* s, const lt_params* p, const lt_render_opt
   set_privatization(s, g, kp);
   cudaError_t e = launch_naive(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_naive: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+namespace {
+lt_status check_bidir(const lt_scene* s, const lt_render_opts* o, const lt_bidir_opts* b, BidirArgs& ba) {
+  if (!b) return fail(LT_ERR_INVALID_ARG, "bidir opts is NULL");
+  if (b->n_cam < 0 || b->n_cam > LT_MAX_PATHS) return fail(LT_ERR_INVALID_ARG, "n_cam must be in 0..2^40");
+  if (o->attached) return fail(LT_ERR_UNSUPPORTED, "the bidirectional estimator is detached only");
+  if (s->has_dielectric) return fail(LT_ERR_UNSUPPORTED, "the bidirectional estimator needs a scene without dielectrics");
+  if (o->rr_depth > 0) return fail(LT_ERR_UNSUPPORTED, "the bidirectional estimator has no Russian roulette");
+  ba.N = (float)(o->n_norm > 0 ? o->n_norm : o->n_paths);
+  ba.M = (float)b->n_cam;
+  ba.n_cam = b->n_cam;
+  ba.cam_mask = b->cam_mask;
+  ba.cam_hash = b->cam_hash;
+  return LT_OK;
+}
+}  // namespace
+
+lt_status lt_bidir_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, const lt_bidir_opts* b,
+                          float* image, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!image) return fail(LT_ERR_INVALID_ARG, "image is NULL");
+  BidirArgs ba;
+  v = check_bidir(s, o, b, ba);
+  if (v != LT_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+  LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
+  if (o->n_paths == 0 && b->n_cam == 0) return LT_OK;
+  cudaError_t e = launch_bidir(dev_for(s, o->bvh_width), kparams(p, o), ba, false, image, nullptr, GradPtrs{},
+                               cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_bidir_primal: ") + cudaGetErrorString(e));
+  return LT_OK;
+}
+
+lt_status lt_bidir_backward(lt_scene* s, const lt_params* p, const lt_render_opts* o, const lt_bidir_opts* b,
+                            const float* dI, const lt_grads* g, void* stream) {
+  lt_status v = check_opts(s, p, o);
+  if (v != LT_OK) return v;
+  if (!dI) return fail(LT_ERR_INVALID_ARG, "d_image is NULL");
+  BidirArgs ba;
+  v = check_bidir(s, o, b, ba);
+  if (v != LT_OK) return v;
+  cudaStream_t st = (cudaStream_t)stream;
+  GradPtrs gp;
+  v = prep_grads(s, g, st, gp);
+  if (v != LT_OK) return v;
+  if (o->n_paths == 0 && b->n_cam == 0) return LT_OK;
+  KParams kp = kparams(p, o);
+  set_privatization(s, g, kp);
+  kp.n_h = 0;  // detached: no height gradients
+  kp.priv_n = kp.n_alb;
+  cudaError_t e = launch_bidir(dev_for(s, o->bvh_width), kp, ba, true, nullptr, dI, gp, cfg_for(s, o), st);
+  if (e) return fail(LT_ERR_CUDA, std::string("lt_bidir_backward: ") + cudaGetErrorString(e));
   return LT_OK;
 }
 

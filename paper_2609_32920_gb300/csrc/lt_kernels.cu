@@ -731,6 +731,7 @@ __global__ void __launch_bounds__(128) k_collect(DevScene S, KParams kp, const f
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
+    if (kp.mask && !kp.mask[p]) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
     Walk w;
     float3 x0;
@@ -772,12 +773,25 @@ __global__ void __launch_bounds__(128) k_collect(DevScene S, KParams kp, const f
 // lanes call take() together at the top of the step loop).
 struct Dispenser {
   int64_t next, end;
+  int64_t stride = 0;  // interleaved mode: distance between a warp's 32-entry blocks
+  bool strided = false;
   __device__ __forceinline__ void init(int64_t n_paths) {
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t per = (n_paths + warps - 1) / warps;
     next = min(wid * per, n_paths);
     end = min(next + per, n_paths);
+  }
+  // Interleaved over the grid's warps: a warp takes 32 consecutive entries, then the 32
+  // entries one grid stride further (for a list whose order follows the time its entries
+  // were found, so that no warp receives only the entries of one stretch of it).
+  __device__ __forceinline__ void init_strided(int64_t n_paths) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    next = wid * 32;
+    end = n_paths;
+    stride = warps * 32;
+    strided = true;
   }
   // The block alone works on [0, n_paths): contiguous ranges of its warps.
   __device__ __forceinline__ void init_local(int64_t n_paths) {
@@ -792,6 +806,20 @@ struct Dispenser {
     const unsigned m = __ballot_sync(0xffffffffu, want);
     const unsigned lane = threadIdx.x & 31;
     int64_t mine = -1;
+    if (strided) {
+      // `next` is the warp's next entry; its block [next & ~31, +32) continues one grid
+      // stride further once used up (a request of at most 32 spans at most two blocks)
+      const int64_t blk = next & ~(int64_t)31;
+      const int used = (int)(next - blk);
+      if (want) {
+        const int pos = used + __popc(m & ((1u << lane) - 1u));
+        const int64_t cand = pos < 32 ? blk + pos : blk + stride + (pos - 32);
+        mine = cand < end ? cand : -1;
+      }
+      const int u2 = used + __popc(m);
+      next = u2 < 32 ? blk + u2 : blk + stride + (u2 - 32);
+      return mine;
+    }
     if (want) {
       int64_t cand = next + __popc(m & ((1u << lane) - 1u));
       mine = cand < end ? cand : -1;
@@ -866,8 +894,9 @@ __device__ __forceinline__ void add3(float* d, float3 v) {
 // BATCH: the lane's scene, parameters and outputs are those of the batch item its path
 // belongs to (BatchDispenser); S0, kp0, image0 and aux0 are not used.
 // LEARN compiles the learned reservoir target (ResLRB only); plain ResLRB does not carry its
-// registers.
-template <int EST, bool BATCH, bool LEARN = false>
+// registers.  ST compiles the work census (rays, box and primitive tests, vertices,
+// connections) of a counting variant.
+template <int EST, bool BATCH, bool LEARN = false, bool ST = false>
 __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& kp0, float* __restrict__ image0,
                                             void* aux0, const BatchArgs& ba) {
   // learned reservoir target: network image, one 32x16 feature tile per warp, and two
@@ -904,6 +933,8 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
   TravState ts;  // the lane's ray in flight (see TravState)
   LocalStack stk;
   bool inflight = false;
+  Census cs = {0, 0, 0};
+  uint32_t nverts = 0, nconns = 0;
   while (true) {
     const bool want = more && !busy;
     int jnew = jb;
@@ -939,13 +970,26 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
     h.prim = -1;
     bool pending = false;  // the ray has visits left: the lane resumes it in the next step
     if (trav) {
-      if (!inflight) trace_begin(S, w.org, w.dir, w.skip, ts);
-      inflight = !trace_resume(S, w.org, w.dir, w.skip, ts, stk);
+      if (!inflight) trace_begin<ST>(S, w.org, w.dir, w.skip, ts, &cs);
+      inflight = !trace_resume<ST>(S, w.org, w.dir, w.skip, ts, stk, &cs);
       pending = inflight;
       h = ts.h;
     }
     Vtx v;
     const bool alive = trav && !pending && walk_finish(S, w, h, v);
+    if (EST == 0 && !BATCH && kp0.list) {
+      // a path that ends now with a valid connection joins the list that LRB-3 passes 2
+      // and 3 visit (one atomic per warp and step)
+      const bool ends = busy && !pending && !alive && active && vmask != 0ull;
+      const unsigned b = __ballot_sync(0xffffffffu, ends);
+      if (b) {
+        const int lane = threadIdx.x & 31, leader = __ffs(b) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(kp0.list_n, (unsigned long long)__popc(b));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (ends) kp0.list[base + __popc(b & ((1u << lane) - 1u))] = (uint32_t)p;
+      }
+    }
     float3 ns = f3(0, 0, 0);
     Conn c;
     c.valid = false; c.ux = c.uy = 0.0f;
@@ -953,7 +997,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
       ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
       c = connect_pre(S, v.x, ns);
     }
-    if (c.valid && occluded(S, v.x, c.wc, c.dist, v.prim)) c.valid = false;
+    if (c.valid && occluded<ST>(S, v.x, c.wc, c.dist, v.prim, &cs)) c.valid = false;
     // Learned reservoir target: warp-wide tensor-core evaluations (all 32 lanes take part).
     // The first candidate of a path is kept whatever its weight (acceptance probability
     // w_1 / Omega = 1), so its weight is only needed once a second candidate arrives: its
@@ -1027,9 +1071,11 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
     float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
     float3 rho = f3(0, 0, 0);
     float3 L = f3(0, 0, 0);
+    if (ST) ++nverts;
     if (v.diffuse) {
       rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
       if (c.valid) {
+        if (ST) ++nconns;
         ++nconn;
         vmask |= 1ull << k;
         L = mul(w.beta, rho) * (c.geo * kp.inv_n);
@@ -1081,11 +1127,22 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
     }
     ++k;
   }
+  if (ST && kp0.census) {
+    atomicAdd(kp0.census + 0, (unsigned long long)cs.rays);
+    atomicAdd(kp0.census + 1, (unsigned long long)cs.nodes);
+    atomicAdd(kp0.census + 2, (unsigned long long)cs.prims);
+    atomicAdd(kp0.census + 3, (unsigned long long)nverts);
+    atomicAdd(kp0.census + 4, (unsigned long long)nconns);
+  }
 }
 
 template <int EST>
 __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
   primal_body<EST, false>(S, kp, image, aux, BatchArgs{});
+}
+// Counting variant of the plain primal (work census for the roofline; not for timed runs)
+__global__ void __launch_bounds__(128) k_primal_census(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
+  primal_body<0, false, false, true>(S, kp, image, aux, BatchArgs{});
 }
 // ResLRB primal with the learned reservoir target, held to four blocks per SM
 __global__ void __launch_bounds__(128, 4) k_primal_learned(DevScene S, KParams kp, float* __restrict__ image,
@@ -1115,6 +1172,8 @@ __global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
 // connection validity from it, traces no visibility rays, stops after the last valid
 // connection and skips paths without one.
 // LOCAL: the calling block alone works on the path range (a span of a batch item).
+// With a path list (kp.list, masks known): MODE 1 (MK) and MODE 2 visit only the listed
+// paths, the ones with a valid connection, so no lane draws a path it has nothing to do for.
 template <bool ATT, bool ST, bool CH, bool BATCH, int MODE = 0, bool MK = false, bool LOCAL = false>
 __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0, const float* __restrict__ dI0,
                                           const GradPtrs& g0, const BatchArgs& ba, float4* xrec = nullptr,
@@ -1132,7 +1191,12 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   uint32_t nverts = 0, nconns = 0;
   Dispenser disp;
   BatchDispenser bdisp;
-  if (BATCH) bdisp.init(); else if (LOCAL) disp.init_local(kp0.n_paths); else disp.init(kp0.n_paths);
+  // the path list applies to pass 2 with known masks and to pass 3
+  const uint32_t* list = (!BATCH && !LOCAL && (MODE == 2 || (MODE == 1 && MK))) ? kp0.list : nullptr;
+  if (BATCH) bdisp.init();
+  else if (LOCAL) disp.init_local(kp0.n_paths);
+  else if (list) disp.init_strided(min((int64_t)*kp0.list_n, kp0.n_paths));
+  else disp.init(kp0.n_paths);
   int jb = 0;
   enum { IDLE = 0, PASS2 = 1, PASS3 = 2 };
   int phase = IDLE, k = 0, last = 0, nconn = 0;
@@ -1160,6 +1224,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       xr = (float4*)ba.jobs[jb].state;
       xh = (uint32_t*)((char*)ba.jobs[jb].state + lrb3_state_split(kp.n_paths));
     }
+    if (got >= 0 && list) got = (int64_t)list[got];
     if (got < 0) {
       more = false;
     } else if (MODE == 2) {
@@ -1714,6 +1779,232 @@ __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const flo
   block_add3(g.d_Le, gLe);
 }
 
+// ======================================================================= bidirectional
+// Two strategies for the paths x0 (emitter), x1..xk (diffuse) -> camera, combined by the
+// balance heuristic: the light tracer's sensor connection at xk (N light paths) and a camera
+// sample through a film position uniform over the film, traced to xk = y1, ..., x1 = ym by
+// cosine sampling, with next-event estimation from ym to a point x0 uniform on the emitter
+// (M camera samples).  For Lambertian surfaces, cosine sampling and cosine emission a
+// segment between two surfaces has the same area density in both directions, so the
+// density ratio of the camera strategy to the light strategy is R = p_film(xk) / pf0
+// (p_film: the film's area density at xk, geo * pi / (W H); pf0 = cos0 cos1 / (pi r01^2),
+// the light tracer's density of x1), and a sample of either strategy contributes
+// L_N / (N + M R), L_N the light tracer's splat value times N.  Diffuse scenes, detached.
+
+// Balance-heuristic factor N / (N + M R) of a light-tracer connection of weight geo
+// (importance without the estimator's 1/N) on a path whose first segment has density pf0.
+__device__ __forceinline__ float bidir_light_w(const DevScene& S, const BidirArgs& ba, float geo, float pf0) {
+  const float R = geo * kPi / ((float)S.W * (float)S.H * pf0);
+  return ba.N / fmaf(ba.M, R, ba.N);
+}
+
+// Light side.  BWD = false: the primal (splat every weighted connection).  BWD = true: the
+// LRB-3 adjoint in one kernel per path (pass 2 accumulates delta_total, Eq. 14; pass 3
+// replays to the last valid connection, Eq. 15-17), detached.
+template <bool BWD>
+__global__ void __launch_bounds__(128) k_bidir_light(DevScene S, KParams kp, BidirArgs ba, float* __restrict__ image,
+                                                     const float* __restrict__ dI, GradPtrs g0) {
+  extern __shared__ float sgrad[];
+  GradPtrs g = g0;
+  if (BWD) g.d_albedo = sink_begin(kp, g0, sgrad).alb;
+  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  float3 gLe = f3(0, 0, 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
+    const bool active = !kp.mask || kp.mask[p];
+    const uint64_t n = (uint64_t)(kp.path_offset + p);
+    Walk w;
+    float3 x0;
+    walk_start(S, kp.seed, n, Le, w, x0);
+    uint32_t hash = 2166136261u;
+    float pf0 = 0.0f;
+    float3 dtot = f3(0, 0, 0);
+    uint64_t valid = 0;
+    for (int k = 0; k < kp.max_depth; ++k) {
+      Vtx v;
+      if (!walk_hit(S, w, v)) break;
+      if (k == 0) {
+        const float3 d = v.x - x0;
+        pf0 = fabsf(dot(S.ln, w.dir)) * fabsf(dot(v.n, w.dir)) / (kPi * dot(d, d));
+      }
+      const float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+      bool conn = false;
+      if (v.diffuse) {
+        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
+        const Conn c = connect(S, v.x, ns, v.prim);
+        conn = c.valid;
+        if (c.valid && active) {
+          const float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n * bidir_light_w(S, ba, c.geo, pf0));
+          if (!BWD) {
+            splat_f(image, S.W, S.H, c.ux, c.uy, L, kp.filter);
+          } else {
+            dtot = dtot + mul(adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, nullptr, kp.filter), L);
+            valid |= 1ull << k;
+          }
+        }
+      }
+      const bool refl = walk_scatter(S, w, v, ns, rho, r);
+      fnv(hash, (uint32_t)v.P.orig);
+      fnv(hash, vtx_flags(v, refl, conn));
+    }
+    if (!BWD && kp.hash) kp.hash[p] = hash;
+    if (!BWD || !valid) continue;
+    gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);  // emitted factor, weight delta_total
+    walk_start(S, kp.seed, n, Le, w, x0);
+    float3 rem = dtot;
+    const int last = 63 - __clzll((long long)valid);
+    for (int k = 0; k <= last; ++k) {
+      Vtx v;
+      if (!walk_hit(S, w, v)) { set_err(S, ERR_BOUNDS); break; }  // the replay must reach `last`
+      if (k == 0) {
+        const float3 d = v.x - x0;
+        pf0 = fabsf(dot(S.ln, w.dir)) * fabsf(dot(v.n, w.dir)) / (kPi * dot(d, d));
+      }
+      const float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+      if (v.diffuse) {
+        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+        TexFoot foot;
+        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
+        float3 wsplat = f3(0, 0, 0);
+        if ((valid >> k) & 1ull) {
+          const Conn c = connect_pre(S, v.x, ns);
+          const float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n * bidir_light_w(S, ba, c.geo, pf0));
+          wsplat = mul(adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, nullptr, kp.filter), L);  // Eq. 15
+          rem = rem - wsplat;                                                                  // Eq. 16
+        }
+        scatter_albedo(g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor with delta_rem (Eq. 17)
+      }
+      walk_scatter(S, w, v, ns, rho, r);
+    }
+  }
+  if (BWD) {
+    sink_end(kp, g0, sgrad);
+    block_add3(g0.d_Le, gLe);
+  }
+}
+
+// The camera sample c: film position from Philox stream 3 at (c, 0); at camera vertex m the
+// cosine direction (u0, u1) and the emitter point of the next-event connection (u2, u3)
+// from (c, m).  Returns the vertex's contribution (zero without a valid connection) and
+// continues the sample's walk; false when the walk ends (miss, emitter, depth).
+struct CamWalk {
+  float3 org, dir, thr;  // ray and the product of the albedos so far
+  int skip;
+  float geo1, pfilm;     // sensor connection at the first vertex
+};
+__device__ __forceinline__ void cam_start(const DevScene& S, const KParams& kp, uint64_t c, CamWalk& cw, float& ux,
+                                          float& uy) {
+  const float4 r0 = rand4(kp.seed, c, 0, 3);
+  ux = r0.x * (float)S.W;
+  uy = r0.y * (float)S.H;
+  const float px = (2.0f * ux / (float)S.W - 1.0f) * S.tanx, py = (1.0f - 2.0f * uy / (float)S.H) * S.tany;
+  cw.dir = normalize(S.cf + S.cr * px + S.cu * py);
+  cw.org = S.cpos;
+  cw.skip = -1;
+  cw.thr = f3(1, 1, 1);
+  cw.geo1 = cw.pfilm = 0.0f;
+}
+template <bool VIS>
+__device__ __forceinline__ bool cam_vertex(const DevScene& S, const KParams& kp, const BidirArgs& ba, uint64_t c,
+                                           int m, CamWalk& cw, bool nee_known, float3& contrib, bool& nee,
+                                           TexFoot* foot, float3& rho, uint32_t& hash) {
+  const HitRec h = trace_closest(S, cw.org, cw.dir, cw.skip);
+  if (h.prim < 0) return false;
+  const Prim P = load_prim(S, h.prim);
+  const int4 mt = __ldg(S.mat + P.mat);
+  if (mt.x != MAT_DIFFUSE) return false;  // the emitter absorbs (seen directly it is black)
+  const float3 x = P.o + P.e1 * h.b1 + P.e2 * h.b2;
+  const float3 nraw = cross(P.e1, P.e2), nn = normalize(nraw);
+  const float3 ns = dot(nraw, cw.dir) < 0.0f ? nn : -nn;
+  if (m == 1) {
+    const float3 d = x - S.cpos;
+    const float dist = length(d), cc = dot(d, S.cf) / dist;
+    const float cosc = -dot(ns, d) / dist;
+    cw.geo1 = cosc * S.K0 / (dist * dist * cc * cc * cc);
+    cw.pfilm = cw.geo1 * kPi / ((float)S.W * (float)S.H);
+  }
+  rho = tex_lookup(kp.albedo, mt, h.b1, h.b2, foot);
+  cw.thr = mul(cw.thr, rho);
+  const float4 r = rand4(kp.seed, c, (uint32_t)m, 3);
+  const float3 xl = S.lo + S.le1 * r.z + S.le2 * r.w;
+  const float3 wl = xl - x;
+  const float dl = length(wl);
+  const float3 wn = wl * (1.0f / dl);
+  const float cx = dot(ns, wn), cl = -dot(S.ln, wn);
+  nee = VIS ? (cx > 0.0f && cl > 0.0f && !occluded(S, x, wn, dl, h.prim)) : nee_known;
+  contrib = f3(0, 0, 0);
+  if (nee) {
+    const float pf0 = cx * cl / (kPi * dl * dl);
+    const float wgt = S.light_area * kPi * cw.geo1 / fmaf(ba.M, cw.pfilm / pf0, ba.N);
+    contrib = mul(f3(kp.Le[0], kp.Le[1], kp.Le[2]), cw.thr) * wgt;
+  }
+  fnv(hash, (uint32_t)P.orig);
+  fnv(hash, nee ? 1u : 0u);
+  cw.dir = cosine_dir(ns, r.x, r.y);
+  cw.org = x;
+  cw.skip = h.prim;
+  return true;
+}
+
+// Camera side.  BWD = false: each sample splats the sum of its vertices' contributions at
+// its film position.  BWD = true: path replay backpropagation (one adjoint read per sample,
+// the sample's film position being fixed): a first walk sums the contributions, a replay
+// weights each vertex's albedo with the adjoint of the contributions from that vertex on.
+template <bool BWD>
+__global__ void __launch_bounds__(128) k_bidir_cam(DevScene S, KParams kp, BidirArgs ba, float* __restrict__ image,
+                                                   const float* __restrict__ dI, GradPtrs g0) {
+  extern __shared__ float sgrad[];
+  GradPtrs g = g0;
+  if (BWD) g.d_albedo = sink_begin(kp, g0, sgrad).alb;
+  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  float3 gLe = f3(0, 0, 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ba.n_cam; c += stride) {
+    const bool active = !ba.cam_mask || ba.cam_mask[c];
+    CamWalk cw;
+    float ux, uy;
+    cam_start(S, kp, (uint64_t)c, cw, ux, uy);
+    uint32_t hash = 2166136261u;
+    float3 total = f3(0, 0, 0), contrib, rho;
+    uint64_t nees = 0;
+    bool nee;
+    for (int m = 1; m <= kp.max_depth; ++m) {
+      if (!cam_vertex<true>(S, kp, ba, (uint64_t)c, m, cw, false, contrib, nee, nullptr, rho, hash)) break;
+      total = total + contrib;
+      if (nee) nees |= 1ull << (m - 1);
+    }
+    if (!BWD) {
+      if (ba.cam_hash) ba.cam_hash[c] = hash;
+      if (active && nees) splat_f(image, S.W, S.H, ux, uy, total, kp.filter);
+      continue;
+    }
+    if (!active || !nees) continue;
+    const float3 Lb = adjoint_read_f(dI, S.W, S.H, ux, uy, total, nullptr, kp.filter);
+    const float3 P = mul(Lb, total);
+    gLe = gLe + f3(P.x / Le.x, P.y / Le.y, P.z / Le.z);
+    cam_start(S, kp, (uint64_t)c, cw, ux, uy);
+    float3 rem = total;
+    const int last = 64 - __clzll((long long)nees);
+    for (int m = 1; m <= last; ++m) {
+      TexFoot foot;
+      if (!cam_vertex<false>(S, kp, ba, (uint64_t)c, m, cw, (nees >> (m - 1)) & 1ull, contrib, nee, &foot, rho,
+                             hash)) {
+        set_err(S, ERR_BOUNDS);  // the replay must reach the last connection
+        break;
+      }
+      scatter_albedo(g.d_albedo, foot, mul(Lb, rem), rho);  // every contribution from this vertex on
+      rem = rem - contrib;
+    }
+  }
+  if (BWD) {
+    sink_end(kp, g0, sgrad);
+    block_add3(g0.d_Le, gLe);
+  }
+}
+
 // ======================================================================= film
 __global__ void k_film_l2(const float* __restrict__ I, const float* __restrict__ T, int64_t n, float* dI,
                           float* loss) {
@@ -1781,7 +2072,10 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
                                                 sizeof(float) * 2 * kMlpIn * L.block
                                           : 0;
   switch (est) {
-    case 0: launch_paths(k_primal<0>, L, kp.n_paths, 0, st, S, kp, image, aux); break;
+    case 0:
+      if (kp.census) launch_paths(k_primal_census, L, kp.n_paths, 0, st, S, kp, image, aux);
+      else launch_paths(k_primal<0>, L, kp.n_paths, 0, st, S, kp, image, aux);
+      break;
     case 1:
       if (kp.mlp) launch_paths(k_primal_learned, L, kp.n_paths, smem, st, S, kp, image, aux);
       else launch_paths(k_primal<1>, L, kp.n_paths, 0, st, S, kp, image, aux);
@@ -1933,6 +2227,20 @@ int batch_occupancy(int pass, bool att, bool chains, int block) {
   return n;
 }
 #undef LT_BATCH_DISPATCH
+
+cudaError_t launch_bidir(const DevScene& S, const KParams& kp, const BidirArgs& ba, bool backward, float* image,
+                         const float* dI, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
+  const size_t smem = backward && kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
+  if (kp.n_paths > 0) {
+    if (backward) launch_paths(k_bidir_light<true>, L, kp.n_paths, smem, st, S, kp, ba, image, dI, g);
+    else launch_paths(k_bidir_light<false>, L, kp.n_paths, smem, st, S, kp, ba, image, dI, g);
+  }
+  if (ba.n_cam > 0) {
+    if (backward) launch_paths(k_bidir_cam<true>, L, ba.n_cam, smem, st, S, kp, ba, image, dI, g);
+    else launch_paths(k_bidir_cam<false>, L, ba.n_cam, smem, st, S, kp, ba, image, dI, g);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,
                            cudaStream_t st) {

@@ -30,6 +30,9 @@ struct KParams {
   int rr_depth;                // Russian roulette after vertices of depth >= rr_depth (0: off)
   float rr_q;                  // survival probability of the roulette
   int filter;                  // reconstruction filter: 0 tent, 1 truncated Gaussian
+  uint32_t* list;              // paths with a valid connection (plain primal: appends;
+                               // LRB-3 passes 2 and 3 with known masks: visit only these) or null
+  unsigned long long* list_n;  // length of `list`
 };
 
 struct GradPtrs {
@@ -61,6 +64,16 @@ struct RefitArgs {
 
 struct BatchArgs;
 
+// Bidirectional estimator (light-tracer connections + camera samples with next-event
+// estimation, balance heuristic): counts N (light paths of the estimator) and M (camera
+// samples), the camera samples' optional mask and decision hashes.
+struct BidirArgs {
+  float N, M;
+  int64_t n_cam;
+  const uint8_t* cam_mask;
+  uint32_t* cam_hash;
+};
+
 // Kernel launchers.  lt_kernels.cu is compiled once per BVH width into namespaces w2, w4
 // and w8; the functions of the same names in lt itself pick the variant by the scene's
 // width (DevScene::width).
@@ -80,7 +93,9 @@ struct BatchArgs;
                              float* targets, int64_t cap, unsigned long long* count, const LaunchCfg& L,          \
                              cudaStream_t st);                                                                    \
   cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,          \
-                             cudaStream_t st);
+                             cudaStream_t st);                                                                    \
+  cudaError_t launch_bidir(const DevScene& S, const KParams& kp, const BidirArgs& ba, bool backward, float* image, \
+                           const float* dI, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
 
 namespace w2 { LT_KERNEL_LAUNCHERS }
 namespace w4 { LT_KERNEL_LAUNCHERS }
@@ -88,10 +103,18 @@ namespace w8 { LT_KERNEL_LAUNCHERS }
 LT_KERNEL_LAUNCHERS
 
 // `state` of launch_lrb3 (or null: fused kernel): per-path state of the two-kernel form,
-// layout float4[n_paths] then, at byte lrb3_state_split(n_paths), uint32[n_paths].
+// layout float4[n_paths] then, at byte lrb3_state_split(n_paths), uint32[n_paths] (together
+// lrb3_state_core bytes); then the list of the paths that have a valid connection (uint32
+// indices relative to the call, at lrb3_state_list) and its length (uint64, at
+// lrb3_state_count), written by a plain primal so that passes 2 and 3 visit only those.
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t lrb3_state_split(int64_t n) { return align256((size_t)n * 16); }
-__host__ __device__ inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_split(n) + align256((size_t)n * 4); }
+__host__ __device__ inline size_t lrb3_state_core(int64_t n) { return lrb3_state_split(n) + align256((size_t)n * 4); }
+__host__ __device__ inline size_t lrb3_state_list(int64_t n) { return lrb3_state_core(n); }
+__host__ __device__ inline size_t lrb3_state_count(int64_t n) { return lrb3_state_list(n) + align256((size_t)n * 4); }
+__host__ __device__ inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_count(n) + 256; }
+// The path list is used for calls of at most this many paths (uint32 indices).
+constexpr int64_t kListMaxPaths = 0xffffffffll;
 
 // Buffer of the buffered two-pass estimator (lrb_2pass): the LRB-3 per-path state, then
 // per path its traced vertex count (int), then per vertex [depth][path] the splat record
@@ -101,7 +124,7 @@ struct Lrb2Layout {
 };
 __host__ __device__ inline Lrb2Layout lrb2_layout(int64_t n, int d) {
   Lrb2Layout L;
-  L.counts = lrb3_state_bytes(n);
+  L.counts = lrb3_state_core(n);
   L.rec4 = L.counts + align256((size_t)n * 4);
   L.recz = L.rec4 + align256((size_t)n * (size_t)d * 16);
   L.total = L.recz + align256((size_t)n * (size_t)d * 4);

@@ -66,6 +66,10 @@ class lt_batch_item(C.Structure):
                 ("image", C.c_void_p), ("records", C.c_void_p), ("d_image", C.c_void_p), ("grads", lt_grads)]
 
 
+class lt_bidir_opts(C.Structure):
+    _fields_ = [("n_cam", C.c_int64), ("cam_mask", C.c_void_p), ("cam_hash", C.c_void_p)]
+
+
 class lt_batch_config(C.Structure):
     _fields_ = [("block_size", C.c_int), ("paths_per_thread", C.c_int), ("blocks_per_sm", C.c_int),
                 ("bvh_width", C.c_int)]
@@ -82,7 +86,7 @@ EXPORTS = ["lt_scene_create", "lt_scene_refit", "lt_scene_destroy", "lt_primal",
            "lt_sync_status", "lt_last_error", "lt_version", "lt_mlp_collect", "lt_mlp_init_stats", "lt_mlp_grad",
            "lt_mlp_adam", "lt_mlp_forward", "lt_naive_gradient_static", "lt_batch_create", "lt_batch_run",
            "lt_batch_set_config", "lt_batch_get_config", "lt_batch_tune", "lt_batch_destroy", "lt_lrb3_state_bytes",
-           "lt_backward_lrb2", "lt_lrb2_buffer_bytes"]
+           "lt_backward_lrb2", "lt_lrb2_buffer_bytes", "lt_bidir_primal", "lt_bidir_backward"]
 MLP_PARAMS, MLP_WEIGHTS = 5352, 5313
 
 
@@ -113,6 +117,8 @@ def lib():
             L.lt_lrb2_buffer_bytes.restype = C.c_size_t
             L.lt_lrb3_state_bytes.argtypes = [P(lt_render_opts)]
             L.lt_lrb3_state_bytes.restype = C.c_size_t
+            L.lt_bidir_primal.argtypes = [V, P(lt_params), P(lt_render_opts), P(lt_bidir_opts), V, V]
+            L.lt_bidir_backward.argtypes = [V, P(lt_params), P(lt_render_opts), P(lt_bidir_opts), V, P(lt_grads), V]
             L.lt_sync_status.argtypes = [V, V]
             L.lt_last_error.restype = C.c_char_p
             L.lt_version.restype = C.c_char_p
@@ -318,6 +324,31 @@ class Scene:
                                        nbytes, C.byref(gr), _stream(stream)))
         return g
 
+    @staticmethod
+    def bidir_opts(n_cam, cam_mask=None, cam_hash=None):
+        """Camera-side settings of the bidirectional estimator (see include/lt.h)."""
+        b = lt_bidir_opts(int(n_cam), None if cam_mask is None else cam_mask.data_ptr(),
+                          None if cam_hash is None else cam_hash.data_ptr())
+        b._keep = (cam_mask, cam_hash)
+        return b
+
+    def bidir_primal(self, o, b, image=None, albedo=None, Le=None, stream=None):
+        """Bidirectional image: light paths of `o` and camera samples of `b` (bidir_opts)."""
+        img = image if image is not None else self.new_image()
+        p = self.params(albedo, Le)
+        _check(lib().lt_bidir_primal(self._h, C.byref(p), C.byref(o), C.byref(b), _ptr(img), _stream(stream)))
+        return img
+
+    def bidir_backward(self, o, b, d_image, grads=None, accumulate=False, albedo=None, Le=None, stream=None):
+        """Gradient of <d_image, bidirectional image>: LRB-3 on the light paths, path replay
+        backpropagation on the camera samples."""
+        g = grads if grads is not None else self.new_grads()
+        p = self.params(albedo, Le)
+        gr = self._grads(*g, accumulate)
+        _check(lib().lt_bidir_backward(self._h, C.byref(p), C.byref(o), C.byref(b), _ptr(d_image.contiguous()),
+                                       C.byref(gr), _stream(stream)))
+        return g
+
     def mlp_collect(self, o, d_image, capacity, target_floor=0.0, stream=None):
         """Training pairs (features [n,16], targets [n]) from an LRB-3 pass-2 replay."""
         f = torch.empty((capacity, 16), device=self.device, dtype=torch.float32)
@@ -337,7 +368,8 @@ class Batch:
     """Many scenes in one persistent launch per pass (lt_batch_*).
 
     `items`: list of dicts with keys scene (Scene), n_paths, max_depth and optionally seed,
-    path_offset, n_norm, attached, albedo, Le, heights (refit by the primal passes),
+    path_offset, n_norm, attached, mask (uint8 per path, 0 = skip), albedo, Le, heights
+    (refit by the primal passes),
     d_image, reslrb (allocate ResLRB records), lrb3_state (allocate an LRB-3 state: the
     LRB-3 pass then runs in two kernels reusing the primal pass's validity masks),
     accumulate.  The batch allocates each item's
@@ -352,8 +384,8 @@ class Batch:
             it["_state"] = S.new_lrb3_state(it["n_paths"]) if it.get("lrb3_state") else None
             o = Scene.opts(seed=it.get("seed", 0), n_paths=it["n_paths"], max_depth=it["max_depth"],
                            attached=it.get("attached", 0), path_offset=it.get("path_offset", 0),
-                           n_norm=it.get("n_norm", 0), dbg_out=it.get("dbg_out"), lrb3_state=it["_state"],
-                           lrb3_mask_ready=int(it["_state"] is not None))
+                           n_norm=it.get("n_norm", 0), dbg_out=it.get("dbg_out"), mask=it.get("mask"),
+                           lrb3_state=it["_state"], lrb3_mask_ready=int(it["_state"] is not None))
             it.setdefault("albedo", S.albedo)
             it.setdefault("Le", S.Le)
             it.setdefault("d_image", torch.zeros((S.H, S.W, 3), device=S.device))

@@ -74,3 +74,21 @@ def test_argument_validation_without_gpu(liblt):
     assert liblt.lt_film_l2(None, None, 0, None, None, None) == 1
     assert liblt.lt_scene_refit(None, None, None) == 1
     assert liblt.lt_sync_status(None, None) == 1
+
+
+def test_size_queries_refuse_path_counts_that_would_wrap(liblt):
+    """Byte counts are derived from n_paths; beyond LT_MAX_PATHS (2^40) the size queries
+    return 0 instead of a wrapped-around size (and every call rejects the opts)."""
+    from paper_2609_32920_gb300 import lt
+    liblt.lt_naive_workspace_bytes.restype = C.c_size_t
+    liblt.lt_lrb2_buffer_bytes.restype = C.c_size_t
+    liblt.lt_lrb3_state_bytes.restype = C.c_size_t
+    o = lt.lt_render_opts()
+    o.max_depth = 64
+    o.n_paths = 1 << 40
+    assert liblt.lt_naive_workspace_bytes(C.byref(o)) == 256 * ((4 * (1 << 40) + 255) // 256) + (1 << 40) * 64 * 32
+    for n in ((1 << 40) + 1, 1 << 62):
+        o.n_paths = n
+        assert liblt.lt_naive_workspace_bytes(C.byref(o)) == 0
+        assert liblt.lt_lrb2_buffer_bytes(C.byref(o)) == 0
+        assert liblt.lt_lrb3_state_bytes(C.byref(o)) == 0

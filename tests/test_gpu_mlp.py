@@ -118,3 +118,48 @@ def test_learned_reservoir_target_unbiased_and_lower_variance():
     var = {k: L[k].var(axis=0, ddof=1).mean() for k in L}
     print("mean per-parameter variance", var)
     assert var["learned"] < var["plain"]
+
+
+def test_mlp_collect_pairs_match_oracle_connections():
+    """Every training pair of the learned target against an FP64 computation from the
+    oracle's own connections: the 16 features (position, arrival-side normal, arrival
+    direction, log throughput, relative depth, film position, log connection weight) and
+    the regression target log(|Lbar * L|_1 / lum(L) + floor) (Lbar: the filter-weighted
+    read of dI, Eq. 21).  Rows are matched one to one by depth and nearest film position
+    (rows of one depth lie far farther apart on the film than the FP32 drift of a
+    position); paths whose FP32 and FP64 decisions differ are masked on both sides.  Along
+    a path the FP32 vertex positions drift from the FP64 ones (each vertex is found from its
+    predecessor): up to a few 1e-3 pixels on the film at depth 6, which moves the tent
+    weights of the adjoint read and so the target by a few 1e-3; the bounds below allow for
+    that, and 99 % of the targets must agree within 1e-3."""
+    from scipy.spatial import cKDTree
+    sc = I.box_scene(64, heightmap=8, hm_std=0.03)
+    S = lt.Scene(sc)
+    n, D, seed = 1 << 13, 6, 17
+    dI_np = I.blob_adjoint(sc.W, sc.H, 5)
+    floor = 0.01 * float(np.abs(dI_np).max())
+    mask = agree_mask(S, sc, seed, n, D)
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, mask=torch.tensor(mask, device="cuda"))
+    f, t, cnt = S.mlp_collect(o, t32(dI_np), capacity=1 << 17, target_floor=floor)
+    rows = O.connections(sc, dI_np, seed=seed, n_paths=n, max_depth=D, mask=mask)
+    L, Lb = rows[:, 17:20], rows[:, 20:23]
+    lum = 0.2126 * L[:, 0] + 0.7152 * L[:, 1] + 0.0722 * L[:, 2]
+    rows, L, Lb, lum = rows[lum > 0], L[lum > 0], Lb[lum > 0], lum[lum > 0]
+    assert cnt == rows.shape[0]
+    ref_f = np.concatenate([rows[:, 2:11], np.log(rows[:, 11:14] + 1e-30), ((rows[:, 1] + 1) / D)[:, None],
+                            (rows[:, 14] / sc.W)[:, None], (rows[:, 15] / sc.H)[:, None],
+                            np.log(rows[:, 16] + 1e-30)[:, None]], axis=1)
+    ref_t = np.log(np.abs(Lb * L).sum(axis=1) / lum + floor)
+    gf, gt = f.cpu().numpy().astype(np.float64), t.cpu().numpy().astype(np.float64)
+    # key: depth (far apart) and film position in pixels
+    key = lambda F: np.stack([F[:, 12] * D * 1e3, F[:, 13] * sc.W, F[:, 14] * sc.H], axis=1)  # noqa: E731
+    dist, idx = cKDTree(key(ref_f)).query(key(gf))
+    assert dist.max() < 1e-2 and np.unique(idx).size == idx.size  # a one-to-one matching
+    ref_f, ref_t = ref_f[idx], ref_t[idx]
+    assert np.array_equal(gf[:, 12], np.float32(ref_f[:, 12]).astype(np.float64))  # same depths
+    assert np.abs(gf[:, 13:15] - ref_f[:, 13:15]).max() < 5e-5           # film position / size
+    assert np.abs(gf[:, 0:9] - ref_f[:, 0:9]).max() < 2e-4               # position, normal, direction
+    assert np.abs(gf[:, 9:12] - ref_f[:, 9:12]).max() < 5e-4             # log throughput
+    assert np.abs(gf[:, 15] - ref_f[:, 15]).max() < 5e-4                 # log connection weight
+    assert np.abs(gt - ref_t).max() < 5e-3                               # regression target
+    assert np.quantile(np.abs(gt - ref_t), 0.99) < 1e-3

@@ -45,6 +45,14 @@ MUTANTS = {
     "gauss_no_cut": ("const double inv_c = 1.0 / gauss_norm(), cut = std::exp(-4.5);",
                      "const double inv_c = 1.0 / gauss_norm(), cut = 0.0;",
                      ["test_gaussian_filter_definition_and_flux"]),
+    # bidirectional weights: the light-tracer side's density ratio without the pi of its film density
+    "bidir_ratio_pi": ("const double pfilm = c.geo * N * PI / ((double)sc.s->W * (double)sc.s->H);",
+                       "const double pfilm = c.geo * N / ((double)sc.s->W * (double)sc.s->H);",
+                       ["test_bidirectional_estimator_unbiased_and_exact"]),
+    # bidirectional weights: the camera side's next-event density without the cosine at the emitter
+    "bidir_nee_cos": ("const double pf0 = dot(v.ns, wn) * -dot(nL, wn) / (PI * dl * dl);",
+                      "const double pf0 = dot(v.ns, wn) / (PI * dl * dl);",
+                      ["test_bidirectional_estimator_unbiased_and_exact"]),
     # attached slide: intersection parameter with the wrong sign
     "slide_sign": ("T tt = dot(o - xprev, n) / dot(din, n);", "T tt = dot(xprev - o, n) / dot(din, n);",
                    ["test_attached_height_gradient_vs_frozen_central_differences"]),

@@ -474,3 +474,76 @@ def test_filter_kink_distance_query(oracle):
     assert np.allclose(kr[one, 0], d, rtol=0, atol=1e-12)
     assert np.all(kr[n_conn == 0, 0] == 1e9)
     assert np.all((kr[n_conn > 0, 0] >= 0) & (kr[n_conn > 0, 0] <= 0.5))
+
+
+def test_connection_query_reproduces_image_and_adjoints(oracle):
+    """The per-connection query (the source of the learned target's reference pairs) holds the
+    same connections the image and the gradient use: splatting its L at its u gives the
+    rendered image, its Lbar . L summed per path gives each path's delta_total (Eq. 14), its
+    counts the connection counts; and each row is geometrically consistent (unit normal and
+    direction, the normal on the arrival side, L = throughput x albedo x connection weight
+    for the uniform albedo of the height field)."""
+    sc = I.box_scene(24, heightmap=5, hm_std=0.03)
+    dI = I.smooth_adjoint(sc.W, sc.H, 9)
+    kw = dict(seed=6, n_paths=1 << 11, max_depth=5)
+    rows = oracle.connections(sc, dI, **kw)
+    img = oracle.render(sc, **kw)
+    acc = np.zeros_like(img)
+    for r in rows:
+        px, py, w = oracle.filter_taps(0, sc.W, sc.H, r[14], r[15])
+        for x, y, ww in zip(px, py, w):
+            acc[y, x] += ww * r[17:20]
+    assert np.allclose(acc, img, rtol=1e-12, atol=1e-15)
+    g = oracle.gradient(sc, dI, want_dbg=True, **kw)
+    per_path = np.zeros((kw["n_paths"], 3))
+    np.add.at(per_path, rows[:, 0].astype(int), rows[:, 20:23] * rows[:, 17:20])
+    assert np.allclose(per_path, g["dbg"][:, :3], rtol=1e-12, atol=1e-18)
+    assert np.array_equal(np.bincount(rows[:, 0].astype(int), minlength=kw["n_paths"]), g["dbg"][:, 3])
+    assert np.allclose(np.linalg.norm(rows[:, 5:8], axis=1), 1, atol=1e-12)
+    assert np.allclose(np.linalg.norm(rows[:, 8:11], axis=1), 1, atol=1e-12)
+    assert np.all(np.einsum("ij,ij->i", rows[:, 5:8], rows[:, 8:11]) < 0)
+    x, y, z = rows[:, 2], rows[:, 3], rows[:, 4]
+    hm = (x > 0.26) & (x < 0.74) & (z > 0.26) & (z < 0.74) & (y > 0.1) & (y < 0.4)  # the height field (albedo 0.5)
+    assert hm.sum() > 10
+    assert np.allclose(rows[hm, 17:20], rows[hm, 11:14] * 0.5 * rows[hm, 16:17], rtol=1e-12)
+
+
+def test_bidirectional_estimator_unbiased_and_exact(oracle):
+    """The bidirectional estimator (light-tracer connections and camera samples with
+    next-event estimation, balance heuristic): without camera samples it is the light
+    tracer exactly; its expectation is the light tracer's, and so is that of the camera
+    samples alone (per-pixel z-scores over 16 seeds; a wrong density ratio would leave the
+    two strategies' weights not summing to one and bias the image); its naive-AD gradient
+    equals central differences of its own image (detached: a polynomial in the albedos with
+    weights that depend on geometry only) and is linear in Le."""
+    sc = I.box_scene(16)
+    D = 3
+    dI = I.smooth_adjoint(sc.W, sc.H, 17)
+    assert np.array_equal(oracle.render_bidir(sc, 0, seed=1, n_paths=1 << 12, max_depth=D),
+                          oracle.render(sc, seed=1, n_paths=1 << 12, max_depth=D))
+    g0 = oracle.gradient_bidir(sc, dI, 0, seed=1, n_paths=1 << 12, max_depth=D)
+    g1 = oracle.gradient(sc, dI, seed=1, n_paths=1 << 12, max_depth=D)
+    assert np.allclose(g0["d_albedo"], g1["d_albedo"], rtol=1e-12, atol=1e-300)
+    assert np.allclose(g0["d_Le"], g1["d_Le"], rtol=1e-12)
+    S = 16
+    lt = np.array([oracle.render(sc, seed=100 + s, n_paths=1 << 14, max_depth=D) for s in range(S)])
+    for n_light, base in ((1 << 14, 200), (0, 300)):
+        bi = np.array([oracle.render_bidir(sc, 1 << 14, seed=base + s, n_paths=n_light, max_depth=D)
+                       for s in range(S)])
+        d = bi.mean(0) - lt.mean(0)
+        se = np.sqrt(lt.var(0, ddof=1) / S + bi.var(0, ddof=1) / S)
+        z = d[se > 0] / se[se > 0]
+        assert 0.8 < np.mean(z * z) < 1.35 and np.abs(z).max() < 4.5, (n_light, np.mean(z * z), np.abs(z).max())
+    kw = dict(seed=5, n_paths=1 << 11, max_depth=D)
+    g = oracle.gradient_bidir(sc, dI, 1 << 11, **kw)
+    rng = np.random.default_rng(2)
+    v = rng.normal(size=sc.albedo.size)
+    h = 1e-3
+
+    def loss(a):
+        return (oracle.render_bidir(sc, 1 << 11, albedo=a, **kw) * dI).sum()
+    fd = (loss(sc.albedo + h * v) - loss(sc.albedo - h * v)) / (2 * h)
+    assert g["d_albedo"] @ v == pytest.approx(fd, rel=1e-7)
+    img = oracle.render_bidir(sc, 1 << 11, **kw)
+    assert np.allclose(g["d_Le"], (dI * img).sum(axis=(0, 1)) / sc.Le, rtol=1e-12)
+    assert g["loss"] == pytest.approx((dI * img).sum(), rel=1e-12)

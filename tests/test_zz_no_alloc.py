@@ -37,8 +37,10 @@ def test_static_tape_gradient_matches_workspace_calls_twice_in_a_row(attached):
     sc = I.box_scene(32, heightmap=6, hm_std=0.03)
     S = lt.Scene(sc)
     dI = t32(I.smooth_adjoint(sc.W, sc.H, 91))
-    for seed in (5, 6):  # two calls in a row share (and overwrite) the fixed tape
-        o = S.opts(seed=seed, n_paths=3000, max_depth=7, attached=attached)
+    # two calls in a row share (and overwrite) the fixed tape; the second is smaller, so its
+    # tape layout (header size, depth stride) differs and stale entries of the first remain
+    for seed, n, D in ((5, 3000, 7), (6, 1200, 4)):
+        o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached)
         assert S.naive_workspace_bytes(o) <= LT_NAIVE_STATIC_BYTES
         ws = torch.empty(S.naive_workspace_bytes(o), dtype=torch.uint8, device="cuda")
         ref_img = S.primal(o, estimator=lt.EST_NAIVE, aux=ws).clone()
@@ -65,3 +67,6 @@ def test_static_tape_rejects_requests_beyond_its_size():
     grads = S.new_grads()
     assert _static_call(S, o, dI, img, grads) == lt.LT_ERR_INVALID_ARG
     assert b"fixed scratch" in lt.lib().lt_last_error()
+    # a path count whose byte size would wrap around is rejected as well
+    o = S.opts(seed=0, n_paths=1 << 62, max_depth=64)
+    assert _static_call(S, o, dI, img, grads) == lt.LT_ERR_INVALID_ARG
