@@ -242,13 +242,13 @@ def run_reference(args):
 # ------------------------------------------------------------------ GPU arm
 class Step:
     """One pass of the hot path on a workload: refit the height field (update_tris,
-    refit_nodes, refit_wide<4>, refit_wide<8>: every width stays current), primal light
+    refit_nodes, refit_big, refit_wide<4>, refit_wide<8>: every width stays current), primal light
     tracing storing the paths' connection-validity masks (1 kernel), film L2 loss and
     image adjoint (1), LRB-3-pass backward in its three-pass form, attached (pass 2 and
     pass 3: 2 kernels).  Events around the primal and the backward pair time them on the
     launching stream."""
 
-    LAUNCHES = 8
+    LAUNCHES = 9
 
     def __init__(self, name, dev, path_offset=0, n_norm=0, n_paths=0):
         import torch
@@ -453,18 +453,23 @@ def run_ours(args):
     if rank == 0:
         studies[other] = workload_study(other, dev, flush, barrier, args.steps)
     if not args.no_sweep:
+        studies["scatter"] = scatter_study(step, flush)
         studies["methods"], studies["memory_vs_depth"] = method_sweep(step, dev, flush)
         if rank == 0:
             box = Step("box256_hm32", dev)
             studies["box_methods"], studies["box_memory_vs_depth"] = method_sweep(box, dev, flush)
             studies["russian_roulette"] = roulette_study(box, dev, flush)
             del box
+    if not args.no_sweep and rank == 0:
+        studies["bidirectional"] = bidir_study(dev, flush)
     if not args.no_learned and rank == 0:
         studies["learned_target"] = learned_target_study(dev)
     if not args.no_batch and rank == 0:
         studies["batched"] = batched_study(dev)
     if not args.no_inverse and rank == 0:
-        studies["caustic_inverse"] = caustic_inverse_study(dev)
+        studies["caustic_inverse"] = {
+            "configured (lr 1e-3, per-vertex heights, L2)": caustic_inverse_study(dev, lr=1e-3),
+            "blurred loss, smooth heights": caustic_inverse_study(dev, lr=2e-4, blur_px=8, smooth_cells=8)}
     clk = clocks.stop()
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N=1 only)
@@ -504,6 +509,77 @@ def workload_study(name, dev, flush, barrier, steps):
     ms = statistics.median(step_ms)
     return {"config": workload_config(step.n, name), "ms_per_step": ms, "paths_per_s": step.n / (ms * 1e-3),
             "primal_ms": statistics.median(primal_ms), "backward_ms": statistics.median(bwd_ms)}
+
+
+def scatter_study(step, flush, reps=3):
+    """Primal and LRB-3 backward times of the workload for each way of bringing gradients and
+    splats to memory (opts.scatter 0-3, see include/lt.h)."""
+    import torch
+    S, st = step.S, step.stream
+    names = {0: "default (46 KB shared-memory arrays, else plain global atomics)",
+             1: "shared-memory arrays up to the opt-in limit", 2: "plain global atomics",
+             3: "warp-aggregated global atomics for gradients and splats"}
+    out = {"workload": f"{step.name}, 2^{step.n.bit_length() - 1} paths, depth {step.depth}, attached"}
+    for mode in (0, 1, 2, 3):
+        kw = dict(seed=1, n_paths=step.n, max_depth=step.depth, lrb3_state=step.state, scatter=mode)
+        op, om = S.opts(**kw), S.opts(attached=1, lrb3_mask_ready=1, **kw)
+        p_ms, b_ms = [], []
+        for r in range(reps + 1):
+            flush.fill_(r)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(st)
+            S.primal(op, image=step.img)
+            e[1].record(st)
+            S.backward_lrb3(om, step.dI, grads=step.grads)
+            e[2].record(st)
+            torch.cuda.synchronize()
+            if r:
+                p_ms.append(e[0].elapsed_time(e[1]))
+                b_ms.append(e[1].elapsed_time(e[2]))
+        out[str(mode)] = {"mode": names[mode], "primal_ms": statistics.median(p_ms),
+                          "backward_ms": statistics.median(b_ms)}
+    S.sync_status()
+    return out
+
+
+def bidir_study(dev, flush, seeds=16, n_log2=21, m_log2=19, depth=6):
+    """The bidirectional estimator against the light tracer alone on the box with textured
+    walls (256x256, detached albedo and Le): time of one gradient (primal + backward) and the
+    mean per-parameter variance of the albedo gradient over seeds; time x variance is the
+    efficiency (lower is better)."""
+    import torch
+
+    from paper_2609_32920_gb300 import inputs as I
+    from paper_2609_32920_gb300 import lt
+    sc = I.box_scene(256)
+    S = lt.Scene(sc)
+    dI = torch.tensor(I.smooth_adjoint(sc.W, sc.H, 3), dtype=torch.float32, device=dev)
+    n, m = 1 << n_log2, 1 << m_log2
+    st = torch.cuda.current_stream()
+    out = {"workload": f"box256 (textured walls), detached, depth {depth}, 2^{n_log2} light paths, "
+                       f"2^{m_log2} camera samples, {seeds} seeds"}
+    for name, mc in (("light_tracer", 0), ("bidirectional", m)):
+        G, ms = [], []
+        for s_ in range(seeds + 1):
+            o = S.opts(seed=40 + s_, n_paths=n, max_depth=depth)
+            b = S.bidir_opts(mc)
+            flush.fill_(s_)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            S.bidir_primal(o, b)
+            g = S.bidir_backward(o, b, dI)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if s_:
+                ms.append(e0.elapsed_time(e1))
+                G.append(g[0].double().cpu())
+        G = torch.stack(G)
+        var = float(G.var(dim=0, unbiased=True).mean())
+        out[name] = {"ms_per_gradient": statistics.median(ms), "variance": var,
+                     "time_x_variance": statistics.median(ms) * var}
+    out["efficiency_gain"] = out["light_tracer"]["time_x_variance"] / out["bidirectional"]["time_x_variance"]
+    S.sync_status()
+    return out
 
 
 METHODS = ("lrb3", "lrb3_fused", "lrb2", "reslrb", "naive")
@@ -705,15 +781,134 @@ def _learned_one(dev, kind, seeds, paths_log2, depth):
 
 
 def learned_target_study(dev):
-    return {"caustic": _learned_one(dev, "caustic", 16, 20, 32), "interior": _learned_one(dev, "interior", 16, 20, 16)}
+    return {"caustic": _learned_one(dev, "caustic", 16, 20, 32), "interior": _learned_one(dev, "interior", 16, 20, 16),
+            "cfg_stated": learned_stated_study(dev)}
 
 
-def caustic_inverse_study(dev, steps=200, paths_log2=24, depth=8, lr=1e-3):
+def learned_stated_study(dev, seeds=16, ref_seeds=256, depth=32):
+    """The learned reservoir target at its stated size: ResLRB at depth 32 with 2^24 paths
+    per gradient on the caustic workload (slab512_hm128, attached heights), the network
+    trained on 2^20 pairs collected by an LRB-3 pass-2 replay; and, because caustic paths
+    have about one connection each, on the slab inside the textured box (slabbox256_hm64,
+    2^22 paths).  Per workload: time x variance of ResLRB with the luminance and with the
+    learned target over `seeds` seeds, and each one's mean gradient error
+    ||mean_s g - g_ref|| / ||g_ref|| next to the error that its variance alone predicts
+    (sqrt(P Var / S) / ||g_ref||: an unbiased estimator's error matches it), with g_ref the
+    LRB-3 gradient averaged over `ref_seeds` seeds."""
+    import torch
+
+    from paper_2609_32920_gb300 import inputs as I
+    from paper_2609_32920_gb300 import lt
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        out = fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    res = {}
+    for kind in ("caustic", "slab_in_box"):
+        if kind == "caustic":
+            n = 1 << 24
+            sc = I.slab_scene(512, n=128, seed=0)
+            S = lt.Scene(sc)
+            T_S = lt.Scene(I.slab_scene(512, n=128, seed=1))
+            target = T_S.primal(T_S.opts(seed=7, n_paths=n, max_depth=8))
+            del T_S
+            img = S.primal(S.opts(seed=8, n_paths=n, max_depth=8))
+            _, dI = lt.film_l2(img, target)
+        else:
+            n = 1 << 22
+            sc = I.slab_in_box(256, n=64, seed=0)
+            S = lt.Scene(sc)
+            dI = torch.tensor(I.blob_adjoint(sc.W, sc.H, 81), dtype=torch.float32, device=dev)
+        (f, t, cnt), ms_collect = timed(lambda: S.mlp_collect(
+            S.opts(seed=9, n_paths=n, max_depth=depth, attached=1), dI, capacity=1 << 20,
+            target_floor=0.01 * float(dI.abs().max())))
+        P = lt.mlp_init(0)
+        losses, ms_train = timed(lambda: lt.mlp_train(P, f, t, epochs=20, batch=4096, lr=1e-3))
+        state = S.new_lrb3_state(n)
+        ref = torch.zeros(S.n_heights, dtype=torch.float64, device=dev)
+        for s_ in range(ref_seeds):
+            o = S.opts(seed=20000 + s_, n_paths=n, max_depth=depth, attached=1, lrb3_state=state)
+            S.primal(o)
+            om = S.opts(seed=20000 + s_, n_paths=n, max_depth=depth, attached=1, lrb3_state=state, lrb3_mask_ready=1)
+            ref += S.backward_lrb3(om, dI)[2][: S.n_heights].double()
+        ref /= ref_seeds
+        rec = torch.empty((n, 8), device=dev)
+        row = {"workload": f"{sc.name}, depth {depth}, 2^{n.bit_length() - 1} paths per gradient, attached heights, "
+                           f"{seeds} seeds; g_ref = LRB-3 over {ref_seeds} seeds",
+               "connections_per_path": cnt / n, "pairs": int(f.shape[0]), "collect_ms": ms_collect,
+               "train_ms": ms_train, "train_loss_first_last": [losses[0], losses[-1]]}
+        for name, extra in (("luminance", {}), ("learned", {"target": lt.TARGET_MLP, "mlp": P})):
+            G, ms = [], []
+            for s_ in range(seeds):
+                o = S.opts(seed=100 + s_, n_paths=n, max_depth=depth, attached=1, **extra)
+                g, m_ = timed(lambda: (S.primal(o, estimator=lt.EST_RESLRB, aux=rec), S.backward_reslrb(o, dI, rec))[1])
+                G.append(g[2][: S.n_heights].double())
+                ms.append(m_)
+            G = torch.stack(G)
+            var = float(G.var(dim=0, unbiased=True).mean())
+            nref = float(torch.linalg.norm(ref))
+            row[name] = {"ms_per_gradient": statistics.median(ms), "variance": var,
+                         "time_x_variance": statistics.median(ms) * var,
+                         "mean_gradient_error": float(torch.linalg.norm(G.mean(0) - ref)) / nref,
+                         "noise_only_error": (S.n_heights * var / seeds) ** 0.5 / nref}
+        row["efficiency_gain"] = row["luminance"]["time_x_variance"] / row["learned"]["time_x_variance"]
+        S.sync_status()
+        res[kind] = row
+        del S
+    return res
+
+
+def _gauss1d(sigma, dev):
+    import torch
+    r = int(3 * sigma + 1)
+    x = torch.arange(-r, r + 1, device=dev, dtype=torch.float32)
+    k = torch.exp(-x * x / (2 * sigma * sigma))
+    return k / k.sum(), r
+
+
+def blur_image(im, sigma):
+    """Separable Gaussian blur of an [H, W, 3] image with zero padding (a symmetric linear
+    operator, so it is its own adjoint)."""
+    import torch
+    if not sigma:
+        return im
+    k, r = _gauss1d(sigma, im.device)
+    x = im.permute(2, 0, 1).unsqueeze(1)
+    x = torch.nn.functional.conv2d(x, k.view(1, 1, 1, -1), padding=(0, r))
+    x = torch.nn.functional.conv2d(x, k.view(1, 1, -1, 1), padding=(r, 0))
+    return x.squeeze(1).permute(1, 2, 0).contiguous()
+
+
+def blur_field(g, n, sigma):
+    """Separable Gaussian blur of an n x n parameter field (edge values repeated)."""
+    import torch
+    if not sigma:
+        return g
+    k, r = _gauss1d(sigma, g.device)
+    G = g.view(1, 1, n, n)
+    G = torch.nn.functional.conv2d(torch.nn.functional.pad(G, (r, r, 0, 0), mode="replicate"), k.view(1, 1, 1, -1))
+    G = torch.nn.functional.conv2d(torch.nn.functional.pad(G, (0, 0, r, r), mode="replicate"), k.view(1, 1, -1, 1))
+    return G.view(-1)
+
+
+def caustic_inverse_study(dev, steps=200, paths_log2=24, depth=8, lr=1e-3, blur_px=0, smooth_cells=0):
     """The paper's geometric inverse problem on the caustic workload: starting from a flat
     slab top, recover the 128x128 height field of the dielectric slab (512x512 film) from
-    the caustic it casts, by Adam on the heights with attached LRB-3 gradients of the L2
-    film loss, 2^24 light paths per iteration (a new seed each), against a target rendered
-    from the true height field (sum of Gaussians, seed 1) at 2^26 paths."""
+    the caustic it casts, by Adam with attached LRB-3 gradients, 2^24 light paths per
+    iteration (a new seed each), against a target rendered from the true height field (sum
+    of Gaussians, seed 1) at 2^26 paths.  blur_px > 0: the loss compares the two images
+    after a Gaussian blur of that standard deviation (pixels), whose adjoint is the blurred
+    residual; smooth_cells > 0: Adam moves a latent field z and the heights are z blurred by
+    that many cells (the gradient of z is the blurred height gradient).  Reported: the loss,
+    the caustic error at 2^26 paths (relative L2, raw and after a 4-pixel blur; a second
+    render of the true heights gives the noise floor) and the height error (RMSE, and with
+    the mean removed, since a constant offset does not change the caustic)."""
     import torch
 
     from paper_2609_32920_gb300 import inputs as I
@@ -726,49 +921,63 @@ def caustic_inverse_study(dev, steps=200, paths_log2=24, depth=8, lr=1e-3):
     sc = I.slab_scene(512, n=128, seed=0, flat=True)
     S = lt.Scene(sc)
     h_true = torch.tensor(true_sc.heights, dtype=torch.float32, device=dev)
-    h = torch.zeros_like(h_true).requires_grad_(True)
-    opt = torch.optim.Adam([h], lr=lr)
+    z = torch.zeros_like(h_true).requires_grad_(True)
+    opt = torch.optim.Adam([z], lr=lr)
     state = S.new_lrb3_state(n)
     img = S.new_image()
     dI = torch.empty_like(img)
     loss = torch.empty(1, device=dev)
     grads = S.new_grads()
+    bt = blur_image(target, blur_px)
     losses = []
-    rmse0 = float(torch.sqrt(((h.detach() - h_true) ** 2).mean()))
+
+    def evaluate(hh):
+        S.refit(hh)
+        im = S.primal(S.opts(seed=777, n_paths=4 * n, max_depth=depth))
+        a, b = blur_image(im, 4), blur_image(target, 4)
+        d = hh - h_true
+        return {"caustic_rel_l2": float(torch.linalg.norm(im - target) / torch.linalg.norm(target)),
+                "caustic_rel_l2_blur4": float(torch.linalg.norm(a - b) / torch.linalg.norm(b)),
+                "height_rmse_m": float(torch.sqrt((d ** 2).mean())),
+                "height_rmse_shape_m": float(torch.sqrt(((d - d.mean()) ** 2).mean()))}
+
+    ev = {"floor (true heights)": evaluate(h_true), "0": evaluate(torch.zeros_like(h_true))}
     stream = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a.record(stream)
+    ms = 0.0
     for it in range(steps):
-        S.refit(h.detach())
+        torch.cuda.synchronize()
+        a.record(stream)
+        h = blur_field(z.detach(), 128, smooth_cells)
+        S.refit(h)
         o = S.opts(seed=1000 + it, n_paths=n, max_depth=depth, attached=1, lrb3_state=state)
         S.primal(o, image=img)
-        lt.film_l2(img, target, d_image=dI, loss=loss)
+        if blur_px:
+            r = blur_image(img, blur_px) - bt
+            losses.append((r * r).mean())
+            dI = blur_image(2.0 * r / r.numel(), blur_px)
+        else:
+            lt.film_l2(img, target, d_image=dI, loss=loss)
+            losses.append(loss.clone())
         om = S.opts(seed=1000 + it, n_paths=n, max_depth=depth, attached=1, lrb3_state=state, lrb3_mask_ready=1)
         S.backward_lrb3(om, dI, grads=grads)
-        h.grad = grads[2][: h.numel()].clone()
+        z.grad = blur_field(grads[2][: h.numel()].clone(), 128, smooth_cells)
         opt.step()
-        losses.append(loss.clone())
-    b.record(stream)
-    torch.cuda.synchronize()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        if (it + 1) % 100 == 0:
+            ev[str(it + 1)] = evaluate(blur_field(z.detach(), 128, smooth_cells))
     S.sync_status()
     L = [float(x) for x in losses]
-    rmse1 = float(torch.sqrt(((h.detach() - h_true) ** 2).mean()))
-
-    def caustic_error(heights):
-        # relative L2 distance of a 2^26-path render from the target (both with little noise)
-        S.refit(heights)
-        im = S.primal(S.opts(seed=777, n_paths=4 * n, max_depth=depth))
-        return float(torch.linalg.norm(im - target) / torch.linalg.norm(target))
-
-    err = [caustic_error(torch.zeros_like(h_true)), caustic_error(h.detach())]
     return {"workload": "slab512_hm128 (caustic), flat start, 128x128 heights, depth 8, 2^%d paths per "
                         "iteration, %d Adam steps lr %g" % (paths_log2, steps, lr),
-            "ms_per_iteration": a.elapsed_time(b) / steps,
+            "loss": "L2 of images blurred by %g px" % blur_px if blur_px else "L2 (film_l2)",
+            "parameterisation": "heights = latent blurred by %g cells" % smooth_cells if smooth_cells
+                                else "per-vertex heights",
+            "ms_per_iteration": ms / steps,
             "loss_mean_of_10_at": {str(i): sum(L[i:i + 10]) / 10 for i in range(0, steps, max(10, steps // 5))},
-            "loss_first10_last10": [sum(L[:10]) / 10, sum(L[-10:]) / 10],
-            "height_rmse_m_start_end": [rmse0, rmse1],
-            "caustic_rel_l2_start_end_2p%d" % (paths_log2 + 2): err}
+            "eval": ev}
 
 
 def batched_study(dev, n_scenes=64, reps=3):

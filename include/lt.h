@@ -144,6 +144,20 @@ typedef struct {
   int bvh_width;        /* BVH node width traversed: 2 (threaded binary BVH, stackless),
                            4 or 8 (wide BVH, ordered stack traversal); 0 = 4.  The
                            scene holds all three; results agree up to ties.        */
+  int scatter;          /* how gradients and splats reach memory (Eq. 3 scatter, Eq. 20
+                           splat); results agree up to the order of float additions:
+                           0 default: albedo then height gradients accumulate per block
+                             in shared memory when the arrays fit in 46 KB, and are added
+                             to the caller's arrays once per block; an array that does
+                             not fit is added with plain global atomics, and so are the
+                             splats;
+                           1 as 0, the per-block arrays up to the device's opt-in shared
+                             memory per block (227 KB on GB300; fewer blocks may then be
+                             resident per SM);
+                           2 no per-block arrays, plain global atomics;
+                           3 no per-block arrays, warp-aggregated global atomics (lanes of
+                             a warp adding to the same element sum first) for the
+                             gradients and for the plain primal's splats.           */
 } lt_render_opts;
 
 /* Gradient outputs (DEVICE, FP32, caller-owned).  NULL skips a parameter group.

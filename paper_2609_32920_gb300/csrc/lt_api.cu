@@ -158,12 +158,15 @@ struct lt_scene {
   int n_albedo = 0, n_heights = 0, n_tris_h = 0;
   bool has_dielectric = false;
   int sms = 1;
+  int smem_optin = 48 * 1024;  // opt-in dynamic shared memory per block
   // device buffers
   float4* d_prim = nullptr;
   int4* d_prim_h = nullptr;
   float4* d_tri_base = nullptr;
   float4* d_node = nullptr;
   int2* d_range = nullptr;
+  int* d_big = nullptr;  // binary nodes refitted by a whole block
+  int n_big = 0;
   int4* d_mat = nullptr;
   float* d_ior = nullptr;
   int* d_err = nullptr;
@@ -179,18 +182,19 @@ namespace {
 void free_scene(lt_scene* s) {
   if (!s) return;
   cudaFree(s->d_prim); cudaFree(s->d_prim_h); cudaFree(s->d_tri_base); cudaFree(s->d_node);
-  cudaFree(s->d_range); cudaFree(s->d_mat); cudaFree(s->d_ior); cudaFree(s->d_err);
+  cudaFree(s->d_range); cudaFree(s->d_big); cudaFree(s->d_mat); cudaFree(s->d_ior); cudaFree(s->d_err);
   for (int k = 0; k < 2; ++k) { cudaFree(s->d_wnode[k]); cudaFree(s->d_wmap[k]); }
   delete s;
 }
 
 RefitArgs refit_args(const lt_scene* s, const float* heights) {
   RefitArgs ra{s->d_prim, s->d_prim_h, s->d_tri_base, heights, s->n_prims, s->d_node, s->d_range, s->n_nodes,
+               s->d_big, s->n_big,
                {s->d_wnode[0], s->d_wnode[1]}, {s->d_wmap[0], s->d_wmap[1]}, {s->n_wnodes[0], s->n_wnodes[1]}};
   return ra;
 }
 
-// The scene as one call's kernels see it: BVH width from opts (0 = 4).
+// The scene as one call's kernels see it: BVH width from opts (0 = 4), plain atomics.
 DevScene dev_for(const lt_scene* s, int width) {
   if (width == 0) width = 4;
   DevScene S = s->dev;
@@ -203,6 +207,13 @@ DevScene dev_for(const lt_scene* s, int width) {
     S.wnode = s->d_wnode[k];
     S.n_wnodes = s->n_wnodes[k];
   }
+  S.atomics = 0;
+  return S;
+}
+// ... and with the call's atomics (opts->scatter).
+DevScene dev_for(const lt_scene* s, const lt_render_opts* o) {
+  DevScene S = dev_for(s, o->bvh_width);
+  S.atomics = o->scatter == 3 ? 2 : 0;
   return S;
 }
 
@@ -319,6 +330,7 @@ lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->rr_depth < 0 || (o->rr_depth > 0 && !(o->rr_prob > 0.0f && o->rr_prob <= 1.0f)))
     return fail(LT_ERR_INVALID_ARG, "rr_depth must be >= 0 and rr_prob in (0, 1]");
   if (o->filter != 0 && o->filter != 1) return fail(LT_ERR_INVALID_ARG, "filter must be 0 (tent) or 1 (Gaussian)");
+  if (o->scatter < 0 || o->scatter > 3) return fail(LT_ERR_INVALID_ARG, "scatter must be 0, 1, 2 or 3");
   return LT_OK;
 }
 
@@ -344,15 +356,19 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.filter = o->filter;
   k.list = nullptr;
   k.list_n = nullptr;
+  k.ticket = nullptr;
   return k;
 }
 
 // Gradients accumulate per block in shared memory for each parameter array that fits in
-// the default 48 KB shared-memory limit (46 KB, leaving room for static shared memory):
-// the albedo array first (usually small and hit by every diffuse vertex), then the
-// heights if room remains; an array that does not fit goes to global memory directly.
-void set_privatization(const lt_scene* s, const lt_grads* g, KParams& kp) {
-  const int budget = (46 * 1024) / (int)sizeof(float);
+// the budget (opts->scatter 0: the default 48 KB shared-memory limit less room for static
+// shared memory, 46 KB; 1: the device's opt-in limit less 4 KB; 2, 3: none): the albedo
+// array first (usually small and hit by every diffuse vertex), then the heights if room
+// remains; an array that does not fit goes to global memory.
+void set_privatization(const lt_scene* s, const lt_grads* g, KParams& kp, int scatter = 0) {
+  const int budget = scatter >= 2 ? 0
+                     : scatter == 1 ? (s->smem_optin - 4096) / (int)sizeof(float)
+                                    : (46 * 1024) / (int)sizeof(float);
   kp.n_alb = (g && g->d_albedo && s->n_albedo > 0 && s->n_albedo <= budget) ? s->n_albedo : 0;
   kp.n_h = (g && g->d_heights && s->n_heights > 0 && s->n_heights <= budget - kp.n_alb) ? s->n_heights : 0;
   kp.priv_n = kp.n_alb + kp.n_h;
@@ -429,11 +445,11 @@ lt_status lt_naive_gradient_static(lt_scene* s, const lt_params* p, const lt_ren
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
   const LaunchCfg L = cfg_for(s, o);
-  cudaError_t e = launch_primal(dev_for(s, o->bvh_width), kparams(p, o), LT_EST_NAIVE, image, tape, L, st);
+  cudaError_t e = launch_primal(dev_for(s, o), kparams(p, o), LT_EST_NAIVE, image, tape, L, st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_naive_gradient_static: ") + cudaGetErrorString(e));
   KParams kb = kparams(p, o);
-  set_privatization(s, g, kb);
-  e = launch_naive(dev_for(s, o->bvh_width), kb, o->attached != 0, s->has_dielectric, dI, tape, gp, L, st);
+  set_privatization(s, g, kb, o->scatter);
+  e = launch_naive(dev_for(s, o), kb, o->attached != 0, s->has_dielectric, dI, tape, gp, L, st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_naive_gradient_static: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -556,6 +572,9 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
   lt_scene* s = new lt_scene();
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device) != cudaSuccess ||
+      s->smem_optin < 48 * 1024)
+    s->smem_optin = 48 * 1024;
   s->n_albedo = d->n_albedo;
   s->n_heights = d->n_heights;
   s->has_dielectric = has_diel;
@@ -572,6 +591,11 @@ lt_status lt_scene_create(const lt_scene_desc* d, void* stream, lt_scene** out) 
   if (!e) e = up((void**)&s->d_tri_base, tri_base.data(), tri_base.size() * sizeof(float4));
   if (!e) e = up((void**)&s->d_node, node.data(), node.size() * sizeof(float4));
   if (!e) e = up((void**)&s->d_range, range.data(), range.size() * sizeof(int2));
+  std::vector<int> big;
+  for (int i = 0; i < nn; ++i)
+    if (range[i].y - range[i].x > kRefitBig) big.push_back(i);
+  s->n_big = (int)big.size();
+  if (!e && !big.empty()) e = up((void**)&s->d_big, big.data(), big.size() * sizeof(int));
   if (!e) e = up((void**)&s->d_mat, mats.data(), mats.size() * sizeof(int4));
   if (!e) e = up((void**)&s->d_ior, iors.data(), iors.size() * sizeof(float));
   for (int k = 0; k < 2 && !e; ++k) {
@@ -682,7 +706,7 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
       LT_CUDA(cudaMemsetAsync(kp.list_n, 0, sizeof(unsigned long long), st));
     }
   }
-  cudaError_t e = launch_primal(dev_for(s, o->bvh_width), kp, est, image, aux, cfg_for(s, o), st);
+  cudaError_t e = launch_primal(dev_for(s, o), kp, est, image, aux, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_primal: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -700,14 +724,16 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
-  set_privatization(s, g, kp);
+  set_privatization(s, g, kp, o->scatter);
   if (o->lrb3_state && o->lrb3_mask_ready && o->n_paths <= kListMaxPaths) {
     // the primal listed the paths with a valid connection: passes 2 and 3 visit only those
     char* base = (char*)o->lrb3_state;
     kp.list = (uint32_t*)(base + lrb3_state_list(o->n_paths));
     kp.list_n = (unsigned long long*)(base + lrb3_state_count(o->n_paths));
+    kp.ticket = kp.list_n + 1;
+    LT_CUDA(cudaMemsetAsync(kp.ticket, 0, 2 * sizeof(unsigned long long), st));
   }
-  cudaError_t e = launch_lrb3(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, gp,
+  cudaError_t e = launch_lrb3(dev_for(s, o), kp, o->attached != 0, s->has_dielectric, dI, gp,
                               o->lrb3_state, o->lrb3_state && o->lrb3_mask_ready, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
   return LT_OK;
@@ -724,8 +750,8 @@ lt_status lt_backward_reslrb(lt_scene* s, const lt_params* p, const lt_render_op
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
-  set_privatization(s, g, kp);
-  cudaError_t e = launch_reslrb(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
+  set_privatization(s, g, kp, o->scatter);
+  cudaError_t e = launch_reslrb(dev_for(s, o), kp, o->attached != 0, s->has_dielectric, dI, rec, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_reslrb: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -743,8 +769,8 @@ lt_status lt_backward_lrb2(lt_scene* s, const lt_params* p, const lt_render_opts
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
-  set_privatization(s, g, kp);
-  cudaError_t e = launch_lrb2(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, buf, gp,
+  set_privatization(s, g, kp, o->scatter);
+  cudaError_t e = launch_lrb2(dev_for(s, o), kp, o->attached != 0, s->has_dielectric, dI, buf, gp,
                               cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb2: ") + cudaGetErrorString(e));
   return LT_OK;
@@ -763,8 +789,8 @@ lt_status lt_backward_naive(lt_scene* s, const lt_params* p, const lt_render_opt
   if (v != LT_OK) return v;
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
-  set_privatization(s, g, kp);
-  cudaError_t e = launch_naive(dev_for(s, o->bvh_width), kp, o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
+  set_privatization(s, g, kp, o->scatter);
+  cudaError_t e = launch_naive(dev_for(s, o), kp, o->attached != 0, s->has_dielectric, dI, ws, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_naive: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -796,7 +822,7 @@ lt_status lt_bidir_primal(lt_scene* s, const lt_params* p, const lt_render_opts*
   cudaStream_t st = (cudaStream_t)stream;
   LT_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)s->dev.W * s->dev.H, st));
   if (o->n_paths == 0 && b->n_cam == 0) return LT_OK;
-  cudaError_t e = launch_bidir(dev_for(s, o->bvh_width), kparams(p, o), ba, false, image, nullptr, GradPtrs{},
+  cudaError_t e = launch_bidir(dev_for(s, o), kparams(p, o), ba, false, image, nullptr, GradPtrs{},
                                cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_bidir_primal: ") + cudaGetErrorString(e));
   return LT_OK;
@@ -816,10 +842,10 @@ lt_status lt_bidir_backward(lt_scene* s, const lt_params* p, const lt_render_opt
   if (v != LT_OK) return v;
   if (o->n_paths == 0 && b->n_cam == 0) return LT_OK;
   KParams kp = kparams(p, o);
-  set_privatization(s, g, kp);
+  set_privatization(s, g, kp, o->scatter);
   kp.n_h = 0;  // detached: no height gradients
   kp.priv_n = kp.n_alb;
-  cudaError_t e = launch_bidir(dev_for(s, o->bvh_width), kp, ba, true, nullptr, dI, gp, cfg_for(s, o), st);
+  cudaError_t e = launch_bidir(dev_for(s, o), kp, ba, true, nullptr, dI, gp, cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_bidir_backward: ") + cudaGetErrorString(e));
   return LT_OK;
 }
@@ -846,7 +872,7 @@ lt_status lt_mlp_collect(lt_scene* s, const lt_params* p, const lt_render_opts* 
   cudaStream_t st = (cudaStream_t)stream;
   LT_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), st));
   if (o->n_paths == 0) return LT_OK;
-  cudaError_t e = launch_collect(dev_for(s, o->bvh_width), kparams(p, o), dI, tfloor, feats, targets, cap, (unsigned long long*)count,
+  cudaError_t e = launch_collect(dev_for(s, o), kparams(p, o), dI, tfloor, feats, targets, cap, (unsigned long long*)count,
                                  cfg_for(s, o), st);
   if (e) return fail(LT_ERR_CUDA, std::string("lt_mlp_collect: ") + cudaGetErrorString(e));
   return LT_OK;

@@ -51,6 +51,9 @@ struct DevScene {
   const float4* wnode;
   int n_wnodes;
   int width;
+  // Global atomics of one call: 0 plain; 1 warp-aggregated for gradient arrays in global
+  // memory; 2 warp-aggregated for those and for the plain primal's splats (see agg_add).
+  int atomics;
 };
 
 // ------------------------------------------------------------------ small vector ops
@@ -114,6 +117,61 @@ __device__ __forceinline__ float3 cosine_dir(float3 n, float u0, float u1) {
 __device__ __forceinline__ void fnv(uint32_t& h, uint32_t x) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) { h ^= (x >> (8 * i)) & 0xffu; h *= 16777619u; }
+}
+
+// Add v at p, which points to shared or to global memory: a reduction without return value
+// in the pointer's own space.  Given a pointer that may be either, the compiler would issue a
+// generic atomic that returns the old value.
+__device__ __forceinline__ void red_add(float* p, float v) {
+  if (__isShared(p)) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+  } else {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+  }
+}
+
+// Atomic adds of N values at consecutive addresses p..p+N-1 with warp aggregation: the lanes
+// executing the call together that add at the same address first sum their values (a tree
+// over the peers in lane order: at step d the peer of rank r, r a multiple of 2d, adds the
+// partial sum of rank r + d), then the first of them issues the atomics.  When no two lanes
+// share an address (the common case for incoherent paths) each lane adds its own values.
+template <int N>
+__device__ __forceinline__ void agg_add(float* p, const float (&v)[N]) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, (unsigned long long)p);
+  const unsigned lane = threadIdx.x & 31;
+  float s[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) s[k] = v[k];
+  if (!__all_sync(act, peers == (1u << lane))) {
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned src = __fns(peers, lane, d + 1);  // the peer d ranks above, if any
+      const int from = src < 32u ? (int)src : (int)lane;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const float o = __shfl_sync(act, s[k], from);
+        if (src < 32u && (rank & (2 * d - 1)) == 0) s[k] += o;
+      }
+    }
+    if (rank != 0) return;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (s[k] != 0.0f) red_add(p + k, s[k]);
+}
+
+// Out-of-line forms for the gradient scatter (opts.scatter 3 only), so that the path
+// kernels' hot loops do not carry the aggregation code.
+static __device__ __noinline__ void agg_add1(float* p, float v) {
+  const float a[1] = {v};
+  agg_add<1>(p, a);
+}
+static __device__ __noinline__ void agg_add3(float* p, float x, float y, float z) {
+  const float a[3] = {x, y, z};
+  agg_add<3>(p, a);
 }
 
 // ------------------------------------------------------------------ primitives
@@ -682,7 +740,7 @@ __device__ __forceinline__ Taps taps(float ux, float uy) {
   return t;
 }
 
-__device__ __forceinline__ void splat(float* img, int W, int H, float ux, float uy, float3 L) {
+__device__ __forceinline__ void splat(float* img, int W, int H, float ux, float uy, float3 L, bool agg = false) {
   Taps t = taps(ux, uy);
   const float wx[2] = {1.0f - t.fx, t.fx}, wy[2] = {1.0f - t.fy, t.fy};
 #pragma unroll
@@ -695,9 +753,14 @@ __device__ __forceinline__ void splat(float* img, int W, int H, float ux, float 
       if (X < 0 || X >= W) continue;
       float w = wx[i] * wy[j];
       float* p = img + 3 * ((size_t)Y * W + X);
-      atomicAdd(p + 0, w * L.x);
-      atomicAdd(p + 1, w * L.y);
-      atomicAdd(p + 2, w * L.z);
+      if (agg) {
+        const float v[3] = {w * L.x, w * L.y, w * L.z};
+        agg_add<3>(p, v);
+      } else {
+        atomicAdd(p + 0, w * L.x);
+        atomicAdd(p + 1, w * L.y);
+        atomicAdd(p + 2, w * L.z);
+      }
     }
   }
 }
@@ -763,9 +826,10 @@ __device__ __forceinline__ Axis3 gauss_axis(float u, int extent) {
 }
 
 // Splat and adjoint read with the chosen filter (0 tent, 1 Gaussian).
-__device__ __forceinline__ void splat_f(float* img, int W, int H, float ux, float uy, float3 L, int filter) {
+__device__ __forceinline__ void splat_f(float* img, int W, int H, float ux, float uy, float3 L, int filter,
+                                        bool agg = false) {
   if (filter == 0) {
-    splat(img, W, H, ux, uy, L);
+    splat(img, W, H, ux, uy, L, agg);
     return;
   }
   const Axis3 ax = gauss_axis(ux, W), ay = gauss_axis(uy, H);

@@ -53,15 +53,11 @@ __global__ void k_update_tris(float4* prim, const int4* prim_h, const float4* tr
   prim[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, c.w);
 }
 
-// One warp per BVH node: the node's subtree covers the contiguous leaf-order primitive
-// range [range.x, range.y), so its bounds are a reduction over that range.
-__global__ void k_refit_nodes(float4* node, const int2* range, const float4* prim, int n_nodes) {
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= n_nodes) return;
-  int2 r = range[w];
-  float3 lo = f3(3e38f, 3e38f, 3e38f), hi = f3(-3e38f, -3e38f, -3e38f);
-  for (int k = r.x + lane; k < r.y; k += 32) {
+// Bounds of the primitives [r.x, r.y) that this thread visits with the given stride.
+__device__ __forceinline__ void range_bounds(const float4* prim, int2 r, int first, int stride, float3& lo, float3& hi) {
+  lo = f3(3e38f, 3e38f, 3e38f);
+  hi = f3(-3e38f, -3e38f, -3e38f);
+  for (int k = r.x + first; k < r.y; k += stride) {
     float3 o = xyz(prim[3 * k]), e1 = xyz(prim[3 * k + 1]), e2 = xyz(prim[3 * k + 2]);
     bool tri = __float_as_int(prim[3 * k + 2].w) != 0;
     float3 p[4] = {o, o + e1, o + e2, o + e1 + e2};
@@ -71,6 +67,8 @@ __global__ void k_refit_nodes(float4* node, const int2* range, const float4* pri
       hi = f3(fmaxf(hi.x, p[j].x), fmaxf(hi.y, p[j].y), fmaxf(hi.z, p[j].z));
     }
   }
+}
+__device__ __forceinline__ void warp_bounds(float3& lo, float3& hi) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, off));
@@ -80,14 +78,53 @@ __global__ void k_refit_nodes(float4* node, const int2* range, const float4* pri
     hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, off));
     hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, off));
   }
+}
+__device__ __forceinline__ void store_node(float4* node, int w, float3 lo, float3 hi) {
+  // conservative padding for FP32 rounding of the stored primitive edges
+  float3 pad = f3(1e-6f * fmaxf(1.0f, fmaxf(fabsf(lo.x), fabsf(hi.x))),
+                  1e-6f * fmaxf(1.0f, fmaxf(fabsf(lo.y), fabsf(hi.y))),
+                  1e-6f * fmaxf(1.0f, fmaxf(fabsf(lo.z), fabsf(hi.z))));
+  float4 a = node[2 * w], b = node[2 * w + 1];
+  node[2 * w] = make_float4(lo.x - pad.x, lo.y - pad.y, lo.z - pad.z, a.w);
+  node[2 * w + 1] = make_float4(hi.x + pad.x, hi.y + pad.y, hi.z + pad.z, b.w);
+}
+
+// One warp per BVH node: the node's subtree covers the contiguous leaf-order primitive
+// range [range.x, range.y), so its bounds are a reduction over that range.  Nodes with more
+// than kRefitBig primitives are left to k_refit_big.
+__global__ void k_refit_nodes(float4* node, const int2* range, const float4* prim, int n_nodes) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= n_nodes) return;
+  int2 r = range[w];
+  if (r.y - r.x > kRefitBig) return;
+  float3 lo, hi;
+  range_bounds(prim, r, lane, 32, lo, hi);
+  warp_bounds(lo, hi);
+  if (lane == 0) store_node(node, w, lo, hi);
+}
+
+// One block per node with more than kRefitBig primitives (the top of the tree), so the
+// root's reduction over every primitive is not left to a single warp.
+__global__ void __launch_bounds__(256) k_refit_big(float4* node, const int2* range, const int* big,
+                                                   const float4* prim) {
+  __shared__ float sh[6][8];
+  const int w = big[blockIdx.x];
+  float3 lo, hi;
+  range_bounds(prim, range[w], threadIdx.x, blockDim.x, lo, hi);
+  warp_bounds(lo, hi);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    // conservative padding for FP32 rounding of the stored primitive edges
-    float3 pad = f3(1e-6f * fmaxf(1.0f, fmaxf(fabsf(lo.x), fabsf(hi.x))),
-                    1e-6f * fmaxf(1.0f, fmaxf(fabsf(lo.y), fabsf(hi.y))),
-                    1e-6f * fmaxf(1.0f, fmaxf(fabsf(lo.z), fabsf(hi.z))));
-    float4 a = node[2 * w], b = node[2 * w + 1];
-    node[2 * w] = make_float4(lo.x - pad.x, lo.y - pad.y, lo.z - pad.z, a.w);
-    node[2 * w + 1] = make_float4(hi.x + pad.x, hi.y + pad.y, hi.z + pad.z, b.w);
+    sh[0][wid] = lo.x; sh[1][wid] = lo.y; sh[2][wid] = lo.z;
+    sh[3][wid] = hi.x; sh[4][wid] = hi.y; sh[5][wid] = hi.z;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      lo = f3(fminf(lo.x, sh[0][i]), fminf(lo.y, sh[1][i]), fminf(lo.z, sh[2][i]));
+      hi = f3(fmaxf(hi.x, sh[3][i]), fmaxf(hi.y, sh[4][i]), fmaxf(hi.z, sh[5][i]));
+    }
+    store_node(node, w, lo, hi);
   }
 }
 
@@ -277,15 +314,19 @@ __device__ __forceinline__ void sink_end(const KParams& kp, const GradPtrs& g, c
 
 // Albedo gradient at one diffuse vertex: weight (per channel) / rho times the bilinear
 // texel weights (d rho / d texel).
-__device__ __forceinline__ void scatter_albedo(float* g, const TexFoot& f, float3 wt, float3 rho) {
+__device__ __forceinline__ void scatter_albedo(const DevScene& S, float* g, const TexFoot& f, float3 wt, float3 rho) {
   if (!g) return;
   float3 a = f3(wt.x / rho.x, wt.y / rho.y, wt.z / rho.z);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (f.w[k] == 0.0f) continue;
-    atomicAdd(g + f.idx[k] + 0, a.x * f.w[k]);
-    atomicAdd(g + f.idx[k] + 1, a.y * f.w[k]);
-    atomicAdd(g + f.idx[k] + 2, a.z * f.w[k]);
+    if (S.atomics) {  // lanes adding to the same texel sum first
+      agg_add3(g + f.idx[k], a.x * f.w[k], a.y * f.w[k], a.z * f.w[k]);
+      continue;
+    }
+    red_add(g + f.idx[k] + 0, a.x * f.w[k]);
+    red_add(g + f.idx[k] + 1, a.y * f.w[k]);
+    red_add(g + f.idx[k] + 2, a.z * f.w[k]);
   }
 }
 
@@ -327,9 +368,16 @@ __device__ __forceinline__ void scatter_heights(const DevScene& S, float* dh, in
   float a1 = gn.x * e2.z - gn.z * e2.x;
   float a2 = gn.z * e1.x - gn.x * e1.z;
   float h0 = (1.0f - b1 - b2) * gx.y - a1 - a2, h1 = b1 * gx.y + a1, h2 = b2 * gx.y + a2;
-  if (ph.x >= 0) atomicAdd(dh + ph.x, h0);
-  if (ph.y >= 0) atomicAdd(dh + ph.y, h1);
-  if (ph.z >= 0) atomicAdd(dh + ph.z, h2);
+  if (S.atomics) {
+    // lanes adding to the same height sum first
+    if (ph.x >= 0) agg_add1(dh + ph.x, h0);
+    if (ph.y >= 0) agg_add1(dh + ph.y, h1);
+    if (ph.z >= 0) agg_add1(dh + ph.z, h2);
+    return;
+  }
+  if (ph.x >= 0) red_add(dh + ph.x, h0);
+  if (ph.y >= 0) red_add(dh + ph.y, h1);
+  if (ph.z >= 0) red_add(dh + ph.z, h2);
 }
 
 // ------------------------------------------------------------ specular chains (attached)
@@ -773,8 +821,9 @@ __global__ void __launch_bounds__(128) k_collect(DevScene S, KParams kp, const f
 // lanes call take() together at the top of the step loop).
 struct Dispenser {
   int64_t next, end;
-  int64_t stride = 0;  // interleaved mode: distance between a warp's 32-entry blocks
-  bool strided = false;
+  int64_t stride = 0;                    // dynamic mode: the range's end
+  unsigned long long* ticket = nullptr;  // dynamic mode: shared counter of entries taken
+  bool exhausted = false;
   __device__ __forceinline__ void init(int64_t n_paths) {
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -782,16 +831,13 @@ struct Dispenser {
     next = min(wid * per, n_paths);
     end = min(next + per, n_paths);
   }
-  // Interleaved over the grid's warps: a warp takes 32 consecutive entries, then the 32
-  // entries one grid stride further (for a list whose order follows the time its entries
-  // were found, so that no warp receives only the entries of one stretch of it).
-  __device__ __forceinline__ void init_strided(int64_t n_paths) {
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    next = wid * 32;
-    end = n_paths;
-    stride = warps * 32;
-    strided = true;
+  // Dynamic: a warp takes 32 consecutive entries at a time from a counter shared by the
+  // grid (one atomic per 32 entries), so that the warps end together whatever work their
+  // entries hold (no warp waits at the block's final barrier for a slower one).
+  __device__ __forceinline__ void init_dynamic(int64_t n_paths, unsigned long long* t) {
+    next = end = 0;
+    stride = n_paths;  // the range's end
+    ticket = t;
   }
   // The block alone works on [0, n_paths): contiguous ranges of its warps.
   __device__ __forceinline__ void init_local(int64_t n_paths) {
@@ -806,18 +852,30 @@ struct Dispenser {
     const unsigned m = __ballot_sync(0xffffffffu, want);
     const unsigned lane = threadIdx.x & 31;
     int64_t mine = -1;
-    if (strided) {
-      // `next` is the warp's next entry; its block [next & ~31, +32) continues one grid
-      // stride further once used up (a request of at most 32 spans at most two blocks)
-      const int64_t blk = next & ~(int64_t)31;
-      const int used = (int)(next - blk);
-      if (want) {
-        const int pos = used + __popc(m & ((1u << lane) - 1u));
-        const int64_t cand = pos < 32 ? blk + pos : blk + stride + (pos - 32);
-        mine = cand < end ? cand : -1;
+    if (ticket) {
+      // serve the wanting lanes from the current 32-entry chunk [next, end), taking the next
+      // chunk when it is used up; every round serves a lane or takes a chunk, so it ends
+      unsigned rest = m;
+      while (rest != 0u && !exhausted) {
+        if (next >= end) {
+          unsigned long long t = 0;
+          if (lane == 0) t = atomicAdd(ticket, 32ull);
+          t = __shfl_sync(0xffffffffu, t, 0);
+          if ((int64_t)t >= stride) {
+            exhausted = true;
+            break;
+          }
+          next = (int64_t)t;
+          end = min(next + 32, stride);
+        }
+        const bool in = (rest >> lane) & 1u;
+        const int rank = __popc(rest & ((1u << lane) - 1u));
+        const int avail = (int)(end - next);
+        const int k = __popc(rest) < avail ? __popc(rest) : avail;
+        if (in && rank < k) mine = next + rank;
+        next += k;
+        rest = __ballot_sync(0xffffffffu, in && rank >= k);
       }
-      const int u2 = used + __popc(m);
-      next = u2 < 32 ? blk + u2 : blk + stride + (u2 - 32);
       return mine;
     }
     if (want) {
@@ -895,8 +953,8 @@ __device__ __forceinline__ void add3(float* d, float3 v) {
 // belongs to (BatchDispenser); S0, kp0, image0 and aux0 are not used.
 // LEARN compiles the learned reservoir target (ResLRB only); plain ResLRB does not carry its
 // registers.  ST compiles the work census (rays, box and primitive tests, vertices,
-// connections) of a counting variant.
-template <int EST, bool BATCH, bool LEARN = false, bool ST = false>
+// connections) of a counting variant.  AGG compiles warp-aggregated splat atomics.
+template <int EST, bool BATCH, bool LEARN = false, bool ST = false, bool AGG = false>
 __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& kp0, float* __restrict__ image0,
                                             void* aux0, const BatchArgs& ba) {
   // learned reservoir target: network image, one 32x16 feature tile per warp, and two
@@ -1102,7 +1160,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
               if (r.w < om / Om) { R = k; wR = om; LR = L; Rux = c.ux; Ruy = c.uy; }
             }
           } else {
-            splat_f(image, S.W, S.H, c.ux, c.uy, L, kp.filter);
+            splat_f(image, S.W, S.H, c.ux, c.uy, L, kp.filter, AGG);
           }
         }
       }
@@ -1139,6 +1197,10 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
 template <int EST>
 __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
   primal_body<EST, false>(S, kp, image, aux, BatchArgs{});
+}
+// Plain primal with warp-aggregated splat atomics (opts.scatter 3)
+__global__ void __launch_bounds__(128) k_primal_agg(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
+  primal_body<0, false, false, false, true>(S, kp, image, aux, BatchArgs{});
 }
 // Counting variant of the plain primal (work census for the roofline; not for timed runs)
 __global__ void __launch_bounds__(128) k_primal_census(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
@@ -1195,7 +1257,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   const uint32_t* list = (!BATCH && !LOCAL && (MODE == 2 || (MODE == 1 && MK))) ? kp0.list : nullptr;
   if (BATCH) bdisp.init();
   else if (LOCAL) disp.init_local(kp0.n_paths);
-  else if (list) disp.init_strided(min((int64_t)*kp0.list_n, kp0.n_paths));
+  else if (list) disp.init_dynamic(min((int64_t)*kp0.list_n, kp0.n_paths), kp0.ticket + (MODE == 1 ? 0 : 1));
   else disp.init(kp0.n_paths);
   int jb = 0;
   enum { IDLE = 0, PASS2 = 1, PASS3 = 2 };
@@ -1396,7 +1458,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
             rem = rem - P;        // Eq. 16
             if (att) conn_adjoint(S, v.x, v.nraw, hsum(P), q, pv.gx, pv.gn);
           }
-          scatter_albedo(g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor rho_k (Eq. 17)
+          scatter_albedo(S, g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor rho_k (Eq. 17)
           if (att && CH && !v.attached)
             pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
         }
@@ -1609,7 +1671,7 @@ __device__ __forceinline__ void reslrb_body(const DevScene& S0, const KParams& k
       ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
       TexFoot foot;
       rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
-      scatter_albedo(g.d_albedo, foot, P, rho);  // scattering factor (k < R) or splat factor (k = R)
+      scatter_albedo(S, g.d_albedo, foot, P, rho);  // scattering factor (k < R) or splat factor (k = R)
       if (att) {
         if (k == R) conn_adjoint(S, v.x, v.nraw, lam, q, pv.gx, pv.gn);
         if (CH && !v.attached) pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, P, rho);
@@ -1728,7 +1790,7 @@ __global__ void __launch_bounds__(128) k_naive(DevScene S, KParams kp, const flo
           float3 Lb = adjoint_read_f(dI, S.W, S.H, t0.w, t1.w, L, ATT ? &q : nullptr, kp.filter);
           P3 = mul(Lb, L);
         }
-        scatter_albedo(g.d_albedo, foot, P3 + acc, rho);
+        scatter_albedo(S, g.d_albedo, foot, P3 + acc, rho);
       }
       if (ATT) {
         float3 x = P.o + P.e1 * t0.y + P.e2 * t0.z, nr = cross(P.e1, P.e2);
@@ -1875,7 +1937,7 @@ __global__ void __launch_bounds__(128) k_bidir_light(DevScene S, KParams kp, Bid
           wsplat = mul(adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, nullptr, kp.filter), L);  // Eq. 15
           rem = rem - wsplat;                                                                  // Eq. 16
         }
-        scatter_albedo(g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor with delta_rem (Eq. 17)
+        scatter_albedo(S, g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor with delta_rem (Eq. 17)
       }
       walk_scatter(S, w, v, ns, rho, r);
     }
@@ -1995,7 +2057,7 @@ __global__ void __launch_bounds__(128) k_bidir_cam(DevScene S, KParams kp, Bidir
         set_err(S, ERR_BOUNDS);  // the replay must reach the last connection
         break;
       }
-      scatter_albedo(g.d_albedo, foot, mul(Lb, rem), rho);  // every contribution from this vertex on
+      scatter_albedo(S, g.d_albedo, foot, mul(Lb, rem), rho);  // every contribution from this vertex on
       rem = rem - contrib;
     }
   }
@@ -2035,6 +2097,7 @@ __global__ void k_film_l2(const float* __restrict__ I, const float* __restrict__
 template <typename... P, typename... A>
 static void launch_paths(void (*kern)(P...), const LaunchCfg& L, int64_t work, size_t smem, cudaStream_t st,
                          A&&... args) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = L.blocks_per_sm, occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, L.block, smem) == cudaSuccess && occ > 0 &&
       occ < per_sm)
@@ -2053,6 +2116,7 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
   if (a.n_nodes > 0) {
     int threads = a.n_nodes * 32;
     k_refit_nodes<<<(threads + 255) / 256, 256, 0, st>>>(a.node, a.range, a.prim, a.n_nodes);
+    if (a.n_big > 0) k_refit_big<<<a.n_big, 256, 0, st>>>(a.node, a.range, a.big, a.prim);
   }
   if (a.n_wnodes[0] > 0) {
     const int t = a.n_wnodes[0] * 4;
@@ -2074,6 +2138,7 @@ cudaError_t launch_primal(const DevScene& S, const KParams& kp, int est, float* 
   switch (est) {
     case 0:
       if (kp.census) launch_paths(k_primal_census, L, kp.n_paths, 0, st, S, kp, image, aux);
+      else if (S.atomics == 2) launch_paths(k_primal_agg, L, kp.n_paths, 0, st, S, kp, image, aux);
       else launch_paths(k_primal<0>, L, kp.n_paths, 0, st, S, kp, image, aux);
       break;
     case 1:

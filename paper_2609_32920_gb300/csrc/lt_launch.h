@@ -33,6 +33,7 @@ struct KParams {
   uint32_t* list;              // paths with a valid connection (plain primal: appends;
                                // LRB-3 passes 2 and 3 with known masks: visit only these) or null
   unsigned long long* list_n;  // length of `list`
+  unsigned long long* ticket;  // zeroed counters of list entries taken, [0] pass 2, [1] pass 3
 };
 
 struct GradPtrs {
@@ -56,11 +57,17 @@ struct RefitArgs {
   float4* node;
   const int2* range;
   int n_nodes;
+  const int* big;  // nodes whose primitive range exceeds kRefitBig: a whole block reduces each
+  int n_big;
   // wide BVHs (width 4 and 8): child slot -> binary node whose box it takes (-1: empty)
   float4* wnode[2];
   const int* wmap[2];
   int n_wnodes[2];
 };
+
+// Binary BVH nodes with more primitives than this are refitted by a block each, the rest
+// by a warp each.
+constexpr int kRefitBig = 1024;
 
 struct BatchArgs;
 
@@ -113,6 +120,8 @@ __host__ __device__ inline size_t lrb3_state_core(int64_t n) { return lrb3_state
 __host__ __device__ inline size_t lrb3_state_list(int64_t n) { return lrb3_state_core(n); }
 __host__ __device__ inline size_t lrb3_state_count(int64_t n) { return lrb3_state_list(n) + align256((size_t)n * 4); }
 __host__ __device__ inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_count(n) + 256; }
+// After the list's length (uint64) at lrb3_state_count: the two passes' counters of list
+// entries taken (uint64 each).
 // The path list is used for calls of at most this many paths (uint32 indices).
 constexpr int64_t kListMaxPaths = 0xffffffffll;
 

@@ -264,26 +264,20 @@ def gaussian_bumps(n: int, extent: float, seed: int, n_gauss: int = 8, amp_std: 
     return h.reshape(-1)
 
 
-def slab_scene(res: int = 512, n: int = 128, seed: int = 0, Le_scale: float = 1.0,
-               light_size: float = 0.05, ior: float = 1.5, flat: bool = False) -> Scene:
-    """Caustic workload: 2x2 m diffuse receiver (albedo 0.7) at y=0, a 1x1 m dielectric slab
-    with flat bottom at y=0.5 and an n x n heightmap top at y=0.6 (sum of Gaussians), sides
-    closed by strips that follow the boundary heights, small light at y=2.0 facing -y."""
-    b = _Builder()
-    rm = b.diffuse(np.full((1, 1, 3), 0.7))
-    b.quad(np.array([-1.0, 0, -1.0]), np.array([0, 0, 2.0]), np.array([2.0, 0, 0]), rm)  # +y
-    em = b.emitter()
-    ls = light_size
-    b.emitter_quad = b.quad(np.array([-ls / 2, 2.0, -ls / 2]), np.array([ls, 0, 0.0]),
-                            np.array([0, 0, ls]), em)  # -y
+def _slab(b: _Builder, n: int, x0: float, z0: float, size: float, y_bottom: float, y_top: float, ior: float):
+    """A dielectric slab over [x0, x0+size] x [z0, z0+size]: an n x n height-field top at
+    y_top, a flat bottom at y_bottom, and side strips that follow the top's boundary
+    heights (bottom edge fixed)."""
     gm = b.dielectric(ior)
-    top = b.heightmap(n, n, -0.5, -0.5, 1.0, 1.0, 0.6, gm)
+    top = b.heightmap(n, n, x0, z0, size, size, y_top, gm)
     # bottom face (normal -y): two triangles on fixed vertices
-    c = [b.vertex((-0.5, 0.5, -0.5)), b.vertex((0.5, 0.5, -0.5)),
-         b.vertex((0.5, 0.5, 0.5)), b.vertex((-0.5, 0.5, 0.5))]
+    x1, z1 = x0 + size, z0 + size
+    c = [b.vertex((x0, y_bottom, z0)), b.vertex((x1, y_bottom, z0)),
+         b.vertex((x1, y_bottom, z1)), b.vertex((x0, y_bottom, z1))]
     b.tri(c[0], c[1], c[2], gm)
     b.tri(c[0], c[2], c[3], gm)
-    # side strips: bottom edge fixed at y=0.5, top edge = heightmap boundary vertices
+    # side strips: bottom edge fixed at y_bottom, top edge = heightmap boundary vertices
+
     def strip(top_line, bot_a, bot_b, outward):
         # top_line: vertex indices along the edge; bottom edge interpolated with fixed verts
         k = len(top_line)
@@ -300,15 +294,45 @@ def slab_scene(res: int = 512, n: int = 128, seed: int = 0, Le_scale: float = 1.
             else:
                 b.tri(b0, t1, b1, gm)
                 b.tri(b0, t0, t1, gm)
-    strip(list(top[0, :]), c[0], c[1], np.array([0, 0, -1.0]))      # z=-0.5
-    strip(list(top[n - 1, :]), c[3], c[2], np.array([0, 0, 1.0]))   # z=+0.5
-    strip(list(top[:, 0]), c[0], c[3], np.array([-1.0, 0, 0]))      # x=-0.5
-    strip(list(top[:, n - 1]), c[1], c[2], np.array([1.0, 0, 0]))   # x=+0.5
+    strip(list(top[0, :]), c[0], c[1], np.array([0, 0, -1.0]))      # z = z0
+    strip(list(top[n - 1, :]), c[3], c[2], np.array([0, 0, 1.0]))   # z = z0 + size
+    strip(list(top[:, 0]), c[0], c[3], np.array([-1.0, 0, 0]))      # x = x0
+    strip(list(top[:, n - 1]), c[1], c[2], np.array([1.0, 0, 0]))   # x = x0 + size
+
+
+def slab_scene(res: int = 512, n: int = 128, seed: int = 0, Le_scale: float = 1.0,
+               light_size: float = 0.05, ior: float = 1.5, flat: bool = False) -> Scene:
+    """Caustic workload: 2x2 m diffuse receiver (albedo 0.7) at y=0, a 1x1 m dielectric slab
+    with flat bottom at y=0.5 and an n x n heightmap top at y=0.6 (sum of Gaussians), sides
+    closed by strips that follow the boundary heights, small light at y=2.0 facing -y."""
+    b = _Builder()
+    rm = b.diffuse(np.full((1, 1, 3), 0.7))
+    b.quad(np.array([-1.0, 0, -1.0]), np.array([0, 0, 2.0]), np.array([2.0, 0, 0]), rm)  # +y
+    em = b.emitter()
+    ls = light_size
+    b.emitter_quad = b.quad(np.array([-ls / 2, 2.0, -ls / 2]), np.array([ls, 0, 0.0]),
+                            np.array([0, 0, ls]), em)  # -y
+    _slab(b, n, -0.5, -0.5, 1.0, 0.5, 0.6, ior)
     heights = np.zeros(n * n) if flat else gaussian_bumps(n, 1.0, seed)
     # Le chosen so that the mean receiver pixel is O(1) for the default camera
     Le = np.full(3, 2000.0 * Le_scale)
     return b.build((0.0, 1.2, -1.6), (0.0, 0.0, 0.0), (0, 1, 0), 45.0, res, res, Le, heights,
                    f"slab{res}_hm{n}", meta={"kind": "slab", "heightmap": n})
+
+
+def slab_in_box(res: int = 256, n: int = 64, seed: int = 0, tex_seed: int = 0, ior: float = 1.5) -> Scene:
+    """The caustic slab inside the textured box (high path-sensor connectivity with
+    refraction): the open box of box_scene with its emitter, and a 0.5 x 0.5 m dielectric
+    slab over x, z in [0.25, 0.75], flat bottom at y=0.2, n x n height-field top at y=0.3
+    (sum of Gaussians, amplitudes N(0, 0.005) m)."""
+    b = _Builder()
+    tex = _torch_uniform((5, 16, 16, 3), 0.2, 0.8, tex_seed)
+    _box_walls(b, list(tex))
+    _box_light(b)
+    _slab(b, n, 0.25, 0.25, 0.5, 0.2, 0.3, ior)
+    heights = gaussian_bumps(n, 0.5, seed, amp_std=0.005)
+    return b.build((0.5, 0.5, -1.4), (0.5, 0.5, 0.0), (0, 1, 0), 40.0, res, res, (8.0, 8.0, 8.0), heights,
+                   f"slabbox{res}_hm{n}", meta={"kind": "slab_in_box", "heightmap": n})
 
 
 def plane_under_light(res: int = 32, albedo: float = 0.5, light_size: float = 0.5, light_h: float = 1.0,

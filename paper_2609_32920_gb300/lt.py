@@ -54,7 +54,8 @@ class lt_render_opts(C.Structure):
                 ("block_size", C.c_int), ("blocks_per_sm", C.c_int), ("path_mask", C.c_void_p),
                 ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p), ("census", C.c_void_p),
                 ("lrb3_state", C.c_void_p), ("lrb3_state_bytes", C.c_size_t), ("lrb3_mask_ready", C.c_int),
-                ("rr_depth", C.c_int), ("rr_prob", C.c_float), ("filter", C.c_int), ("bvh_width", C.c_int)]
+                ("rr_depth", C.c_int), ("rr_prob", C.c_float), ("filter", C.c_int), ("bvh_width", C.c_int),
+                ("scatter", C.c_int)]
 
 
 class lt_grads(C.Structure):
@@ -228,7 +229,8 @@ class Scene:
     @staticmethod
     def opts(seed=0, n_paths=1 << 14, max_depth=4, attached=0, path_offset=0, n_norm=0, block_size=0,
              blocks_per_sm=0, mask=None, hash_out=None, dbg_out=None, target=TARGET_LUMINANCE, mlp=None,
-             census=None, lrb3_state=None, lrb3_mask_ready=0, bvh_width=0, rr_depth=0, rr_prob=1.0, filter=0):
+             census=None, lrb3_state=None, lrb3_mask_ready=0, bvh_width=0, rr_depth=0, rr_prob=1.0, filter=0,
+             scatter=0):
         """Render options.  `lrb3_state`: a device buffer of lrb3_state_bytes(opts) bytes
         selects the two-kernel form of lt_backward_lrb3, and a plain primal given it stores
         the paths' connection-validity masks there; `lrb3_mask_ready=1` lets the backward
@@ -243,6 +245,7 @@ class Scene:
         o.path_dbg = None if dbg_out is None else dbg_out.data_ptr()
         o.census = None if census is None else census.data_ptr()
         o.bvh_width = int(bvh_width)
+        o.scatter = int(scatter)
         o.rr_depth, o.rr_prob, o.filter = int(rr_depth), float(rr_prob), int(filter)
         o.lrb3_mask_ready = int(lrb3_mask_ready)
         o.lrb3_state = None if lrb3_state is None else lrb3_state.data_ptr()

@@ -629,3 +629,37 @@ def test_reslrb_matches_naive_in_expectation_over_256_seeds(boxhm, attached):
     assert np.mean(np.abs(z) <= 3.0) >= 0.99, np.sort(np.abs(z))[-5:]
     assert 0.7 < np.mean(z * z) < 1.4, np.mean(z * z)
     assert np.all(np.abs(zp) < 3.0), zp
+
+
+@pytest.mark.parametrize("which", ["slab128", "boxhm"])
+def test_scatter_modes_agree(which):
+    """Every way of bringing gradients and splats to memory (opts.scatter: per-block
+    shared-memory arrays within 46 KB or within the opt-in limit, plain global atomics,
+    warp-aggregated global atomics for gradients and splats) gives the same image and
+    gradients up to the order of float additions; the 128x128 height field (64 KB) goes
+    to global memory by default and to shared memory under the opt-in limit."""
+    sc = I.slab_scene(96, n=128, seed=0) if which == "slab128" else I.box_scene(64, heightmap=8, hm_std=0.03)
+    S = lt.Scene(sc)
+    n, D, seed = 1 << 16, 6, 3
+    dI = t32(I.smooth_adjoint(sc.W, sc.H, 77))
+    out = {}
+    for mode in (0, 1, 2, 3):
+        state = S.new_lrb3_state(n)
+        op = S.opts(seed=seed, n_paths=n, max_depth=D, lrb3_state=state, scatter=mode)
+        img = S.primal(op).cpu().numpy()
+        om = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, lrb3_state=state, lrb3_mask_ready=1,
+                    scatter=mode)
+        g = [x.cpu().numpy() for x in S.backward_lrb3(om, dI)]
+        rec = torch.zeros((n, 8), device="cuda")
+        o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=1, scatter=mode)
+        S.primal(o, estimator=lt.EST_RESLRB, aux=rec)
+        gr = [x.cpu().numpy() for x in S.backward_reslrb(o, dI, rec)]
+        out[mode] = (img, g, gr)
+    S.sync_status()
+    ref = out[2]
+    assert np.abs(ref[1][2]).sum() > 0
+    for mode in (0, 1, 3):
+        img, g, gr = out[mode]
+        assert rel_l2(img, ref[0]) < 1e-6, mode
+        for a, b in zip(g + gr, ref[1] + ref[2]):
+            assert rel_l2(a, b) < 1e-5, mode
