@@ -454,6 +454,7 @@ def run_ours(args):
         studies[other] = workload_study(other, dev, flush, barrier, args.steps)
     if not args.no_sweep:
         studies["scatter"] = scatter_study(step, flush)
+        studies["literal_transport"] = literal_study(step, flush)
         studies["methods"], studies["memory_vs_depth"] = method_sweep(step, dev, flush)
         if rank == 0:
             box = Step("box256_hm32", dev)
@@ -538,6 +539,41 @@ def scatter_study(step, flush, reps=3):
                 b_ms.append(e[1].elapsed_time(e[2]))
         out[str(mode)] = {"mode": names[mode], "primal_ms": statistics.median(p_ms),
                           "backward_ms": statistics.median(b_ms)}
+    S.sync_status()
+    return out
+
+
+def literal_study(step, flush, reps=3):
+    """The paper-literal attached transport (opts.literal; determinant-guarded inverse, with
+    and without Jacobian noise) against the exact chain transport on the workload: time of
+    one LRB-3 backward and the relative L2 distance of its height gradient from the exact
+    one at the same seed."""
+    import torch
+    S, st = step.S, step.stream
+    kw = dict(seed=1, n_paths=step.n, max_depth=step.depth, attached=1)
+    out = {"workload": f"{step.name}, 2^{step.n.bit_length() - 1} paths, depth {step.depth}, attached"}
+    variants = (("exact (two kernels, path list)", dict(lrb3_state=step.state, lrb3_mask_ready=1)),
+                ("exact (fused)", {}), ("literal, guard only", dict(literal=1)),
+                ("literal, Jacobian noise", dict(literal=1, jac_noise=1, noise_seed=3)))
+    ref = None
+    for name, extra in variants:
+        o = S.opts(**kw, **extra)
+        ms = []
+        for r in range(reps + 1):
+            flush.fill_(r)
+            S.primal(S.opts(seed=1, n_paths=step.n, max_depth=step.depth, lrb3_state=step.state), image=step.img)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            g = S.backward_lrb3(o, step.dI)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if r:
+                ms.append(e0.elapsed_time(e1))
+        gh = g[2].double()
+        if ref is None:
+            ref = gh
+        out[name] = {"backward_ms": statistics.median(ms),
+                     "height_rel_l2_to_exact": float(torch.linalg.norm(gh - ref) / torch.linalg.norm(ref))}
     S.sync_status()
     return out
 

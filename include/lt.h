@@ -158,6 +158,27 @@ typedef struct {
                            3 no per-block arrays, warp-aggregated global atomics (lanes of
                              a warp adding to the same element sum first) for the
                              gradients and for the plain primal's splats.           */
+  int literal;          /* lt_backward_lrb3, attached: 0 exact transport of the splat-
+                           position adjoint along specular chains (default); 1 the
+                           paper's transport (Sec. 3.3, Eq. 4-7, Eq. 18-19, Sec. 5):
+                           forward-accumulated 4x4 Jacobians of the two-point segment
+                           parameterisation (v_{k-1}, v_k) of surface coordinates, the
+                           position rows of each connection summed as A_pos in pass 2 and
+                           projected back in pass 3 with the inverse of the accumulated
+                           Jacobian, zero when it is singular by construction (a zero
+                           block entered it) or |det| < det_eps times the product of
+                           its row norms (Hadamard's bound).  After a diffuse vertex
+                           the next vertex keeps its surface coordinates, so that
+                           Jacobian is singular and chains starting there lose their
+                           position transport (biased) unless jac_noise is set.  Runs
+                           one fused kernel, one path per thread; the radiance terms are
+                           those of the exact form                                */
+  int jac_noise;        /* with literal: zero-mean noise eps [I 0], eps = +-1 (Philox
+                           stream 4 at that depth, keyed by noise_seed), in the zero
+                           block of the Jacobian at diffuse vertices: unbiased over the
+                           noise                                                  */
+  uint64_t noise_seed;  /* Philox key of that noise                                 */
+  float det_eps;        /* with literal: relative determinant guard; 0 = 1e-6      */
 } lt_render_opts;
 
 /* Gradient outputs (DEVICE, FP32, caller-owned).  NULL skips a parameter group.

@@ -42,6 +42,7 @@
 // or refracted ray (they slide).  Dielectric branch weights are F/F0 and (1-F)/(1-F0).
 // Detached mode treats the geometry as constant.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -578,9 +579,13 @@ template <class T> struct ConnOut {
 // beta_0 = Le A_light pi (cosine emission from a uniformly sampled point); a diffuse
 // vertex connects with f_s = rho/pi and importance  W H / (N A_img r^2 cos^3 theta_c)
 // (pinhole, image plane at distance 1), then scatters with weight rho.
+// lit_u: the film position of a connection at a sliding vertex is taken at the vertex's
+// surface coordinates frozen at theta0 on its (moving) primitive, instead of at the
+// position the specular chain delivers: the split used by the paper-literal attached
+// variant (or_gradient_literal), whose chain transport of the film position is separate.
 template <class T, class AA, class AL, class AH>
 void eval_path(const Scene& sc, const Path& P, const AA& albedo, const AL& Le, const AH& hts, double N,
-               std::vector<ConnOut<T>>& out, Path* fill = nullptr) {
+               std::vector<ConnOut<T>>& out, Path* fill = nullptr, bool lit_u = false) {
   // `fill`: evaluation at the decision parameters theta0; records the frozen denominators
   // (g0, F0) of the weight ratios so later evaluations at other parameters reuse them.
   out.clear();
@@ -635,6 +640,10 @@ void eval_path(const Scene& sc, const Path& P, const AA& albedo, const AL& Le, c
         co.vi = (int)k;
         T zc, dd;
         project<T>(sc, x, co.ux, co.uy, zc, dd);
+        if (lit_u && !v.attached) {
+          T zl, dl;
+          project<T>(sc, o + e1 * T(val(s)) + e2 * T(val(t)), co.ux, co.uy, zl, dl);
+        }
         T cc = zc / dist;
         T geo = cosc * T(K) / (dist2 * cc * cc * cc);
         for (int c = 0; c < 3; ++c) co.L[c] = beta[c] * rho[c] * geo;
@@ -856,6 +865,99 @@ double light_weight(const Scene& sc, const ConnOut<double>& c, double N, double 
   if (M <= 0) return 1.0;
   const double pfilm = c.geo * N * PI / ((double)sc.s->W * (double)sc.s->H);
   return N / (N + M * (pfilm / c.pf0));
+}
+
+// ---------------------------------------------------------------- paper-literal attached LRB-3
+// The paper's attached formulation (Sec. 3.3, Eq. 4-7; Sec. 4.3.2, Eq. 18-19; Sec. 5) moves
+// the splat-position adjoint along the path with forward-accumulated Jacobians of the
+// two-point segment parameterisation p_j = (v_{j-1}, v_j) (v: surface coordinates, the
+// emitter's (s, t) for j = 1): J_j = d p_{j+1} / d p_j (4x4), J_{1->j} = J_{j-1} ... J_1,
+// A_pos = sum_i (0, 0, dL/du_i du_i/dv_i) J_{1->i} (Eq. 18, the position rows of the
+// sensor Jacobian), and at vertex j the remainder projected back with the inverse,
+// A_loc(j) = A_rem(j) J_{1->j}^{-1} (Eq. 19), replaced by zero when |det| falls below a
+// threshold (Sec. 5) times the product of the row norms, or when a zero block has entered
+// the product (singular by construction).  In this model a vertex that follows a diffuse vertex keeps its
+// surface coordinates, so the lower block of J at a diffuse vertex is zero and J_{1->j}
+// is singular after the first diffuse vertex: the guard then drops the transport along
+// later (second-generation) specular chains.  Optional zero-mean noise (Sec. 5): at a
+// diffuse vertex the lower block becomes eps sigma [I 0] with eps = +-1 from Philox stream 4
+// at that depth (keyed by a noise seed of its own); the transport is linear in each noise
+// factor, so it is unbiased over the noise.  The parameters enter the transport where a specular vertex maps p_j to p_{j+1}
+// (K_j: the explicit dependence of v_{j+1} on the heights at fixed v_{j-1}, v_j), weighted
+// by the position rows of A_loc(j+1).  Everything else (the radiance factors, each
+// connection's film position at its own frozen surface coordinates) is the naive-AD
+// gradient of the frozen path function with that split (eval_path's lit_u).
+
+// Surface coordinates of the sliding vertex that follows specular vertex x_j (on prim j
+// at v_j, reached from x_{j-1} on prim jp, or the emitter for jp = -1, at v_{j-1}) along the
+// reflected (refl) or refracted direction, on prim jn's plane.
+template <class T, class AH>
+void spec_next(const Scene& sc, const AH& hts, int jp, const T vp[2], int j, const T vj[2], bool refl, int jn,
+               T out[2]) {
+  Vec<T> op, e1p, e2p;
+  if (jp < 0) prim_geom<T>(sc, sc.s->emitter_quad, ConstV{sc.p->heights}, op, e1p, e2p);
+  else prim_geom<T>(sc, jp, hts, op, e1p, e2p);
+  Vec<T> o, e1, e2;
+  prim_geom<T>(sc, j, hts, o, e1, e2);
+  const Vec<T> xp = op + e1p * vp[0] + e2p * vp[1], xj = o + e1 * vj[0] + e2 * vj[1];
+  const Vec<T> din = normalize(xj - xp);
+  const Vec<T> n = normalize(cross(e1, e2));
+  bool ent, tir;
+  T F;
+  Vec<T> rl, rf;
+  dielectric<T>(din, n, sc.s->mat_ior[sc.mat(j)], ent, tir, F, rl, rf);
+  const Vec<T> dout = refl ? rl : rf;
+  Vec<T> on, e1n, e2n;
+  prim_geom<T>(sc, jn, hts, on, e1n, e2n);
+  const Vec<T> m = cross(e1n, e2n);
+  const T tau = dot(on - xj, m) / dot(dout, m);
+  const Vec<T> q = xj + dout * tau - on;
+  const T nn = dot(m, m);
+  out[0] = dot(cross(q, e2n), m) / nn;
+  out[1] = dot(cross(e1n, q), m) / nn;
+}
+
+typedef double M4[4][4];
+void m4_mul(const M4 a, const M4 b, M4 c) {  // c = a b
+  M4 r;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      r[i][j] = 0;
+      for (int k = 0; k < 4; ++k) r[i][j] += a[i][k] * b[k][j];
+    }
+  std::memcpy(c, r, sizeof(M4));
+}
+// Inverse by Gauss-Jordan elimination with partial pivoting; false when |det| < eps times
+// the product of the row norms (Hadamard's bound on |det|: a scale-free test of singularity).
+bool m4_inv(const M4 a, M4 inv, double eps) {
+  double bound = 1.0;
+  for (int i = 0; i < 4; ++i)
+    bound *= std::sqrt(a[i][0] * a[i][0] + a[i][1] * a[i][1] + a[i][2] * a[i][2] + a[i][3] * a[i][3]);
+  if (!(bound > 0.0)) return false;
+  double m[4][8];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 8; ++j) m[i][j] = j < 4 ? a[i][j] : (j - 4 == i ? 1.0 : 0.0);
+  double det = 1.0;
+  for (int c = 0; c < 4; ++c) {
+    int pr = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (std::fabs(m[r][c]) > std::fabs(m[pr][c])) pr = r;
+    if (pr != c) {
+      for (int j = 0; j < 8; ++j) std::swap(m[pr][j], m[c][j]);
+      det = -det;
+    }
+    det *= m[c][c];
+    if (m[c][c] == 0.0) return false;
+    for (int r = 0; r < 4; ++r) {
+      if (r == c) continue;
+      const double f = m[r][c] / m[c][c];
+      for (int j = 0; j < 8; ++j) m[r][j] -= f * m[c][j];
+    }
+  }
+  if (!(std::fabs(det) >= eps * bound)) return false;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) inv[i][j] = m[i][j + 4] / m[i][i];
+  return true;
 }
 
 int bidir_check(const or_scene* s, const or_run* run) {
@@ -1319,6 +1421,188 @@ int or_gradient_bidir(const or_scene* s, const or_params* p, const or_run* run, 
       out->d_albedo[j] = v;
     }
   if (out->d_heights) for (int j = 0; j < p->n_heights; ++j) out->d_heights[j] = 0.0;
+  if (out->d_Le) for (int c = 0; c < 3; ++c) { double v = 0; for (int t = 0; t < nt; ++t) v += acc[t].gL[c]; out->d_Le[c] = v; }
+  if (out->loss) { double v = 0; for (int t = 0; t < nt; ++t) v += acc[t].loss; out->loss[0] = v; }
+  return 0;
+}
+
+// Paper-literal attached LRB-3 gradient of <dI, I_s> (see the section above): naive AD of
+// the frozen path function with each connection's film position at its own frozen surface
+// coordinates, plus the film-position transport along specular chains by accumulated
+// two-point Jacobians with the determinant-guarded inverse (threshold det_eps) and, when
+// jac_noise, Rademacher noise of scale sigma at diffuse vertices.  Attached only.
+int or_gradient_literal(const or_scene* s, const or_params* p, const or_run* run, const double* dI,
+                        const uint8_t* mask, int jac_noise, uint64_t noise_seed, double sigma, double det_eps,
+                        or_grads* out) {
+  if (!run->attached) return -1;
+  Scene sc{s, p};
+  sc.setup();
+  int nt = std::max(1, run->n_threads);
+  std::vector<Acc> acc(nt);
+  const double N = (double)(run->n_norm > 0 ? run->n_norm : run->n_paths);
+  const int W = s->W, H = s->H;
+  parallel_paths(nt, run->n_paths, [&](int tid, int64_t a, int64_t b) {
+    Acc& A = acc[tid];
+    A.ga.assign(p->n_albedo, 0.0);
+    A.gh.assign(p->n_heights, 0.0);
+    Tape tape;
+    TP = &tape;
+    std::vector<int> node_a(p->n_albedo, -1), node_h(p->n_heights, -1), touch_a, touch_h;
+    std::vector<ConnOut<double>> cs;
+    std::vector<ConnOut<V>> cv;
+    auto flush_h = [&](double w) {  // add w * d(root)/d(heights) of the current tape
+      for (int idx : touch_h) A.gh[idx] += w * tape.adj[node_h[idx]];
+      for (int idx : touch_h) node_h[idx] = -1;
+      touch_h.clear();
+    };
+    for (int64_t i = a; i < b; ++i) {
+      if (mask && !mask[i]) continue;
+      const uint64_t n = (uint64_t)(run->path_begin + i);
+      Path P = trace(sc, run->seed, n, run->max_depth, run->rr_depth, run->rr_q);
+      eval_path<double>(sc, P, Plain{p->albedo}, Plain{p->Le}, Plain{p->heights}, N, cs, &P);
+      // (1) naive AD of the frozen path function with the film-position split
+      tape.clear();
+      touch_a.clear(); touch_h.clear();
+      V Lev[3];
+      for (int c = 0; c < 3; ++c) Lev[c] = V(p->Le[c], tape.push(-1, 0, -1, 0));
+      Leaves la{p->albedo, &node_a, &touch_a}, lh{p->heights, &node_h, &touch_h};
+      eval_path<V>(sc, P, la, Lev, lh, N, cv, nullptr, true);
+      V loss(0.0);
+      for (auto& c : cv) {
+        V Lb[3];
+        adjoint_read<V>(dI, W, H, c.ux, c.uy, Lb, run->filter);
+        loss = loss + c.L[0] * Lb[0] + c.L[1] * Lb[1] + c.L[2] * Lb[2];
+      }
+      A.loss += loss.v;
+      if (loss.i >= 0) {
+        tape.backward(loss.i);
+        for (int c = 0; c < 3; ++c) A.gL[c] += tape.adj[Lev[c].i];
+        for (int idx : touch_a) A.ga[idx] += tape.adj[node_a[idx]];
+        for (int idx : touch_h) A.gh[idx] += tape.adj[node_h[idx]];
+      }
+      for (int idx : touch_a) node_a[idx] = -1;
+      for (int idx : touch_h) node_h[idx] = -1;
+      touch_h.clear();
+      // (2) film-position transport along specular chains (Eq. 18-19)
+      const int K = (int)P.v.size();
+      if (K < 2 || cs.empty()) continue;
+      const Rand4 r0 = rand4(run->seed, n, 0, 0);
+      auto prim_of = [&](int j) { return j == 0 ? -1 : P.v[j - 1].prim; };  // vertex j = 1..K, 0 = emitter
+      auto coords = [&](int j, double v[2]) {
+        if (j == 0) { v[0] = r0.u[0]; v[1] = r0.u[1]; }
+        else { v[0] = P.v[j - 1].b1; v[1] = P.v[j - 1].b2; }
+      };
+      // a_i (position rows of the sensor Jacobian, weighted by dL/du_i) per connection vertex
+      std::vector<std::array<double, 4>> arow(K + 1, std::array<double, 4>{0, 0, 0, 0});
+      for (auto& c : cs) {
+        const int j = c.vi + 1;
+        tape.clear();
+        V u[2] = {V(c.ux, tape.push(-1, 0, -1, 0)), V(c.uy, tape.push(-1, 0, -1, 0))};
+        V Lb[3];
+        adjoint_read<V>(dI, W, H, u[0], u[1], Lb, run->filter);
+        V term = Lb[0] * V(c.L[0]) + Lb[1] * V(c.L[1]) + Lb[2] * V(c.L[2]);
+        double q[2] = {0, 0};
+        if (term.i >= 0) { tape.backward(term.i); q[0] = tape.adj[u[0].i]; q[1] = tape.adj[u[1].i]; }
+        // du/dv = du/dx [e1 e2] at the vertex's frozen coordinates
+        double vv[2];
+        coords(j, vv);
+        D3 o, e1, e2;
+        sc.prim<double>(prim_of(j), p->heights, o, e1, e2);
+        for (int d = 0; d < 2; ++d) {
+          tape.clear();
+          V t0(vv[0], tape.push(-1, 0, -1, 0)), t1(vv[1], tape.push(-1, 0, -1, 0));
+          Vec<V> X = lift<V>(o) + lift<V>(e1) * t0 + lift<V>(e2) * t1;
+          V ux, uy, zc, dd;
+          project<V>(sc, X, ux, uy, zc, dd);
+          const V& uo = d == 0 ? ux : uy;
+          if (uo.i < 0) continue;
+          tape.backward(uo.i);
+          arow[j][2] += q[d] * tape.adj[t0.i];
+          arow[j][3] += q[d] * tape.adj[t1.i];
+        }
+      }
+      // J_j for j = 1..K-1 and the accumulated products J_{1->j}
+      std::vector<std::array<double, 16>> Jacc(K + 1);
+      M4 Jp = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+      std::memcpy(Jacc[1].data(), Jp, sizeof(M4));
+      std::vector<bool> spec(K + 1, false);
+      // singular by construction once a zero block has entered the product (a diffuse vertex
+      // without noise): detected exactly, the determinant guard judges the rest
+      std::vector<bool> sing(K + 1, false);
+      for (int j = 1; j < K; ++j) {
+        sing[j + 1] = sing[j];
+        M4 Jj = {{0, 0, 1, 0}, {0, 0, 0, 1}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+        const Vtx& vx = P.v[j - 1];
+        if (vx.kind == K_SPECULAR) {
+          spec[j] = true;
+          double vp[2], vj[2];
+          coords(j - 1, vp);
+          coords(j, vj);
+          for (int d = 0; d < 2; ++d) {
+            tape.clear();
+            V a0(vp[0], tape.push(-1, 0, -1, 0)), a1(vp[1], tape.push(-1, 0, -1, 0));
+            V b0(vj[0], tape.push(-1, 0, -1, 0)), b1(vj[1], tape.push(-1, 0, -1, 0));
+            const V A2[2] = {a0, a1}, B2[2] = {b0, b1};
+            V outv[2];
+            spec_next<V>(sc, ConstV{p->heights}, prim_of(j - 1), A2, prim_of(j), B2, vx.refl, prim_of(j + 1), outv);
+            if (outv[d].i < 0) continue;
+            tape.backward(outv[d].i);
+            Jj[2 + d][0] = tape.adj[a0.i]; Jj[2 + d][1] = tape.adj[a1.i];
+            Jj[2 + d][2] = tape.adj[b0.i]; Jj[2 + d][3] = tape.adj[b1.i];
+          }
+        } else if (jac_noise) {
+          const double eps = rand4(noise_seed, n, (uint32_t)j, 4).u[0] < 0.5 ? -sigma : sigma;
+          Jj[2][0] = eps;
+          Jj[3][1] = eps;
+        } else {
+          sing[j + 1] = true;
+        }
+        M4 Jn;
+        m4_mul(Jj, reinterpret_cast<const double(*)[4]>(Jacc[j].data()), Jn);
+        std::memcpy(Jacc[j + 1].data(), Jn, sizeof(M4));
+      }
+      // A_rem(j) = sum_{i >= j} a_i J_{1->i}; at each specular x_j project A_rem(j+1) with
+      // the guarded inverse of J_{1->j+1} and contract with the explicit height dependence
+      // of v_{j+1}
+      std::array<double, 4> Arem = {0, 0, 0, 0};
+      for (int j = K; j >= 1; --j) {
+        // Arem currently holds sum_{i > j}; add vertex j's own row
+        const double(*Ji)[4] = reinterpret_cast<const double(*)[4]>(Jacc[j].data());
+        for (int c = 0; c < 4; ++c)
+          for (int k = 0; k < 4; ++k) Arem[c] += arow[j][k] * Ji[k][c];
+        // now Arem = A_rem(j); vertex j-1 (if specular) maps p_{j-1} -> p_j
+        const int js = j - 1;
+        if (js < 1 || !spec[js]) continue;
+        M4 inv;
+        if (sing[j] || !m4_inv(Ji, inv, det_eps)) continue;
+        double aloc[4] = {0, 0, 0, 0};
+        for (int c = 0; c < 4; ++c)
+          for (int k = 0; k < 4; ++k) aloc[c] += Arem[k] * inv[k][c];
+        if (aloc[2] == 0.0 && aloc[3] == 0.0) continue;
+        double vp[2], vj[2];
+        coords(js - 1, vp);
+        coords(js, vj);
+        tape.clear();
+        touch_h.clear();
+        const V A2[2] = {V(vp[0]), V(vp[1])}, B2[2] = {V(vj[0]), V(vj[1])};
+        V outv[2];
+        spec_next<V>(sc, lh, prim_of(js - 1), A2, prim_of(js), B2, P.v[js - 1].refl, prim_of(js + 1), outv);
+        V w = outv[0] * V(aloc[2]) + outv[1] * V(aloc[3]);
+        if (w.i >= 0) {
+          tape.backward(w.i);
+          flush_h(1.0);
+        } else {
+          for (int idx : touch_h) node_h[idx] = -1;
+          touch_h.clear();
+        }
+      }
+    }
+    TP = nullptr;
+  });
+  if (out->d_albedo)
+    for (int j = 0; j < p->n_albedo; ++j) { double v = 0; for (int t = 0; t < nt; ++t) if (acc[t].ga.size()) v += acc[t].ga[j]; out->d_albedo[j] = v; }
+  if (out->d_heights)
+    for (int j = 0; j < p->n_heights; ++j) { double v = 0; for (int t = 0; t < nt; ++t) if (acc[t].gh.size()) v += acc[t].gh[j]; out->d_heights[j] = v; }
   if (out->d_Le) for (int c = 0; c < 3; ++c) { double v = 0; for (int t = 0; t < nt; ++t) v += acc[t].gL[c]; out->d_Le[c] = v; }
   if (out->loss) { double v = 0; for (int t = 0; t < nt; ++t) v += acc[t].loss; out->loss[0] = v; }
   return 0;

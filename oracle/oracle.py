@@ -93,6 +93,8 @@ def lib():
                                           C.c_void_p, C.c_void_p, C.c_void_p]
             L.or_gradient_bidir.argtypes = [P(or_scene), P(or_params), P(or_run), C.c_int64, C.c_void_p,
                                             C.c_void_p, C.c_void_p, P(or_grads)]
+            L.or_gradient_literal.argtypes = [P(or_scene), P(or_params), P(or_run), C.c_void_p, C.c_void_p,
+                                              C.c_int, C.c_uint64, C.c_double, C.c_double, P(or_grads)]
             L.or_connections.argtypes = [P(or_scene), P(or_params), P(or_run), C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_int64]
             L.or_connections.restype = C.c_int64
@@ -224,6 +226,28 @@ def connections(scene, dI, seed=0, n_paths=1 << 12, max_depth=4, path_begin=0, n
     k = lib().or_connections(C.byref(b.sc), C.byref(b.params), C.byref(run), dI.ctypes.data, _ptr(m),
                              rows.ctypes.data, cap)
     return rows[: min(k, cap)]
+
+
+def gradient_literal(scene, dI, seed=0, n_paths=1 << 12, max_depth=4, path_begin=0, n_norm=0, mask=None,
+                     jac_noise=False, noise_seed=0, sigma=1.0, det_eps=1e-6, n_threads=0, filter=0):
+    """dict(d_albedo, d_Le, d_heights, loss): the paper-literal attached LRB-3 gradient
+    (film-position transport by accumulated two-point Jacobians with the determinant-guarded
+    inverse, optional Jacobian noise; see or_gradient_literal)."""
+    b = _Bound(scene)
+    dI = np.ascontiguousarray(dI, dtype=np.float64)
+    ga = np.zeros(max(1, scene.albedo.size))
+    gl = np.zeros(3)
+    gh = np.zeros(max(1, scene.heights.size))
+    loss = np.zeros(1)
+    g = or_grads(_dp(ga), _dp(gl), _dp(gh), _dp(loss))
+    run = or_run(seed, path_begin, n_paths, n_norm or n_paths, max_depth, 0, 1, _threads(n_threads), 0, 1.0,
+                 int(filter))
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    rc = lib().or_gradient_literal(C.byref(b.sc), C.byref(b.params), C.byref(run), dI.ctypes.data, _ptr(m),
+                                   int(bool(jac_noise)), int(noise_seed), float(sigma), float(det_eps), C.byref(g))
+    if rc != 0:
+        raise ValueError(f"oracle or_gradient_literal refused (code {rc})")
+    return dict(d_albedo=ga[:scene.albedo.size], d_Le=gl, d_heights=gh[:scene.heights.size], loss=float(loss[0]))
 
 
 def render_bidir(scene, n_cam, seed=0, n_paths=1 << 12, max_depth=4, n_norm=0, mask=None, cam_mask=None,

@@ -331,6 +331,8 @@ lt_status check_opts(const lt_scene* s, const lt_params* p, const lt_render_opts
     return fail(LT_ERR_INVALID_ARG, "rr_depth must be >= 0 and rr_prob in (0, 1]");
   if (o->filter != 0 && o->filter != 1) return fail(LT_ERR_INVALID_ARG, "filter must be 0 (tent) or 1 (Gaussian)");
   if (o->scatter < 0 || o->scatter > 3) return fail(LT_ERR_INVALID_ARG, "scatter must be 0, 1, 2 or 3");
+  if (o->literal != 0 && o->literal != 1) return fail(LT_ERR_INVALID_ARG, "literal must be 0 or 1");
+  if (o->det_eps < 0.0f) return fail(LT_ERR_INVALID_ARG, "det_eps must be >= 0");
   return LT_OK;
 }
 
@@ -357,6 +359,9 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.list = nullptr;
   k.list_n = nullptr;
   k.ticket = nullptr;
+  k.jac_noise = o->jac_noise;
+  k.noise_seed = o->noise_seed;
+  k.det_eps = o->det_eps > 0.0f ? o->det_eps : 1e-6f;
   return k;
 }
 
@@ -725,6 +730,12 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
   if (o->n_paths == 0) return LT_OK;
   KParams kp = kparams(p, o);
   set_privatization(s, g, kp, o->scatter);
+  if (o->literal) {
+    if (!o->attached) return fail(LT_ERR_INVALID_ARG, "the literal transport is for attached gradients");
+    cudaError_t e = launch_lrb3_literal(dev_for(s, o), kp, dI, gp, cfg_for(s, o), st);
+    if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
+    return LT_OK;
+  }
   if (o->lrb3_state && o->lrb3_mask_ready && o->n_paths <= kListMaxPaths) {
     // the primal listed the paths with a valid connection: passes 2 and 3 visit only those
     char* base = (char*)o->lrb3_state;

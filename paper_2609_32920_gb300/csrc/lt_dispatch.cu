@@ -47,6 +47,11 @@ cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI,
   return w4::launch_film_l2(I, T, n, dI, loss, sms, st);
 }
 
+cudaError_t launch_lrb3_literal(const DevScene& S, const KParams& kp, const float* dI, const GradPtrs& g,
+                                const LaunchCfg& L, cudaStream_t st) {
+  return LT_BY_WIDTH(S.width, launch_lrb3_literal(S, kp, dI, g, L, st));
+}
+
 cudaError_t launch_bidir(const DevScene& S, const KParams& kp, const BidirArgs& ba, bool backward, float* image,
                          const float* dI, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {
   return LT_BY_WIDTH(S.width, launch_bidir(S, kp, ba, backward, image, dI, g, L, st));

@@ -2067,6 +2067,452 @@ __global__ void __launch_bounds__(128) k_bidir_cam(DevScene S, KParams kp, Bidir
   }
 }
 
+// ======================================================================= paper-literal attached LRB-3
+// The paper's transport of the splat-position adjoint (Sec. 3.3, Eq. 4-7; Sec. 4.3.2, Eq.
+// 18-19; Sec. 5) in place of the exact chain transport: per path the segment states
+// p_k = (v_{k-1}, v_k) (surface coordinates; v_{-1} the emitter's (s, t)), their Jacobians
+// J_k = d p_{k+1} / d p_k accumulated forward (Jacc_k = d p_k / d p_0, 4x4), the position
+// rows a_k = (0, 0, dL/du du/dv_k) of every valid connection summed as
+// A_pos = sum_k a_k Jacc_k in pass 2 (Eq. 18), and in pass 3 the remainder projected back at
+// each specular vertex with the inverse of Jacc (Eq. 19), zero when Jacc is singular by
+// construction or |det| is below det_eps times Hadamard's bound (the product of the row
+// norms; Sec. 5),
+// its position rows contracted with the explicit height dependence of the next vertex's
+// surface coordinates.  A vertex after a diffuse one keeps its surface coordinates, so J's
+// lower block there is zero (and Jacc singular from then on); with jac_noise it is
+// eps [I 0], eps = +-1 from Philox stream 4 at that depth keyed by noise_seed (zero mean: the
+// transport is unbiased over the noise).  Everything else is the exact form (its chain
+// transport keeps the radiance terms); a connection's film position at a sliding vertex
+// enters locally at its frozen surface coordinates.  One path per thread, fused passes.
+
+namespace dual {
+// Forward-mode dual numbers with N directional derivatives.
+template <int N>
+struct Dn {
+  float v;
+  float d[N];
+};
+template <int N>
+__device__ __forceinline__ Dn<N> dn(float v) {
+  Dn<N> r;
+  r.v = v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = 0.0f;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator+(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = fmaf(a.d[i], b.v, a.v * b.d[i]);
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(const Dn<N>& a, float s) {
+  Dn<N> r;
+  r.v = a.v * s;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * s;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator/(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  const float ib = 1.0f / b.v;
+  r.v = a.v * ib;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> dsqrt(const Dn<N>& a) {
+  Dn<N> r;
+  r.v = sqrtf(a.v);
+  const float h = 0.5f / r.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * h;
+  return r;
+}
+template <int N>
+struct V3 {
+  Dn<N> x, y, z;
+};
+template <int N>
+__device__ __forceinline__ V3<N> v3(float3 a) {
+  return V3<N>{dn<N>(a.x), dn<N>(a.y), dn<N>(a.z)};
+}
+template <int N>
+__device__ __forceinline__ V3<N> operator+(const V3<N>& a, const V3<N>& b) {
+  return V3<N>{a.x + b.x, a.y + b.y, a.z + b.z};
+}
+template <int N>
+__device__ __forceinline__ V3<N> operator-(const V3<N>& a, const V3<N>& b) {
+  return V3<N>{a.x - b.x, a.y - b.y, a.z - b.z};
+}
+template <int N>
+__device__ __forceinline__ V3<N> operator*(const V3<N>& a, const Dn<N>& s) {
+  return V3<N>{a.x * s, a.y * s, a.z * s};
+}
+template <int N>
+__device__ __forceinline__ V3<N> operator*(const V3<N>& a, float s) {
+  return V3<N>{a.x * s, a.y * s, a.z * s};
+}
+template <int N>
+__device__ __forceinline__ Dn<N> ddot(const V3<N>& a, const V3<N>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <int N>
+__device__ __forceinline__ V3<N> dcross(const V3<N>& a, const V3<N>& b) {
+  return V3<N>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Surface coordinates of the sliding vertex that follows specular vertex x_j (edges e1, e2)
+// reached from x_p, along the reflected or refracted direction, on the plane (o_n, e1_n,
+// e2_n) of the primitive it hits (Snell, reflection, ray-plane intersection).
+template <int N>
+__device__ __forceinline__ void spec_next(const V3<N>& xp, const V3<N>& xj, const V3<N>& e1, const V3<N>& e2,
+                                          float ior, bool refl, const V3<N>& on, const V3<N>& e1n,
+                                          const V3<N>& e2n, Dn<N> out[2]) {
+  V3<N> d = xj - xp;
+  const Dn<N> il = dn<N>(1.0f) / dsqrt(ddot(d, d));
+  const V3<N> din = d * il;
+  V3<N> n = dcross(e1, e2);
+  n = n * (dn<N>(1.0f) / dsqrt(ddot(n, n)));
+  const bool entering = ddot(din, n).v < 0.0f;
+  const V3<N> ns = entering ? n : n * -1.0f;
+  const float eta = entering ? 1.0f / ior : ior;
+  const Dn<N> ci = ddot(din, ns) * -1.0f;
+  V3<N> dout;
+  if (refl) {
+    dout = din + ns * (ci * 2.0f);
+  } else {
+    const Dn<N> ct = dsqrt(dn<N>(1.0f) - (dn<N>(1.0f) - ci * ci) * (eta * eta));
+    dout = din * eta + ns * (ci * eta - ct);
+  }
+  const V3<N> m = dcross(e1n, e2n);
+  const Dn<N> tau = ddot(on - xj, m) / ddot(dout, m);
+  const V3<N> q = xj + dout * tau - on;
+  const Dn<N> inn = dn<N>(1.0f) / ddot(m, m);
+  out[0] = ddot(dcross(q, e2n), m) * inn;
+  out[1] = ddot(dcross(e1n, q), m) * inn;
+}
+}  // namespace dual
+using dual::Dn;
+using dual::V3;
+
+// A vertex of the path as the literal transport sees it: primitive (-1: the emitter),
+// surface coordinates, and whether it is specular (with its branch).
+struct LitV {
+  int prim;
+  float v0, v1;
+  bool spec, refl;
+};
+
+// Point, edges and (for N = 9, slot base sb) height derivatives of vertex `a` on its
+// primitive: a triangle vertex k of a height field moves along +y with its height, so
+// o moves with h0, e1 with h1 - h0, e2 with h2 - h0 and the point with the barycentric
+// weights.  The emitter and fixed primitives have no derivative.
+template <int N>
+__device__ __forceinline__ void lit_geom(const DevScene& S, const LitV& a, int sb, V3<N>& x, V3<N>& e1, V3<N>& e2,
+                                         V3<N>& o, int hidx[3]) {
+  float3 O, E1, E2;
+  hidx[0] = hidx[1] = hidx[2] = -1;
+  if (a.prim < 0) {
+    O = S.lo; E1 = S.le1; E2 = S.le2;
+  } else {
+    const Prim P = load_prim(S, a.prim);
+    O = P.o; E1 = P.e1; E2 = P.e2;
+    const int4 ph = __ldg(S.prim_h + a.prim);
+    hidx[0] = ph.x; hidx[1] = ph.y; hidx[2] = ph.z;
+  }
+  o = dual::v3<N>(O); e1 = dual::v3<N>(E1); e2 = dual::v3<N>(E2);
+  x = dual::v3<N>(O + E1 * a.v0 + E2 * a.v1);
+  if (N == 9 && sb >= 0) {
+    const float w[3] = {1.0f - a.v0 - a.v1, a.v0, a.v1};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (hidx[k] < 0) continue;
+      x.y.d[sb + k] = w[k];
+      if (k == 0) { o.y.d[sb] = 1.0f; e1.y.d[sb] = -1.0f; e2.y.d[sb] = -1.0f; }
+      if (k == 1) e1.y.d[sb + 1] = 1.0f;
+      if (k == 2) e2.y.d[sb + 2] = 1.0f;
+    }
+  }
+}
+
+// Lower block of J for specular vertex b (reached from a), the next vertex on prim pn:
+// d(v_next) / d(v_a, v_b), 2 x 4.
+__device__ __forceinline__ void lit_jacobian(const DevScene& S, const LitV& a, const LitV& b, int pn, float J[2][4]) {
+  V3<4> xa, e1a, e2a, oa, xb, e1b, e2b, ob, xn, e1n, e2n, on;
+  int h[3];
+  lit_geom<4>(S, a, -1, xa, e1a, e2a, oa, h);
+  lit_geom<4>(S, b, -1, xb, e1b, e2b, ob, h);
+  // directions: 0, 1 = v_a; 2, 3 = v_b
+  xa.x.d[0] = e1a.x.v; xa.y.d[0] = e1a.y.v; xa.z.d[0] = e1a.z.v;
+  xa.x.d[1] = e2a.x.v; xa.y.d[1] = e2a.y.v; xa.z.d[1] = e2a.z.v;
+  xb.x.d[2] = e1b.x.v; xb.y.d[2] = e1b.y.v; xb.z.d[2] = e1b.z.v;
+  xb.x.d[3] = e2b.x.v; xb.y.d[3] = e2b.y.v; xb.z.d[3] = e2b.z.v;
+  const LitV nv = {pn, 0.0f, 0.0f, false, false};
+  lit_geom<4>(S, nv, -1, xn, e1n, e2n, on, h);
+  Dn<4> out[2];
+  dual::spec_next<4>(xa, xb, e1b, e2b, __ldg(S.mat_ior + load_prim(S, b.prim).mat), b.refl, on, e1n, e2n, out);
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) J[r][c] = out[r].d[c];
+}
+
+// The heights' share of the film-position transport at specular vertex b: a . v_next with the
+// surface coordinates of a and b held, differentiated with respect to the heights of the
+// three primitives involved.
+__device__ __forceinline__ void lit_contract(const DevScene& S, const LitV& a, const LitV& b, int pn, float a0,
+                                             float a1, float* dh) {
+  if (!dh) return;
+  V3<9> xa, e1a, e2a, oa, xb, e1b, e2b, ob, xn, e1n, e2n, on;
+  int ha[3], hb[3], hn[3];
+  lit_geom<9>(S, a, 0, xa, e1a, e2a, oa, ha);
+  lit_geom<9>(S, b, 3, xb, e1b, e2b, ob, hb);
+  const LitV nv = {pn, 0.0f, 0.0f, false, false};
+  lit_geom<9>(S, nv, 6, xn, e1n, e2n, on, hn);
+  Dn<9> out[2];
+  dual::spec_next<9>(xa, xb, e1b, e2b, __ldg(S.mat_ior + load_prim(S, b.prim).mat), b.refl, on, e1n, e2n, out);
+  const int* hs[3] = {ha, hb, hn};
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int hi = hs[t][k];
+      const float g = fmaf(a0, out[0].d[3 * t + k], a1 * out[1].d[3 * t + k]);
+      if (hi >= 0 && g != 0.0f) red_add(dh + hi, g);
+    }
+}
+
+// m = A * m (4x4, row major)
+__device__ __forceinline__ void m4_left(const float A[4][4], float m[4][4]) {
+  float r[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r[i][j] = A[i][0] * m[0][j] + A[i][1] * m[1][j] + A[i][2] * m[2][j] + A[i][3] * m[3][j];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m[i][j] = r[i][j];
+}
+// y = x M^-1 for a row vector x (solve M^T y^T = x^T by Gauss-Jordan with partial
+// pivoting); false when |det M| < eps times the product of M's row norms (Hadamard's bound
+// on |det M|: the ratio is 1 for orthogonal rows and 0 for singular M, and a product of
+// Jacobians that is singular in exact arithmetic keeps a ratio at the level of rounding).
+__device__ __forceinline__ bool row_solve(const float M[4][4], const float x[4], float y[4], float eps) {
+  float bound = 1.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    bound *= sqrtf(M[i][0] * M[i][0] + M[i][1] * M[i][1] + M[i][2] * M[i][2] + M[i][3] * M[i][3]);
+  if (!(bound > 0.0f)) return false;
+  float a[4][5];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[i][j] = M[j][i];
+    a[i][4] = x[i];
+  }
+  float det = 1.0f;
+  for (int c = 0; c < 4; ++c) {
+    int pr = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (fabsf(a[r][c]) > fabsf(a[pr][c])) pr = r;
+    if (pr != c) {
+      for (int j = 0; j < 5; ++j) { const float t = a[pr][j]; a[pr][j] = a[c][j]; a[c][j] = t; }
+      det = -det;
+    }
+    det *= a[c][c];
+    if (a[c][c] == 0.0f) return false;
+    for (int r = 0; r < 4; ++r) {
+      if (r == c) continue;
+      const float f = a[r][c] / a[c][c];
+      for (int j = c; j < 5; ++j) a[r][j] -= f * a[c][j];
+    }
+  }
+  if (!(fabsf(det) >= eps * bound)) return false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) y[i] = a[i][4] / a[i][i];
+  return true;
+}
+
+// Accumulated Jacobian after vertex k of a path: J of vertex k-1 applied (its lower block
+// from lit_jacobian when specular; zero, or the noise block, when diffuse).  `singular`
+// records that a zero block has entered the product, which is then singular by construction
+// (rounding would hide that from the determinant).
+__device__ __forceinline__ void lit_advance(const DevScene& S, const KParams& kp, uint64_t n, int k, const LitV& a,
+                                            const LitV& b, int pn, float Jacc[4][4], bool& singular) {
+  float J[4][4] = {{0, 0, 1, 0}, {0, 0, 0, 1}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+  if (b.spec) {
+    float L2[2][4];
+    lit_jacobian(S, a, b, pn, L2);
+    for (int c = 0; c < 4; ++c) { J[2][c] = L2[0][c]; J[3][c] = L2[1][c]; }
+  } else if (kp.jac_noise) {
+    const float eps = rand4(kp.noise_seed, n, (uint32_t)k, 4).x < 0.5f ? -1.0f : 1.0f;
+    J[2][0] = eps;
+    J[3][1] = eps;
+  } else {
+    singular = true;
+  }
+  m4_left(J, Jacc);
+}
+
+// Position row of a connection at vertex x on prim (edges e1, e2): dL/du du/dv.
+__device__ __forceinline__ float2 lit_row(const DevScene& S, float3 x, const Prim& P, float2 q) {
+  const float3 d = x - S.cpos;
+  const float zc = dot(d, S.cf), pr = dot(d, S.cr), pu = dot(d, S.cu);
+  const float ax = 0.5f * (float)S.W / (S.tanx * zc), ay = -0.5f * (float)S.H / (S.tany * zc);
+  const float3 g = (S.cr - S.cf * (pr / zc)) * (q.x * ax) + (S.cu - S.cf * (pu / zc)) * (q.y * ay);
+  return make_float2(dot(g, P.e1), dot(g, P.e2));
+}
+
+__global__ void __launch_bounds__(128) k_lrb3_literal(DevScene S, KParams kp, const float* __restrict__ dI,
+                                                      GradPtrs g0) {
+  extern __shared__ float sgrad[];
+  const Sink sink = sink_begin(kp, g0, sgrad);
+  GradPtrs g = g0;
+  g.d_albedo = sink.alb;
+  g.d_heights = sink.h;
+  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  float3 gLe = f3(0, 0, 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < kp.n_paths; p += stride) {
+    if (kp.mask && !kp.mask[p]) continue;
+    const uint64_t n = (uint64_t)(kp.path_offset + p);
+    const float4 r0 = rand4(kp.seed, n, 0);
+    const LitV em = {-1, r0.x, r0.y, false, false};
+    // ---- pass 2: delta_total (Eq. 14), validity, and A_pos (Eq. 18)
+    Walk w;
+    float3 x0;
+    walk_start(S, kp.seed, n, Le, w, x0);
+    float3 dtot = f3(0, 0, 0);
+    uint64_t valid = 0;
+    float Jacc[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+    float Apos[4] = {0, 0, 0, 0};
+    LitV pa = em, pb = em;  // vertices k-2 and k-1
+    bool singular = false;
+    for (int k = 0; k < kp.max_depth; ++k) {
+      Vtx v;
+      if (!walk_hit(S, w, v)) break;
+      const LitV cur = {v.prim, v.b1, v.b2, !v.diffuse, false};
+      if (k >= 1) lit_advance(S, kp, n, k, pa, pb, v.prim, Jacc, singular);
+      const float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+      if (v.diffuse) {
+        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, nullptr);
+        const Conn c = connect(S, v.x, ns, v.prim);
+        if (c.valid) {
+          valid |= 1ull << k;
+          const float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
+          float2 q;
+          dtot = dtot + mul(adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, &q, kp.filter), L);
+          const float2 a = lit_row(S, v.x, v.P, q);
+          for (int j = 0; j < 4; ++j) Apos[j] += a.x * Jacc[2][j] + a.y * Jacc[3][j];
+        }
+      }
+      const bool refl = walk_scatter(S, w, v, ns, rho, r);
+      walk_rr(kp, n, k, w);
+      pa = pb;
+      pb = cur;
+      pb.refl = refl;
+    }
+    if (!valid) continue;
+    gLe = gLe + f3(dtot.x / Le.x, dtot.y / Le.y, dtot.z / Le.z);  // emitted factor, weight delta_total
+    // ---- pass 3: the exact form's terms with each film position local, and the transport
+    walk_start(S, kp.seed, n, Le, w, x0);
+    float3 rem = dtot;
+    PendAdj pv;
+    pend_init(pv, -1, -1, 0.0f, 0.0f, x0, S.ln);
+    ChainInfo chain;
+    chain.ka = -1;
+    ChainCache cc;
+    cc.reset();
+    const int last = 63 - __clzll((long long)valid);
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) Jacc[i][j] = i == j ? 1.0f : 0.0f;
+    float Arem[4] = {Apos[0], Apos[1], Apos[2], Apos[3]};
+    pa = em;
+    pb = em;
+    singular = false;
+    for (int k = 0; k <= last; ++k) {
+      Vtx v;
+      if (!walk_hit(S, w, v)) { set_err(S, ERR_BOUNDS); break; }  // the replay must reach `last`
+      const LitV cur = {v.prim, v.b1, v.b2, !v.diffuse, false};
+      if (k >= 1) {
+        lit_advance(S, kp, n, k, pa, pb, v.prim, Jacc, singular);
+        if (pb.spec && !singular) {
+          // Eq. 19: the remainder (connections from vertex k on) in the frame of p_k
+          float aloc[4];
+          if (row_solve(Jacc, Arem, aloc, kp.det_eps)) lit_contract(S, pa, pb, v.prim, aloc[2], aloc[3], g.d_heights);
+        }
+      }
+      const float4 r = rand4(kp.seed, n, (uint32_t)(k + 1));
+      att_enter<true>(S, kp, n, k, v, hsum(rem), hsum(rem), pv, chain, g.d_heights, &cc);
+      const bool rec_chain = !v.diffuse;
+      if (rec_chain) cc.record(chain, k, v, w.dir);
+      float3 ns = f3(0, 0, 0), rho = f3(0, 0, 0);
+      if (v.diffuse) {
+        ns = dot(v.nraw, w.dir) < 0.0f ? v.n : -v.n;
+        TexFoot foot;
+        rho = tex_lookup(kp.albedo, v.m, v.b1, v.b2, &foot);
+        float3 wsplat = f3(0, 0, 0);
+        if ((valid >> k) & 1ull) {
+          const Conn c = connect_pre(S, v.x, ns);
+          const float3 L = mul(w.beta, rho) * (c.geo * kp.inv_n);
+          float2 q;
+          const float3 Lb = adjoint_read_f(dI, S.W, S.H, c.ux, c.uy, L, &q, kp.filter);
+          const float3 P = mul(Lb, L);
+          wsplat = P;      // Eq. 15
+          rem = rem - P;   // Eq. 16
+          if (v.attached) {
+            conn_adjoint(S, v.x, v.nraw, hsum(P), q, pv.gx, pv.gn);
+          } else {
+            // radiance terms through the chain; the film position at its own coordinates
+            conn_adjoint(S, v.x, v.nraw, hsum(P), make_float2(0.0f, 0.0f), pv.gx, pv.gn);
+            float3 gxq = f3(0, 0, 0), gnq = f3(0, 0, 0);
+            conn_adjoint(S, v.x, v.nraw, 0.0f, q, gxq, gnq);
+            scatter_heights(S, g.d_heights, v.prim, v.b1, v.b2, gxq, f3(0, 0, 0));
+          }
+          const float2 a = lit_row(S, v.x, v.P, q);
+          for (int j = 0; j < 4; ++j) Arem[j] -= a.x * Jacc[2][j] + a.y * Jacc[3][j];
+        }
+        scatter_albedo(S, g.d_albedo, foot, wsplat + rem, rho);  // + scattering factor (Eq. 17)
+        if (!v.attached) pv.gx = pv.gx + tex_pos_adjoint(kp.albedo, v.m, v.P, v.b1, v.b2, wsplat + rem, rho);
+      }
+      const bool refl = walk_scatter(S, w, v, ns, rho, r);
+      if (rec_chain) cc.record_branch(refl);
+      walk_rr(kp, n, k, w);
+      pa = pb;
+      pb = cur;
+      pb.refl = refl;
+    }
+    pend_flush<true>(S, kp, n, pv, g.d_heights, &cc);
+  }
+  sink_end(kp, g0, sgrad);
+  block_add3(g0.d_Le, gLe);
+}
+
 // ======================================================================= film
 __global__ void k_film_l2(const float* __restrict__ I, const float* __restrict__ T, int64_t n, float* dI,
                           float* loss) {
@@ -2292,6 +2738,13 @@ int batch_occupancy(int pass, bool att, bool chains, int block) {
   return n;
 }
 #undef LT_BATCH_DISPATCH
+
+cudaError_t launch_lrb3_literal(const DevScene& S, const KParams& kp, const float* dI, const GradPtrs& g,
+                                const LaunchCfg& L, cudaStream_t st) {
+  const size_t smem = kp.priv_n > 0 ? sizeof(float) * (size_t)kp.priv_n : 0;
+  launch_paths(k_lrb3_literal, L, kp.n_paths, smem, st, S, kp, dI, g);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bidir(const DevScene& S, const KParams& kp, const BidirArgs& ba, bool backward, float* image,
                          const float* dI, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st) {

@@ -34,6 +34,9 @@ struct KParams {
                                // LRB-3 passes 2 and 3 with known masks: visit only these) or null
   unsigned long long* list_n;  // length of `list`
   unsigned long long* ticket;  // zeroed counters of list entries taken, [0] pass 2, [1] pass 3
+  int jac_noise;               // paper-literal transport: Jacobian noise at diffuse vertices
+  uint64_t noise_seed;         // its Philox key
+  float det_eps;               // its determinant guard
 };
 
 struct GradPtrs {
@@ -102,7 +105,9 @@ struct BidirArgs {
   cudaError_t launch_film_l2(const float* I, const float* T, int64_t n, float* dI, float* loss, int sms,          \
                              cudaStream_t st);                                                                    \
   cudaError_t launch_bidir(const DevScene& S, const KParams& kp, const BidirArgs& ba, bool backward, float* image, \
-                           const float* dI, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);
+                           const float* dI, const GradPtrs& g, const LaunchCfg& L, cudaStream_t st);             \
+  cudaError_t launch_lrb3_literal(const DevScene& S, const KParams& kp, const float* dI, const GradPtrs& g,       \
+                                  const LaunchCfg& L, cudaStream_t st);
 
 namespace w2 { LT_KERNEL_LAUNCHERS }
 namespace w4 { LT_KERNEL_LAUNCHERS }

@@ -55,7 +55,8 @@ class lt_render_opts(C.Structure):
                 ("path_hash", C.c_void_p), ("path_dbg", C.c_void_p), ("census", C.c_void_p),
                 ("lrb3_state", C.c_void_p), ("lrb3_state_bytes", C.c_size_t), ("lrb3_mask_ready", C.c_int),
                 ("rr_depth", C.c_int), ("rr_prob", C.c_float), ("filter", C.c_int), ("bvh_width", C.c_int),
-                ("scatter", C.c_int)]
+                ("scatter", C.c_int), ("literal", C.c_int), ("jac_noise", C.c_int), ("noise_seed", C.c_uint64),
+                ("det_eps", C.c_float)]
 
 
 class lt_grads(C.Structure):
@@ -230,7 +231,7 @@ class Scene:
     def opts(seed=0, n_paths=1 << 14, max_depth=4, attached=0, path_offset=0, n_norm=0, block_size=0,
              blocks_per_sm=0, mask=None, hash_out=None, dbg_out=None, target=TARGET_LUMINANCE, mlp=None,
              census=None, lrb3_state=None, lrb3_mask_ready=0, bvh_width=0, rr_depth=0, rr_prob=1.0, filter=0,
-             scatter=0):
+             scatter=0, literal=0, jac_noise=0, noise_seed=0, det_eps=0.0):
         """Render options.  `lrb3_state`: a device buffer of lrb3_state_bytes(opts) bytes
         selects the two-kernel form of lt_backward_lrb3, and a plain primal given it stores
         the paths' connection-validity masks there; `lrb3_mask_ready=1` lets the backward
@@ -246,6 +247,7 @@ class Scene:
         o.census = None if census is None else census.data_ptr()
         o.bvh_width = int(bvh_width)
         o.scatter = int(scatter)
+        o.literal, o.jac_noise, o.noise_seed, o.det_eps = int(literal), int(jac_noise), int(noise_seed), float(det_eps)
         o.rr_depth, o.rr_prob, o.filter = int(rr_depth), float(rr_prob), int(filter)
         o.lrb3_mask_ready = int(lrb3_mask_ready)
         o.lrb3_state = None if lrb3_state is None else lrb3_state.data_ptr()
