@@ -463,11 +463,18 @@ def _sampled_full_size_check(sc, N, D, seed, blk, dI_seed):
     (where the tent filter's derivative jumps), are masked out on both sides.
 
     Along deep paths the FP32 vertex positions drift from the FP64 ones (each vertex is
-    found from its predecessor and grazing intersections amplify the rounding: film positions
-    differ by up to a few 1e-3 pixels, splat values by about 1e-4 relative through the
-    texture lookups), so the image is held to the per-pixel bound (with the film-position
-    term scaled by the depth) on 99.9 % of its lit pixels and on every unlit one, and the
-    reservoir weights to 1e-3; the gradients keep the 1e-3 relative L2 of the small cases."""
+    found from its predecessor, and grazing intersections and refraction amplify the
+    rounding: film positions differ by up to a few 1e-3 pixels, splat values by about 1e-4
+    relative through the texture lookups), beyond what a per-pixel bound linear in the path
+    length covers.  A film-position error only moves a splat's weight between the pixels
+    of its 2x2 tap square, so the image is held to: its flux (sum) within 1e-5 relative;
+    its relative L2 within 1e-4, and within 1e-4 after summing each pixel's 3x3 neighbourhood
+    (which contains every tap square touching the pixel, so that a film-position error
+    cancels there); every unlit pixel exactly zero.  (Measured: box 3.6e-5 and 1.4e-5,
+    caustic 6.1e-5 and 2.8e-5; the per-pixel bound of the small cases, with its
+    film-position term linear in the path length, holds on all but about 3 in 100 000 lit
+    pixels of the box at depth 16.)  The reservoir
+    weights are held to 1e-3 and the gradients to the 1e-3 relative L2 of the small cases."""
     S = lt.Scene(sc)
     rng = np.random.default_rng(11)
     offs = sorted(int(x) for x in rng.choice(N - blk, 8, replace=False)) + [N - blk]
@@ -509,12 +516,18 @@ def _sampled_full_size_check(sc, N, D, seed, blk, dI_seed):
         mass += O.render(sc, estimator=2, **kw)
         r = O.gradient(sc, dI_np, attached=1, **kw)
         ref = r if ref is None else {k: ref[k] + r[k] for k in ("d_albedo", "d_Le", "d_heights")}
-    # a sparse sample's image error is mostly film-position rounding, which the per-pixel
-    # bound's mass term covers; the relative L2 is a coarse check (box: 4e-5, caustic: 7e-4)
-    assert rel_l2(img, ref_img) < 1e-3
+    def box3(a):
+        p = np.pad(np.asarray(a, dtype=np.float64), ((1, 1), (1, 1), (0, 0)))
+        return sum(p[i:i + a.shape[0], j:j + a.shape[1]] for i in range(3) for j in range(3))
     lit = ref_img != 0
     close = primal_close(img, ref_img, mass=mass, W=max(sc.W, sc.H), depth=D)
-    assert close[lit].mean() >= 0.999 and close[~lit].all()
+    print("full-size primal: rel L2 %.2e, 3x3-summed rel L2 %.2e, flux rel %.2e, per-pixel bound met on %.5f of lit "
+          "pixels" % (rel_l2(img, ref_img), rel_l2(box3(img), box3(ref_img)),
+                      abs(img.sum() - ref_img.sum()) / abs(ref_img.sum()), close[lit].mean()))
+    assert abs(img.sum() - ref_img.sum()) <= 1e-5 * abs(ref_img.sum())
+    assert rel_l2(img, ref_img) < 1e-4
+    assert rel_l2(box3(img), box3(ref_img)) < 1e-4
+    assert np.all(img[~lit] == 0)
     errs = [rel_l2(x.cpu().numpy(), ref[k]) for x, k in ((gH, "d_heights"), (gL, "d_Le"), (gA, "d_albedo"))]
     assert max(errs) < 1e-3, f"LRB-3 gradient relative L2 (heights, Le, albedo): {errs}"
 
