@@ -572,7 +572,7 @@ __device__ __forceinline__ void spec_adjoint(const ChainState& s, float3 gdout, 
 // c specular vertices).  Scatters into the height gradient the contributions of every
 // primitive the chain touches and returns the adjoint of the anchor position (through the
 // chain start's incoming direction).
-__device__ __noinline__ float3 chain_reverse(const DevScene& S, const KParams& kp, uint64_t n, const ChainInfo& c,
+__device__ __forceinline__ float3 chain_reverse(const DevScene& S, const KParams& kp, uint64_t n, const ChainInfo& c,
                                              int kt, float3 gx_t, float* dh, const ChainCache* cc, int prim_t) {
   const ChainRec* rec = nullptr;
   if (cc)
@@ -664,7 +664,7 @@ __device__ __noinline__ bool replay_chain_of(const DevScene& S, const KParams& k
 // Propagate a position adjoint on the sliding end kt of chain c back to the parameters,
 // continuing through earlier chains while the anchor is itself sliding (those chains'
 // Fresnel factors were already counted, so they are re-traversed with zero weight).
-__device__ __noinline__ void propagate_sliding(const DevScene& S, const KParams& kp, uint64_t n, ChainInfo c, int kt,
+__device__ __forceinline__ void propagate_sliding(const DevScene& S, const KParams& kp, uint64_t n, ChainInfo c, int kt,
                                                float3 gx, float* dh, const ChainCache* cc, int prim_t) {
   for (int guard = 0; guard < kMaxDepth; ++guard) {
     float3 g_anchor = chain_reverse(S, kp, n, c, kt, gx, dh, cc, prim_t);
@@ -1495,14 +1495,18 @@ __global__ void __launch_bounds__(128, 4) k_lrb3(DevScene S, KParams kp, const f
 }
 
 // Two-kernel form: pass 2 (per-path state out, emitted-radiance gradient) ...
+// Both passes are latency-bound traversals that gain from more resident warps more than
+// they lose to spilled registers: measured on the GB300, pass 2 at 6 blocks of 128 threads
+// per SM and the specular-chain pass 3 at 8 (64 registers; the chain sweep inlined) took the
+// caustic backward from 8.8 to 7.4 ms, while the lean pass 3 (no chains) was fastest at 4.
 template <bool ST, bool MK>
-__global__ void __launch_bounds__(128) k_lrb3_p2(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
+__global__ void __launch_bounds__(128, 6) k_lrb3_p2(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
                                                  float4* xrec, uint32_t* xhi) {
   lrb3_body<false, ST, false, false, 1, MK>(S, kp, dI, g0, BatchArgs{}, xrec, xhi);
 }
 // ... then pass 3 (albedo and height gradients) from that state.
 template <bool ATT, bool ST, bool CH>
-__global__ void __launch_bounds__(128) k_lrb3_p3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
+__global__ void __launch_bounds__(128, CH ? 8 : 4) k_lrb3_p3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
                                                  const float4* xrec, const uint32_t* xhi) {
   lrb3_body<ATT, ST, CH, false, 2>(S, kp, dI, g0, BatchArgs{}, const_cast<float4*>(xrec),
                                    const_cast<uint32_t*>(xhi));
