@@ -441,6 +441,7 @@ struct ChainState {
 // states are the ones the replay would compute, from the same arithmetic.
 constexpr int kChainCache = 4;
 constexpr int kDraws = 4;  // path draws per lane and step of the LRB-3 loop
+constexpr int kFlushBatch = 16;  // waiting lanes of a warp that sweep their chains together (swept 8-24)
 struct ChainRec {
   ChainInfo info;
   int len;  // recorded specular vertices info.ka .. info.ka+len-1; -1: not usable
@@ -1260,7 +1261,10 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
   else if (list) disp.init_dynamic(min((int64_t)*kp0.list_n, kp0.n_paths), kp0.ticket + (MODE == 1 ? 0 : 1));
   else disp.init(kp0.n_paths);
   int jb = 0;
-  enum { IDLE = 0, PASS2 = 1, PASS3 = 2 };
+  // FLUSH: the lane's path is done except the reverse sweep through the specular chain that
+  // ends at its pending vertex; with DEFER the sweep waits for other lanes of the warp
+  enum { IDLE = 0, PASS2 = 1, PASS3 = 2, FLUSH = 3 };
+  constexpr bool DEFER = CH && ATT && !BATCH && MODE != 1;
   int phase = IDLE, k = 0, last = 0, nconn = 0;
   bool more = true;
   int64_t p = 0;
@@ -1325,6 +1329,21 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     }
   };
   while (true) {
+    // A chain sweep at a path end is long and runs only on the lanes that end a path at that
+    // step.  With DEFER such a lane waits (FLUSH) until kFlushBatch lanes of its warp wait or
+    // the warp has nothing else to do, and the waiting lanes then sweep together.
+    if constexpr (DEFER) {
+      const unsigned fq = __ballot_sync(0xffffffffu, phase == FLUSH);
+      if (fq) {
+        const unsigned busy = __ballot_sync(0xffffffffu, phase == PASS2 || phase == PASS3 || (more && phase == IDLE));
+        if (__popc(fq) >= kFlushBatch || busy == 0u) {
+          if (phase == FLUSH) {
+            pend_flush<CH>(S0, kp0, (uint64_t)(kp0.path_offset + p), pv, gs.d_heights, &cc);
+            phase = IDLE;
+          }
+        }
+      }
+    }
     // A lane that draws a path without a valid connection (pass 3, and pass 2 once the
     // primal's masks are known) has nothing to trace for it: it draws again, up to kDraws
     // times per step, instead of idling through the step.
@@ -1356,7 +1375,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
     if (!__any_sync(0xffffffffu, phase != IDLE || more)) break;
     // pass 2 with known masks also stops after the path's last valid connection
     const int kmax = phase == PASS2 && !MK ? kp.max_depth : last + 1;
-    const bool trav = phase != IDLE && k < kmax && !w.dead;
+    const bool trav = (phase == PASS2 || phase == PASS3) && k < kmax && !w.dead;
     HitRec h;
     h.prim = -1;
     bool pending = false;  // the ray has visits left: the lane resumes it in the next step
@@ -1387,7 +1406,7 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
       const bool vis = phase == PASS2 && c.valid;
       if (vis && occluded<ST>(S, v.x, c.wc, c.dist, v.prim, &cs)) c.valid = false;
     }
-    if (phase == IDLE || pending) continue;
+    if (phase == IDLE || phase == FLUSH || pending) continue;
     const uint64_t n = (uint64_t)(kp.path_offset + p);
     if (MODE != 2 && phase == PASS2) {
       // the path ends at a miss, at the depth limit, or (known masks) once its last valid
@@ -1469,8 +1488,12 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         fin = k > last;
       }
       if (fin) {
-        if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights, &cc);
-        phase = IDLE;
+        if (DEFER && pv.prim >= 0 && pv.sliding && g.d_heights) {
+          phase = FLUSH;
+        } else {
+          if (att) pend_flush<CH>(S, kp, n, pv, g.d_heights, &cc);
+          phase = IDLE;
+        }
       }
     }
   }
