@@ -130,6 +130,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-target study")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched many-scene study")
     ap.add_argument("--no-inverse", action="store_true", help="skip the caustic inverse-rendering study")
+    ap.add_argument("--scatter", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="gradient and splat scatter mode of the step (profiling runs; lt_render_opts.scatter)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: only warm-up and timed steps (no e2e, census, studies or CPU baseline)")
     return ap.parse_args()
@@ -250,7 +252,7 @@ class Step:
 
     LAUNCHES = 9
 
-    def __init__(self, name, dev, path_offset=0, n_norm=0, n_paths=0):
+    def __init__(self, name, dev, path_offset=0, n_norm=0, n_paths=0, scatter=0):
         import torch
 
         from paper_2609_32920_gb300 import lt
@@ -266,7 +268,7 @@ class Step:
         self.state = S.new_lrb3_state(self.n)
         self.path_offset, self.n_norm = path_offset, n_norm or self.n
         kw = dict(seed=1, n_paths=self.n, max_depth=depth, path_offset=path_offset, n_norm=self.n_norm,
-                  lrb3_state=self.state)
+                  lrb3_state=self.state, scatter=scatter)
         self.o_plain = S.opts(**kw)
         self.o_att = S.opts(attached=1, lrb3_mask_ready=1, **kw)
         self.img = S.new_image()
@@ -358,7 +360,7 @@ def run_ours(args):
     n_paths = (1 << args.paths_log2) if args.paths_log2 else (1 << WORKLOADS[wl]["paths_log2"])
     # weak scaling: each rank traces its own paths, no data-path collective
     path_offset, _, n_norm = path_shard(rank, ws, n_paths)
-    step = Step(wl, dev, path_offset, n_norm, n_paths)
+    step = Step(wl, dev, path_offset, n_norm, n_paths, args.scatter)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def barrier():
@@ -367,11 +369,14 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # clocks and throttle reasons are sampled from before the warm-up to the end of the
+    # end-to-end timing, so the record spans both timed regions
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.5)  # nvidia-smi's first sample
     for _ in range(args.warmup):
         step()
     step.S.sync_status()
-    clocks = Clocks(torch.cuda.current_device())
-    clocks.start()
     step_ms, primal_ms, bwd_ms = timed_steps(step, args.steps, flush, barrier)
     total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
@@ -419,6 +424,7 @@ def run_ours(args):
     barrier()
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e_ev) / len(e_ev), dev)
     e2e_value = ws * n_paths / (e2e_ms * 1e-3)
+    clk = clocks.stop()
 
     # ---------------- roofline of the dominant kernel (census from the counting variants)
     census = step.census()
@@ -471,7 +477,6 @@ def run_ours(args):
         studies["caustic_inverse"] = {
             "configured (lr 1e-3, per-vertex heights, L2)": caustic_inverse_study(dev, lr=1e-3),
             "blurred loss, smooth heights": caustic_inverse_study(dev, lr=2e-4, blur_px=8, smooth_cells=8)}
-    clk = clocks.stop()
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N=1 only)
     cpu = None
