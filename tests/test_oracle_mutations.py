@@ -53,6 +53,9 @@ MUTANTS = {
     "bidir_nee_cos": ("const double pf0 = dot(v.ns, wn) * -dot(nL, wn) / (PI * dl * dl);",
                       "const double pf0 = dot(v.ns, wn) / (PI * dl * dl);",
                       ["test_bidirectional_estimator_unbiased_and_exact"]),
+    # Philox key schedule with a wrong Weyl increment (still a good generator: only the
+    # published known-answer vectors tell it apart)
+    "philox_weyl": ("    k1 += 0xBB67AE85u;\n", "    k1 += 0xBB67AE87u;\n", ["test_philox_known_answer_vectors"]),
     # attached slide: intersection parameter with the wrong sign
     "slide_sign": ("T tt = dot(o - xprev, n) / dot(din, n);", "T tt = dot(xprev - o, n) / dot(din, n);",
                    ["test_attached_height_gradient_vs_frozen_central_differences"]),

@@ -32,6 +32,19 @@ def test_philox_uniformity_and_avalanche(oracle):
     assert not np.array_equal(oracle.philox((5, 7), (1, 2, 3, 4)), base)
 
 
+def test_philox_known_answer_vectors(oracle):
+    """The generator reproduces the published known-answer vectors of Philox4x32-10
+    (tests/golden/philox4x32_10_kat.txt, Salmon et al. SC'11): counter, key -> four words."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox((v[4], v[5]), tuple(v[0:4])).astype(np.uint64)
+        assert [int(x) for x in out] == v[6:10], (r, [hex(int(x)) for x in out])
+
+
 def test_uniforms_exact_in_float32(oracle):
     """24-bit uniforms are exactly representable in fp32, so both precisions see the same numbers."""
     u = np.array([oracle.uniforms(99, i, d) for i in range(200) for d in range(3)]).ravel()
