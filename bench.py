@@ -245,12 +245,12 @@ def run_reference(args):
 class Step:
     """One pass of the hot path on a workload: refit the height field (update_tris,
     refit_nodes, refit_big, refit_wide<4>, refit_wide<8>: every width stays current), primal light
-    tracing storing the paths' connection-validity masks (1 kernel), film L2 loss and
-    image adjoint (1), LRB-3-pass backward in its three-pass form, attached (pass 2 and
-    pass 3: 2 kernels).  Events around the primal and the backward pair time them on the
-    launching stream."""
+    tracing storing the paths' connection-validity masks and first connections (1 kernel), film
+    L2 loss and image adjoint (1), LRB-3-pass backward in its three-pass form, attached (pass 2
+    of the single-connection paths, pass 2 of the others, pass 3: 3 kernels).  Events around
+    the primal and the backward time them on the launching stream."""
 
-    LAUNCHES = 9
+    LAUNCHES = 10
 
     def __init__(self, name, dev, path_offset=0, n_norm=0, n_paths=0, scatter=0):
         import torch
@@ -438,7 +438,7 @@ def run_ours(args):
     peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 x max SM clock
     kernel_ms = {"primal": sum(primal_ms) / len(primal_ms), "lrb3_backward": sum(bwd_ms) / len(bwd_ms)}
     names = {"primal": "k_primal<PLAIN> (primal light tracing, sensor connections, splats, validity masks)",
-             "lrb3_backward": "k_lrb3_p2 + k_lrb3_p3 (LRB-3 passes 2 and 3, attached)"}
+             "lrb3_backward": "k_lrb3_single + k_lrb3_p2 + k_lrb3_p3 (LRB-3 passes 2 and 3, attached)"}
     rooflines = {}
     for key in kernel_ms:
         ach = census[key]["flops"] / (kernel_ms[key] * 1e-3) / 1e12

@@ -118,19 +118,22 @@ typedef struct {
                            lt_lrb3_state_bytes(opts) bytes.  Given, passes 2 and 3 run
                            as two kernels and pass 2 stores each path's delta_total
                            and connection-validity mask there (the paper's three-pass
-                           form; 24 B per path, flat in depth); NULL, one fused kernel
+                           form; 44 B per path, flat in depth); NULL, one fused kernel
                            keeps them in registers.  Same result either way.      */
   size_t lrb3_state_bytes; /* size of lrb3_state                                    */
   int lrb3_mask_ready;  /* lt_primal(LT_EST_PLAIN) given lrb3_state also stores each
-                           path's connection-validity mask there, and the list of the
-                           paths that have a valid connection.  Set 1 in the opts of
-                           lt_backward_lrb3 when that primal ran with the same seed,
-                           paths, depth and scene geometry: pass 2 then takes validity
-                           from the mask, traces no visibility rays, stops each path
-                           after its last valid connection, and passes 2 and 3 visit
-                           only the listed paths (the others have delta_total zero;
-                           their stored colour words and path_dbg rows are left as
-                           they are and not read).                              */
+                           path's connection-validity mask there, the list of the
+                           paths that have a valid connection, and each path's first
+                           valid connection (film position, contribution).  Set 1 in
+                           the opts of lt_backward_lrb3 when that primal ran with the
+                           same seed, paths, depth, scene and parameters: pass 2 then
+                           takes validity from the mask, traces no visibility rays,
+                           stops each path after its last valid connection, forms
+                           delta_total of a path with one valid connection from the
+                           stored connection without replaying it, and passes 2 and 3
+                           visit only the listed paths (the others have delta_total
+                           zero; their stored colour words and path_dbg rows are left
+                           as they are and not read).                           */
   int rr_depth;         /* Russian roulette: after each vertex of depth >= rr_depth a
                            path continues with probability rr_prob (Philox stream 2
                            of that depth) and its throughput is divided by rr_prob;
@@ -456,7 +459,10 @@ size_t lt_lrb2_buffer_bytes(const lt_render_opts* opts);
 
 /* Bytes of the optional LRB-3 per-path state (opts->lrb3_state): 16 B (delta_total rgb,
  * validity bits 0-31), 4 B (validity bits 32-63) and 4 B (the list of paths with a valid
- * connection) per path, each array 256-B aligned, then the list's length (8 B). */
+ * connection) per path, then the list's length and the passes' counters (256 B), then
+ * 20 B per path (film position and contribution of the path's first valid connection,
+ * written by the plain primal: pass 2 takes delta_total of a path with exactly one valid
+ * connection from it instead of replaying the path); each array 256-B aligned. */
 size_t lt_lrb3_state_bytes(const lt_render_opts* opts);
 
 /* Bytes of one ResLRB record (constant per path). */

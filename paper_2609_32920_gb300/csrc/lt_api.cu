@@ -359,6 +359,8 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.list = nullptr;
   k.list_n = nullptr;
   k.ticket = nullptr;
+  k.conn1 = nullptr;
+  k.conn1z = nullptr;
   k.jac_noise = o->jac_noise;
   k.noise_seed = o->noise_seed;
   k.det_eps = o->det_eps > 0.0f ? o->det_eps : 1e-6f;
@@ -703,6 +705,8 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
   KParams kp = kparams(p, o);
   if (est == LT_EST_PLAIN && o->lrb3_state) {
     kp.vstate = o->lrb3_state;
+    kp.conn1 = (float4*)((char*)o->lrb3_state + lrb3_state_conn4(o->n_paths));
+    kp.conn1z = (float*)((char*)o->lrb3_state + lrb3_state_connz(o->n_paths));
     if (o->n_paths <= kListMaxPaths) {
       // the list of the paths with a valid connection, for LRB-3 passes 2 and 3
       char* base = (char*)o->lrb3_state;
@@ -735,6 +739,12 @@ lt_status lt_backward_lrb3(lt_scene* s, const lt_params* p, const lt_render_opts
     cudaError_t e = launch_lrb3_literal(dev_for(s, o), kp, dI, gp, cfg_for(s, o), st);
     if (e) return fail(LT_ERR_CUDA, std::string("lt_backward_lrb3: ") + cudaGetErrorString(e));
     return LT_OK;
+  }
+  if (o->lrb3_state && o->lrb3_mask_ready) {
+    // the primal recorded each path's first valid connection: pass 2 takes delta_total of a
+    // path with one valid connection from it
+    kp.conn1 = (float4*)((char*)o->lrb3_state + lrb3_state_conn4(o->n_paths));
+    kp.conn1z = (float*)((char*)o->lrb3_state + lrb3_state_connz(o->n_paths));
   }
   if (o->lrb3_state && o->lrb3_mask_ready && o->n_paths <= kListMaxPaths) {
     // the primal listed the paths with a valid connection: passes 2 and 3 visit only those

@@ -1136,8 +1136,14 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
       if (c.valid) {
         if (ST) ++nconns;
         ++nconn;
-        vmask |= 1ull << k;
         L = mul(w.beta, rho) * (c.geo * kp.inv_n);
+        if (EST == 0 && !BATCH && kp.conn1 && vmask == 0ull) {
+          // the path's first valid connection: LRB-3 pass 2 takes delta_total from this
+          // record when it stays the only one
+          kp.conn1[p] = make_float4(c.ux, c.uy, L.x, L.y);
+          kp.conn1z[p] = L.z;
+        }
+        vmask |= 1ull << k;
         if (active) {
           if (EST == 1) {
             float om = luminance(L);
@@ -1316,6 +1322,8 @@ __device__ __forceinline__ void lrb3_body(const DevScene& S0, const KParams& kp0
         if (kp.dbg) ((float4*)kp.dbg)[got] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         return;
       }
+      // one valid connection: k_lrb3_single has formed its delta_total without a replay
+      if (MODE == 1 && MK && !BATCH && kp.conn1 && (known & (known - 1)) == 0ull) return;
       p = got;
       if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
       float3 x0;
@@ -1527,6 +1535,39 @@ __global__ void __launch_bounds__(128, 6) k_lrb3_p2(DevScene S, KParams kp, cons
                                                  float4* xrec, uint32_t* xhi) {
   lrb3_body<false, ST, false, false, 1, MK>(S, kp, dI, g0, BatchArgs{}, xrec, xhi);
 }
+// Pass 2 of the paths with exactly one valid connection (known masks, the primal's record of
+// each path's first valid connection): delta_total = Lbar (.) L of that connection (Eq. 14)
+// from its recorded film position and contribution, the values a replay computes, one thread
+// per listed path; k_lrb3_p2 leaves these paths out.  On the caustic workload they are 98 %
+// of the paths with a connection.
+__global__ void __launch_bounds__(256) k_lrb3_single(DevScene S, KParams kp, const float* __restrict__ dI,
+                                                    GradPtrs g, float4* xrec, const uint32_t* xhi) {
+  const int64_t n = kp.list ? min((int64_t)*kp.list_n, kp.n_paths) : kp.n_paths;
+  const float3 Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
+  float3 gLe = f3(0, 0, 0);
+  unsigned long long ones = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = kp.list ? (int64_t)kp.list[i] : i;
+    if (kp.mask && !kp.mask[p]) continue;
+    const float4 r = xrec[p];
+    const uint64_t known = (uint64_t)__float_as_uint(r.w) | ((uint64_t)xhi[p] << 32);
+    if (known == 0ull || (known & (known - 1)) != 0ull) continue;
+    const float4 a = kp.conn1[p];
+    const float3 L = f3(a.z, a.w, kp.conn1z[p]);
+    const float3 d = mul(adjoint_read_f(dI, S.W, S.H, a.x, a.y, L, nullptr, kp.filter), L);
+    xrec[p] = make_float4(d.x, d.y, d.z, r.w);
+    gLe = gLe + f3(d.x / Le.x, d.y / Le.y, d.z / Le.z);  // emitted factor, weight delta_total
+    ++ones;
+    if (kp.dbg) ((float4*)kp.dbg)[p] = make_float4(d.x, d.y, d.z, 1.0f);
+  }
+  if (kp.census) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ones += __shfl_xor_sync(0xffffffffu, ones, o);
+    if ((threadIdx.x & 31) == 0 && ones) atomicAdd(kp.census + 4, ones);
+  }
+  block_add3(g.d_Le, gLe);
+}
+
 // ... then pass 3 (albedo and height gradients) from that state.
 template <bool ATT, bool ST, bool CH>
 __global__ void __launch_bounds__(128, CH ? 8 : 4) k_lrb3_p3(DevScene S, KParams kp, const float* __restrict__ dI, GradPtrs g0,
@@ -2634,6 +2675,8 @@ cudaError_t launch_lrb3(const DevScene& S, const KParams& kp, bool att, bool cha
     k2.priv_n = 0;  // pass 2 writes no albedo or height gradients
     GradPtrs g3 = g;
     g3.d_Le = nullptr;  // pass 3 writes no emitted-radiance gradient
+    if (mask_ready && kp.conn1)
+      k_lrb3_single<<<L.sms * 4, 256, 0, st>>>(S, k2, dI, g, xrec, xhi);
     if (kp.census) {
       if (mask_ready) launch_paths(k_lrb3_p2<true, true>, L, kp.n_paths, 0, st, S, k2, dI, g, xrec, xhi);
       else launch_paths(k_lrb3_p2<true, false>, L, kp.n_paths, 0, st, S, k2, dI, g, xrec, xhi);

@@ -34,6 +34,9 @@ struct KParams {
                                // LRB-3 passes 2 and 3 with known masks: visit only these) or null
   unsigned long long* list_n;  // length of `list`
   unsigned long long* ticket;  // zeroed counters of list entries taken, [0] pass 2, [1] pass 3
+  float4* conn1;               // per path: film position and contribution (u_x, u_y, L.r, L.g) of
+  float* conn1z;               // its first valid connection, and L.b (plain primal: writes; LRB-3
+                               // pass 2 with known masks: reads for paths with one connection)
   int jac_noise;               // paper-literal transport: Jacobian noise at diffuse vertices
   uint64_t noise_seed;         // its Philox key
   float det_eps;               // its determinant guard
@@ -118,13 +121,17 @@ LT_KERNEL_LAUNCHERS
 // layout float4[n_paths] then, at byte lrb3_state_split(n_paths), uint32[n_paths] (together
 // lrb3_state_core bytes); then the list of the paths that have a valid connection (uint32
 // indices relative to the call, at lrb3_state_list) and its length (uint64, at
-// lrb3_state_count), written by a plain primal so that passes 2 and 3 visit only those.
+// lrb3_state_count), written by a plain primal so that passes 2 and 3 visit only those;
+// then each path's first valid connection, float4 (u_x, u_y, L.r, L.g) at lrb3_state_conn4
+// and float L.b at lrb3_state_connz, written by the plain primal.
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t lrb3_state_split(int64_t n) { return align256((size_t)n * 16); }
 __host__ __device__ inline size_t lrb3_state_core(int64_t n) { return lrb3_state_split(n) + align256((size_t)n * 4); }
 __host__ __device__ inline size_t lrb3_state_list(int64_t n) { return lrb3_state_core(n); }
 __host__ __device__ inline size_t lrb3_state_count(int64_t n) { return lrb3_state_list(n) + align256((size_t)n * 4); }
-__host__ __device__ inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_count(n) + 256; }
+__host__ __device__ inline size_t lrb3_state_conn4(int64_t n) { return lrb3_state_count(n) + 256; }
+__host__ __device__ inline size_t lrb3_state_connz(int64_t n) { return lrb3_state_conn4(n) + align256((size_t)n * 16); }
+__host__ __device__ inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_connz(n) + align256((size_t)n * 4); }
 // After the list's length (uint64) at lrb3_state_count: the two passes' counters of list
 // entries taken (uint64 each).
 // The path list is used for calls of at most this many paths (uint32 indices).

@@ -136,6 +136,33 @@ def test_lrb3_reuses_primal_validity_masks(request, fixture_name, attached):
         assert rel_l2(x.cpu().numpy(), y.cpu().numpy()) < 1e-5
 
 
+@pytest.mark.parametrize("fixture_name,attached", [("boxhm", 1), ("slab", 1)])
+def test_single_connection_paths_take_delta_total_from_the_primal_record(request, fixture_name, attached):
+    """With the primal's masks, pass 2 forms delta_total of a path with one valid connection
+    from the primal's record of that connection (film position and contribution) instead of
+    replaying it: per path, the same delta_total and connection count as the replay of the
+    fused form, on every path with a connection."""
+    sc, S = request.getfixturevalue(fixture_name)
+    n, D, seed = 1 << 13, 8, 37
+    dI = t32(I.smooth_adjoint(sc.W, sc.H, 39))
+    state = S.new_lrb3_state(n)
+    S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state))
+    dbg = torch.zeros((n, 4), device="cuda")
+    S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state,
+                           lrb3_mask_ready=1, dbg_out=dbg), dI)
+    ref = torch.zeros((n, 4), device="cuda")
+    S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, dbg_out=ref), dI)
+    S.sync_status()
+    a, b = dbg.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+    lit = b[:, 3] > 0
+    one = b[:, 3] == 1
+    assert one.sum() > 100 and one.sum() <= lit.sum()
+    assert np.array_equal(a[lit, 3], b[lit, 3])
+    scale = np.abs(b[lit, :3]).max()
+    assert np.abs(a[lit, :3] - b[lit, :3]).max() <= 1e-6 * scale
+    assert np.all(a[~lit] == 0)
+
+
 def _lrb2(S, o, dI, **kw):
     """Buffered two-pass: primal with splat records, then the backward from them."""
     buf = torch.empty(S.lrb2_buffer_bytes(o), dtype=torch.uint8, device="cuda")
