@@ -712,7 +712,8 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
       char* base = (char*)o->lrb3_state;
       kp.list = (uint32_t*)(base + lrb3_state_list(o->n_paths));
       kp.list_n = (unsigned long long*)(base + lrb3_state_count(o->n_paths));
-      LT_CUDA(cudaMemsetAsync(kp.list_n, 0, sizeof(unsigned long long), st));
+      kp.ticket = kp.list_n + 1;  // the primal's chunk counter (the backward zeroes it again)
+      LT_CUDA(cudaMemsetAsync(kp.list_n, 0, 2 * sizeof(unsigned long long), st));
     }
   }
   cudaError_t e = launch_primal(dev_for(s, o), kp, est, image, aux, cfg_for(s, o), st);

@@ -975,7 +975,11 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
   float3 Le = BATCH ? f3(0, 0, 0) : f3(kp0.Le[0], kp0.Le[1], kp0.Le[2]);
   Dispenser disp;
   BatchDispenser bdisp;
-  if (BATCH) bdisp.init(); else disp.init(kp0.n_paths);
+  // the plain estimator given the LRB-3 state takes 32-path chunks from a counter shared by
+  // the grid (no warp waits for a slower one at the end); the others split the range statically
+  if (BATCH) bdisp.init();
+  else if (EST == 0 && kp0.ticket) disp.init_dynamic(kp0.n_paths, kp0.ticket);
+  else disp.init(kp0.n_paths);
   int jb = 0;
   bool busy = false, more = true, active = false;
   int64_t p = 0;

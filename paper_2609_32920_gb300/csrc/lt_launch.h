@@ -33,7 +33,8 @@ struct KParams {
   uint32_t* list;              // paths with a valid connection (plain primal: appends;
                                // LRB-3 passes 2 and 3 with known masks: visit only these) or null
   unsigned long long* list_n;  // length of `list`
-  unsigned long long* ticket;  // zeroed counters of list entries taken, [0] pass 2, [1] pass 3
+  unsigned long long* ticket;  // zeroed counters of entries taken: [0] pass 2, [1] pass 3 (plain
+                               // primal with the LRB-3 state: [0] its 32-path chunks)
   float4* conn1;               // per path: film position and contribution (u_x, u_y, L.r, L.g) of
   float* conn1z;               // its first valid connection, and L.b (plain primal: writes; LRB-3
                                // pass 2 with known masks: reads for paths with one connection)
