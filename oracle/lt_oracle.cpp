@@ -1527,7 +1527,7 @@ int or_gradient_literal(const or_scene* s, const or_params* p, const or_run* run
       std::memcpy(Jacc[1].data(), Jp, sizeof(M4));
       std::vector<bool> spec(K + 1, false);
       // singular by construction once a zero block has entered the product (a diffuse vertex
-      // without noise): detected exactly, the determinant guard judges the rest
+      // without noise): detected exactly, the determinant guard decides the rest
       std::vector<bool> sing(K + 1, false);
       for (int j = 1; j < K; ++j) {
         sing[j + 1] = sing[j];
