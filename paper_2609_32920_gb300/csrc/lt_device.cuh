@@ -337,19 +337,33 @@ __device__ __forceinline__ bool occluded2(const DevScene& S, float3 org, float3 
 constexpr int kWideStack = 64;
 constexpr int kCodeDone = -1;
 
+// Rows of a wide node's plane arrays (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z) that a ray enters
+// and leaves each slab by: with inv.x >= 0 it enters the x slab at lo.x and leaves at hi.x,
+// else the reverse.  fmaf(plane, inv, -oi) is monotone in the plane coordinate, so the entry
+// and exit distances read from these rows equal the per-axis min and max exactly (for every
+// box with lo <= hi), and the slab test needs no min/max per axis.
+struct Oct {
+  int r[6];  // rows of the near x, y, z planes, then of the far ones
+};
+__device__ __forceinline__ Oct ray_oct(float3 inv) {
+  Oct o;
+  o.r[0] = inv.x < 0.0f ? 3 : 0; o.r[1] = inv.y < 0.0f ? 4 : 1; o.r[2] = inv.z < 0.0f ? 5 : 2;
+  o.r[3] = 3 - o.r[0]; o.r[4] = 5 - o.r[1]; o.r[5] = 7 - o.r[2];
+  return o;
+}
 // Slab test of the `W` children of wide node `j` against a ray (origin times inverse
-// direction precomputed): tn[c] = entry distance, +inf when the child is missed, empty or
-// entered only beyond tmax.
+// direction precomputed, near and far rows from ray_oct): tn[c] = entry distance, +inf when
+// the child is missed, empty or entered only beyond tmax.
 template <int W>
 __device__ __forceinline__ void wide_boxes(const DevScene& S, int j, float3 inv, float3 oi, float tmax, float tn[W],
-                                           int code[W]) {
+                                           int code[W], const Oct& o) {
   const float* nd = reinterpret_cast<const float*>(S.wnode) + (size_t)j * 8 * W;
   float v[6][W];
 #pragma unroll
   for (int q = 0; q < 6; ++q)
 #pragma unroll
     for (int c4 = 0; c4 < W / 4; ++c4) {
-      const float4 a = __ldg(reinterpret_cast<const float4*>(nd + q * W) + c4);
+      const float4 a = __ldg(reinterpret_cast<const float4*>(nd + o.r[q] * W) + c4);
       v[q][4 * c4] = a.x; v[q][4 * c4 + 1] = a.y; v[q][4 * c4 + 2] = a.z; v[q][4 * c4 + 3] = a.w;
     }
 #pragma unroll
@@ -359,13 +373,13 @@ __device__ __forceinline__ void wide_boxes(const DevScene& S, int j, float3 inv,
   }
 #pragma unroll
   for (int c = 0; c < W; ++c) {
-    const float tx0 = fmaf(v[0][c], inv.x, -oi.x), tx1 = fmaf(v[3][c], inv.x, -oi.x);
-    const float ty0 = fmaf(v[1][c], inv.y, -oi.y), ty1 = fmaf(v[4][c], inv.y, -oi.y);
-    const float tz0 = fmaf(v[2][c], inv.z, -oi.z), tz1 = fmaf(v[5][c], inv.z, -oi.z);
-    const float a = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float b = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    // an empty slot (code -1) has an inverted box, which the per-axis min/max would turn
-    // into one that every ray enters: reject it by its code
+    // entry (near) and exit (far) distance of each slab
+    const float txn = fmaf(v[0][c], inv.x, -oi.x), txf = fmaf(v[3][c], inv.x, -oi.x);
+    const float tyn = fmaf(v[1][c], inv.y, -oi.y), tyf = fmaf(v[4][c], inv.y, -oi.y);
+    const float tzn = fmaf(v[2][c], inv.z, -oi.z), tzf = fmaf(v[5][c], inv.z, -oi.z);
+    const float a = fmaxf(fmaxf(txn, tyn), fmaxf(tzn, 0.0f));
+    const float b = fminf(fminf(txf, tyf), fminf(tzf, tmax));
+    // an empty slot (code -1) is rejected by its code, whatever box it stores
     tn[c] = (a <= b && code[c] != -1) ? a : __int_as_float(0x7f800000);
   }
 }
@@ -450,13 +464,14 @@ __device__ __forceinline__ bool trav_resume(const DevScene& S, float3 org, float
   if (next == kCodeDone) return true;
   const float3 inv = safe_inv(dir);
   const float3 oi = f3(org.x * inv.x, org.y * inv.y, org.z * inv.z);
+  const Oct oct = ray_oct(inv);
   while (next != kCodeDone && budget > 0) {
     while (next >= 0 && budget > 0) {
       --budget;
       float tn[W];
       int code[W];
       if (ST) cs->nodes += W;
-      wide_boxes<W>(S, next, inv, oi, T.h.t, tn, code);
+      wide_boxes<W>(S, next, inv, oi, T.h.t, tn, code, oct);
       sort_children<W>(tn, code);
 #pragma unroll
       for (int c = W - 1; c >= 0; --c) {
@@ -518,6 +533,7 @@ __device__ __forceinline__ HitRec trace_closest_w(const DevScene& S, float3 org,
   if (S.n_wnodes == 0) return h;
   const float3 inv = safe_inv(dir);
   const float3 oi = f3(org.x * inv.x, org.y * inv.y, org.z * inv.z);
+  const Oct oct = ray_oct(inv);
   int st_code[kWideStack];
   float st_t[kWideStack];
   int sp = 0;
@@ -528,7 +544,7 @@ __device__ __forceinline__ HitRec trace_closest_w(const DevScene& S, float3 org,
       float tn[W];
       int code[W];
       if (ST) cs->nodes += W;
-      wide_boxes<W>(S, next, inv, oi, h.t, tn, code);
+      wide_boxes<W>(S, next, inv, oi, h.t, tn, code, oct);
       sort_children<W>(tn, code);
 #pragma unroll
       for (int c = W - 1; c >= 0; --c) {
@@ -581,6 +597,7 @@ __device__ __forceinline__ bool occluded_w(const DevScene& S, float3 org, float3
   if (S.n_wnodes == 0) return false;
   const float3 inv = safe_inv(dir);
   const float3 oi = f3(org.x * inv.x, org.y * inv.y, org.z * inv.z);
+  const Oct oct = ray_oct(inv);
   int st_code[kWideStack];
   int sp = 0;
   bool overflow = false;
@@ -591,7 +608,7 @@ __device__ __forceinline__ bool occluded_w(const DevScene& S, float3 org, float3
       float tn[W];
       int code[W];
       if (ST) cs->nodes += W;
-      wide_boxes<W>(S, next, inv, oi, tmax, tn, code);
+      wide_boxes<W>(S, next, inv, oi, tmax, tn, code, oct);
 #pragma unroll
       for (int c = 0; c < W; ++c) {
         if (tn[c] <= tmax) {
