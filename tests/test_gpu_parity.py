@@ -136,14 +136,14 @@ def test_lrb3_reuses_primal_validity_masks(request, fixture_name, attached):
         assert rel_l2(x.cpu().numpy(), y.cpu().numpy()) < 1e-5
 
 
-@pytest.mark.parametrize("fixture_name,attached", [("boxhm", 1), ("slab", 1)])
-def test_single_connection_paths_take_delta_total_from_the_primal_record(request, fixture_name, attached):
+@pytest.mark.parametrize("fixture_name,attached,D", [("boxhm", 1, 8), ("slab", 1, 8), ("boxhm", 0, 40)])
+def test_single_connection_paths_take_delta_total_from_the_primal_record(request, fixture_name, attached, D):
     """With the primal's masks, pass 2 forms delta_total of a path with one valid connection
     from the primal's record of that connection (film position and contribution) instead of
     replaying it: per path, the same delta_total and connection count as the replay of the
-    fused form, on every path with a connection."""
+    fused form, on every path with a connection (depth 40: validity bits beyond 32 too)."""
     sc, S = request.getfixturevalue(fixture_name)
-    n, D, seed = 1 << 13, 8, 37
+    n, seed = 1 << 13, 37
     dI = t32(I.smooth_adjoint(sc.W, sc.H, 39))
     state = S.new_lrb3_state(n)
     S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state))
