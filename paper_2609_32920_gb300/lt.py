@@ -233,9 +233,10 @@ class Scene:
              census=None, lrb3_state=None, lrb3_mask_ready=0, bvh_width=0, rr_depth=0, rr_prob=1.0, filter=0,
              scatter=0, literal=0, jac_noise=0, noise_seed=0, det_eps=0.0):
         """Render options.  `lrb3_state`: a device buffer of lrb3_state_bytes(opts) bytes
-        selects the two-kernel form of lt_backward_lrb3, and a plain primal given it stores
-        the paths' connection-validity masks there; `lrb3_mask_ready=1` lets the backward
-        reuse them (see include/lt.h)."""
+        selects the separate-pass form of lt_backward_lrb3, and a plain primal given it stores
+        the paths' connection-validity masks, the list of paths with a connection and each
+        path's first connection there; `lrb3_mask_ready=1` lets the backward reuse them (see
+        include/lt.h)."""
         o = lt_render_opts()
         o.seed, o.path_offset, o.n_paths, o.n_norm = int(seed), int(path_offset), int(n_paths), int(n_norm)
         o.max_depth, o.attached, o.target = int(max_depth), int(attached), int(target)
