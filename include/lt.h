@@ -118,7 +118,7 @@ typedef struct {
                            lt_lrb3_state_bytes(opts) bytes.  Given, passes 2 and 3 run
                            as two kernels and pass 2 stores each path's delta_total
                            and connection-validity mask there (the paper's three-pass
-                           form; 44 B per path, flat in depth); NULL, one fused kernel
+                           form; 48 B per path and 4.2 MB, flat in depth); NULL, one fused kernel
                            keeps them in registers.  Same result either way.      */
   size_t lrb3_state_bytes; /* size of lrb3_state                                    */
   int lrb3_mask_ready;  /* lt_primal(LT_EST_PLAIN) given lrb3_state also stores each
@@ -462,7 +462,10 @@ size_t lt_lrb2_buffer_bytes(const lt_render_opts* opts);
  * connection) per path, then the list's length and the passes' counters (256 B), then
  * 20 B per path (film position and contribution of the path's first valid connection,
  * written by the plain primal: pass 2 takes delta_total of a path with exactly one valid
- * connection from it instead of replaying the path); each array 256-B aligned. */
+ * connection from it instead of replaying the path), then 4 B per path and a fixed 4.2 MB
+ * (the order in which the plain primal takes the paths, sorted by the cell of each path's
+ * first direction and emitter point, and the counting sort's work area; the order changes
+ * no result); each array 256-B aligned. */
 size_t lt_lrb3_state_bytes(const lt_render_opts* opts);
 
 /* Bytes of one ResLRB record (constant per path). */

@@ -361,6 +361,7 @@ KParams kparams(const lt_params* p, const lt_render_opts* o) {
   k.ticket = nullptr;
   k.conn1 = nullptr;
   k.conn1z = nullptr;
+  k.order = nullptr;
   k.jac_noise = o->jac_noise;
   k.noise_seed = o->noise_seed;
   k.det_eps = o->det_eps > 0.0f ? o->det_eps : 1e-6f;
@@ -685,6 +686,89 @@ size_t lt_naive_workspace_bytes(const lt_render_opts* o) {
   return head + (size_t)o->n_paths * (size_t)o->max_depth * 32;
 }
 
+namespace {
+// Order of the plain primal's paths: a counting sort by the cell of the path's first direction
+// (16 x 16 cells of the two uniforms of the emitter's cosine sample, Eq. 2) and of its point on
+// the emitter (4 x 4), so that the lanes of a warp, and the warps running at the same time,
+// trace first rays that leave in similar directions, and so do their next few rays.  Every
+// path's result depends only on its index, so the order changes no result, only the
+// coherence of the traversals (and, through the path list, of LRB-3 passes 2 and 3).
+__device__ __forceinline__ int sort_key(uint64_t seed, uint64_t n) {
+  const float4 r = rand4(seed, n, 0);
+  const int a = min((int)(r.z * 16.0f), 15), b = min((int)(r.w * 16.0f), 15);
+  const int c = min((int)(r.x * 4.0f), 3), d = min((int)(r.y * 4.0f), 3);
+  return ((a * 16 + b) * 4 + c) * 4 + d;
+}
+__device__ __forceinline__ int64_t sort_range(int64_t n, int blk) {
+  return (n + kSortBlocks - 1) / kSortBlocks * blk;
+}
+// counts[bin][block] of the block's contiguous range of paths
+__global__ void __launch_bounds__(1024) k_sort_count(uint64_t seed, uint64_t off, int64_t n, unsigned* counts) {
+  __shared__ unsigned h[kSortBins];
+  for (int i = threadIdx.x; i < kSortBins; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int64_t lo = min(sort_range(n, blockIdx.x), n), hi = min(sort_range(n, blockIdx.x + 1), n);
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) atomicAdd(&h[sort_key(seed, off + p)], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kSortBins; i += blockDim.x) counts[(size_t)i * kSortBlocks + blockIdx.x] = h[i];
+}
+// exclusive scan of counts in bin-major order: one thread per bin scans its blocks, then one
+// block scans the bins' totals into the bin starts
+__global__ void __launch_bounds__(256) k_sort_rows(unsigned* counts, unsigned* totals) {
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= kSortBins) return;
+  unsigned* row = counts + (size_t)bin * kSortBlocks;
+  unsigned acc = 0;
+  for (int b = 0; b < kSortBlocks; ++b) {
+    const unsigned v = row[b];
+    row[b] = acc;
+    acc += v;
+  }
+  totals[bin] = acc;
+}
+__global__ void __launch_bounds__(1024) k_sort_bins(unsigned* totals) {
+  __shared__ unsigned wsum[32];
+  constexpr int per = kSortBins / 1024;
+  unsigned loc = 0;
+  for (int j = 0; j < per; ++j) loc += totals[threadIdx.x * per + j];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned inc = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned w = wsum[lane];
+    unsigned wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += v;
+    }
+    wsum[lane] = wi - w;
+  }
+  __syncthreads();
+  unsigned run = wsum[wid] + inc - loc;
+  for (int j = 0; j < per; ++j) {
+    const unsigned c = totals[threadIdx.x * per + j];
+    totals[threadIdx.x * per + j] = run;
+    run += c;
+  }
+}
+// each block places its range's paths at bin start + its blocks-before offset + rank
+__global__ void __launch_bounds__(1024) k_sort_place(uint64_t seed, uint64_t off, int64_t n, const unsigned* counts,
+                                                     const unsigned* starts, uint32_t* order) {
+  __shared__ unsigned at[kSortBins];
+  for (int i = threadIdx.x; i < kSortBins; i += blockDim.x)
+    at[i] = starts[i] + counts[(size_t)i * kSortBlocks + blockIdx.x];
+  __syncthreads();
+  const int64_t lo = min(sort_range(n, blockIdx.x), n), hi = min(sort_range(n, blockIdx.x + 1), n);
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x)
+    order[atomicAdd(&at[sort_key(seed, off + p)], 1u)] = (uint32_t)p;
+}
+}  // namespace
+
 lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, int est, float* image, void* aux,
                     size_t aux_bytes, void* stream) {
   lt_status v = check_opts(s, p, o);
@@ -714,6 +798,17 @@ lt_status lt_primal(lt_scene* s, const lt_params* p, const lt_render_opts* o, in
       kp.list_n = (unsigned long long*)(base + lrb3_state_count(o->n_paths));
       kp.ticket = kp.list_n + 1;  // the primal's chunk counter (the backward zeroes it again)
       LT_CUDA(cudaMemsetAsync(kp.list_n, 0, 2 * sizeof(unsigned long long), st));
+      // the order of the paths (see sort_key)
+      uint32_t* order = (uint32_t*)(base + lrb3_state_order(o->n_paths));
+      unsigned* counts = (unsigned*)(base + lrb3_state_sort(o->n_paths));
+      unsigned* starts = counts + (size_t)kSortBins * kSortBlocks;
+      const uint64_t off = (uint64_t)o->path_offset;
+      k_sort_count<<<kSortBlocks, 1024, 0, st>>>(o->seed, off, o->n_paths, counts);
+      k_sort_rows<<<kSortBins / 256, 256, 0, st>>>(counts, starts);
+      k_sort_bins<<<1, 1024, 0, st>>>(starts);
+      k_sort_place<<<kSortBlocks, 1024, 0, st>>>(o->seed, off, o->n_paths, counts, starts, order);
+      LT_CUDA(cudaGetLastError());
+      kp.order = order;
     }
   }
   cudaError_t e = launch_primal(dev_for(s, o), kp, est, image, aux, cfg_for(s, o), st);

@@ -1011,7 +1011,7 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
       if (got < 0) {
         more = false;
       } else {
-        p = got;
+        p = (!BATCH && kp0.order) ? (int64_t)kp0.order[got] : got;
         if (BATCH) Le = f3(kp.Le[0], kp.Le[1], kp.Le[2]);
         active = !kp.mask || kp.mask[p];
         float3 x0;

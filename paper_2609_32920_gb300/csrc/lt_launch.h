@@ -25,6 +25,7 @@ struct KParams {
                                // (array lengths, or 0: that array goes to global memory directly)
   int priv_n;                  // n_alb + n_h: floats of dynamic shared memory per block
   const float* mlp;            // learned reservoir target parameters (DEVICE) or null (luminance)
+  const uint32_t* order;       // plain primal: the order in which it takes the paths (or null)
   void* vstate;                // plain primal: LRB-3 per-path state that receives each path's
                                // connection-validity mask (or null)
   int rr_depth;                // Russian roulette after vertices of depth >= rr_depth (0: off)
@@ -124,7 +125,11 @@ LT_KERNEL_LAUNCHERS
 // indices relative to the call, at lrb3_state_list) and its length (uint64, at
 // lrb3_state_count), written by a plain primal so that passes 2 and 3 visit only those;
 // then each path's first valid connection, float4 (u_x, u_y, L.r, L.g) at lrb3_state_conn4
-// and float L.b at lrb3_state_connz, written by the plain primal.
+// and float L.b at lrb3_state_connz, written by the plain primal; then the order in which the
+// plain primal takes the paths (uint32[n_paths] at lrb3_state_order) and the counting sort's
+// work area that builds it (kSortBins x kSortBlocks counts, then kSortBins bin starts).
+constexpr int kSortBins = 4096;   // 16 x 16 cells of the first direction, 4 x 4 of the emitter point
+constexpr int kSortBlocks = 256;  // blocks of the sort, each over a contiguous range of paths
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t lrb3_state_split(int64_t n) { return align256((size_t)n * 16); }
 __host__ __device__ inline size_t lrb3_state_core(int64_t n) { return lrb3_state_split(n) + align256((size_t)n * 4); }
@@ -132,7 +137,11 @@ __host__ __device__ inline size_t lrb3_state_list(int64_t n) { return lrb3_state
 __host__ __device__ inline size_t lrb3_state_count(int64_t n) { return lrb3_state_list(n) + align256((size_t)n * 4); }
 __host__ __device__ inline size_t lrb3_state_conn4(int64_t n) { return lrb3_state_count(n) + 256; }
 __host__ __device__ inline size_t lrb3_state_connz(int64_t n) { return lrb3_state_conn4(n) + align256((size_t)n * 16); }
-__host__ __device__ inline size_t lrb3_state_bytes(int64_t n) { return lrb3_state_connz(n) + align256((size_t)n * 4); }
+__host__ __device__ inline size_t lrb3_state_order(int64_t n) { return lrb3_state_connz(n) + align256((size_t)n * 4); }
+__host__ __device__ inline size_t lrb3_state_sort(int64_t n) { return lrb3_state_order(n) + align256((size_t)n * 4); }
+__host__ __device__ inline size_t lrb3_state_bytes(int64_t n) {
+  return lrb3_state_sort(n) + align256(sizeof(unsigned) * (size_t)kSortBins * (kSortBlocks + 1));
+}
 // After the list's length (uint64) at lrb3_state_count: the two passes' counters of list
 // entries taken (uint64 each).
 // The path list is used for calls of at most this many paths (uint32 indices).
