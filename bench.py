@@ -712,7 +712,7 @@ def method_sweep(step, dev, flush):
     for D in (4, 8, 16, 32, 64):
         memory[str(D)] = {}
         for m in METHODS:
-            ms, peak, dbytes = run(m, D, timed_reps=1)
+            ms, peak, dbytes = run(m, D, timed_reps=3)
             memory[str(D)][m] = {"extra_bytes": peak, "device_bytes": dbytes, "ms": ms}
     S.sync_status()
     return methods, memory
