@@ -52,7 +52,7 @@ METRIC = "adjoint light paths/s (LRB-3-pass attached: refit + primal + film + ba
 FLOPS_PER = {"node": 24, "prim": 30, "vertex": 150, "conn": 100}
 
 
-KERNEL_SOURCES = ("lt_kernels.cu", "lt_device.cuh", "lt_launch.h", "lt_batch.h", "lt_mlp.cuh")
+KERNEL_SOURCES = ("lt_kernels.cu", "lt_device.cuh", "lt_launch.h", "lt_batch.h", "lt_mlp.cuh", "lt_api.cu")
 
 
 def traffic_profile(workload):

@@ -464,8 +464,8 @@ size_t lt_lrb2_buffer_bytes(const lt_render_opts* opts);
  * written by the plain primal: pass 2 takes delta_total of a path with exactly one valid
  * connection from it instead of replaying the path), then 4 B per path and a fixed 4.2 MB
  * (the order in which the plain primal takes the paths, sorted by the cell of each path's
- * first direction and emitter point, and the counting sort's work area; the order changes
- * no result); each array 256-B aligned. */
+ * first direction, and the counting sort's work area; the order changes no result); each
+ * array 256-B aligned. */
 size_t lt_lrb3_state_bytes(const lt_render_opts* opts);
 
 /* Bytes of one ResLRB record (constant per path). */

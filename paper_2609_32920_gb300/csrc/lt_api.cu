@@ -688,16 +688,16 @@ size_t lt_naive_workspace_bytes(const lt_render_opts* o) {
 
 namespace {
 // Order of the plain primal's paths: a counting sort by the cell of the path's first direction
-// (16 x 16 cells of the two uniforms of the emitter's cosine sample, Eq. 2) and of its point on
-// the emitter (4 x 4), so that the lanes of a warp, and the warps running at the same time,
-// trace first rays that leave in similar directions, and so do their next few rays.  Every
+// (64 x 64 cells of the two uniforms of the emitter's cosine sample, Eq. 2), so that the lanes
+// of a warp, and the warps running at the same time, trace first rays that leave in similar
+// directions, and so do their next few rays (measured on the caustic: cells of the emitter
+// point as well, 16 x 16 x 4 x 4 or 32 x 32 x 2 x 2, were slightly slower).  Every
 // path's result depends only on its index, so the order changes no result, only the
 // coherence of the traversals (and, through the path list, of LRB-3 passes 2 and 3).
 __device__ __forceinline__ int sort_key(uint64_t seed, uint64_t n) {
   const float4 r = rand4(seed, n, 0);
-  const int a = min((int)(r.z * 16.0f), 15), b = min((int)(r.w * 16.0f), 15);
-  const int c = min((int)(r.x * 4.0f), 3), d = min((int)(r.y * 4.0f), 3);
-  return ((a * 16 + b) * 4 + c) * 4 + d;
+  const int a = min((int)(r.z * 64.0f), 63), b = min((int)(r.w * 64.0f), 63);
+  return a * 64 + b;
 }
 __device__ __forceinline__ int64_t sort_range(int64_t n, int blk) {
   return (n + kSortBlocks - 1) / kSortBlocks * blk;

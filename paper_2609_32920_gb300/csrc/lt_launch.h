@@ -128,7 +128,7 @@ LT_KERNEL_LAUNCHERS
 // and float L.b at lrb3_state_connz, written by the plain primal; then the order in which the
 // plain primal takes the paths (uint32[n_paths] at lrb3_state_order) and the counting sort's
 // work area that builds it (kSortBins x kSortBlocks counts, then kSortBins bin starts).
-constexpr int kSortBins = 4096;   // 16 x 16 cells of the first direction, 4 x 4 of the emitter point
+constexpr int kSortBins = 4096;   // 64 x 64 cells of the first direction
 constexpr int kSortBlocks = 256;  // blocks of the sort, each over a contiguous range of paths
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t lrb3_state_split(int64_t n) { return align256((size_t)n * 16); }
