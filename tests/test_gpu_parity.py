@@ -124,10 +124,15 @@ def test_lrb3_reuses_primal_validity_masks(request, fixture_name, attached):
     n, D, seed = 1 << 13, 8, 31
     dI = t32(I.smooth_adjoint(sc.W, sc.H, 33))
     state = S.new_lrb3_state(n)
-    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state)
+    h = torch.zeros(n, dtype=torch.int32, device="cuda")
+    o = S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state, hash_out=h)
     img = S.primal(o)
-    ref_img = S.primal(S.opts(seed=seed, n_paths=n, max_depth=D))
+    h_ref = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ref_img = S.primal(S.opts(seed=seed, n_paths=n, max_depth=D, hash_out=h_ref))
     assert rel_l2(img.cpu().numpy(), ref_img.cpu().numpy()) < 1e-6
+    # the primal given the state visits its paths in its own order: every path once, with the
+    # decisions of the index-ordered run
+    assert torch.equal(h, h_ref)
     om = S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached, lrb3_state=state, lrb3_mask_ready=1)
     g = S.backward_lrb3(om, dI)
     ref = S.backward_lrb3(S.opts(seed=seed, n_paths=n, max_depth=D, attached=attached), dI)
