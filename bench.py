@@ -244,13 +244,14 @@ def run_reference(args):
 # ------------------------------------------------------------------ GPU arm
 class Step:
     """One pass of the hot path on a workload: refit the height field (update_tris,
-    refit_nodes, refit_big, refit_wide<4>, refit_wide<8>: every width stays current), primal light
-    tracing storing the paths' connection-validity masks and first connections (1 kernel), film
-    L2 loss and image adjoint (1), LRB-3-pass backward in its three-pass form, attached (pass 2
-    of the single-connection paths, pass 2 of the others, pass 3: 3 kernels).  Events around
-    the primal and the backward time them on the launching stream."""
+    refit_nodes, refit_big, refit_wide<4>, refit_wide<8>: every width stays current), the
+    order of the paths (a counting sort, 4 kernels) and primal light tracing storing the
+    paths' connection-validity masks and first connections (1 kernel), film L2 loss and image
+    adjoint (1), LRB-3-pass backward in its three-pass form, attached (pass 2 of the
+    single-connection paths, pass 2 of the others, pass 3: 3 kernels).  Events around the
+    primal (with its sort) and the backward time them on the launching stream."""
 
-    LAUNCHES = 10
+    LAUNCHES = 14
 
     def __init__(self, name, dev, path_offset=0, n_norm=0, n_paths=0, scatter=0):
         import torch
