@@ -59,6 +59,37 @@ MUTANTS = {
     # attached slide: intersection parameter with the wrong sign
     "slide_sign": ("T tt = dot(o - xprev, n) / dot(din, n);", "T tt = dot(xprev - o, n) / dot(din, n);",
                    ["test_attached_height_gradient_vs_frozen_central_differences"]),
+    # ResLRB restatement: the winner's adjoint without the reservoir weight Omega/omega_R
+    "reslrb_no_weight": ("for (int c = 0; c < 3; ++c) { rem[c] = Pw[3 * P.R + c] * P.res_w;",
+                         "for (int c = 0; c < 3; ++c) { rem[c] = Pw[3 * P.R + c];",
+                         ["test_reslrb_restatement_equals_ad_of_reservoir_estimator"]),
+    # literal transport: the remainder contracted with the transposed inverse Jacobian
+    "literal_inv_transpose": ("for (int k = 0; k < 4; ++k) aloc[c] += Arem[k] * inv[k][c];",
+                              "for (int k = 0; k < 4; ++k) aloc[c] += Arem[k] * inv[c][k];",
+                              ["test_literal_attached_variant_exact_on_first_chains_and_unbiased_with_noise"]),
+    # Gauss-Jordan inverse without the final division by the pivots
+    "inverse_no_pivot": ("for (int j = 0; j < 4; ++j) inv[i][j] = m[i][j + 4] / m[i][i];",
+                         "for (int j = 0; j < 4; ++j) inv[i][j] = m[i][j + 4];",
+                         ["test_literal_attached_variant_exact_on_first_chains_and_unbiased_with_noise"]),
+    # Jacobian noise on one film axis only (the product stays singular)
+    "literal_noise_one_axis": ("          Jj[3][1] = eps;\n", "          Jj[3][1] = 0.0;\n",
+                               ["test_literal_attached_variant_exact_on_first_chains_and_unbiased_with_noise"]),
+    # network backward: hidden-layer adjoint through the transposed weights
+    "mlp_w2_transpose": ("a += dz2[j] * M.W2(i, j);", "a += dz2[j] * M.W2(j, i);",
+                         ["test_mlp_oracle_gradient_vs_central_differences"]),
+    # network backward: first ReLU's derivative dropped
+    "mlp_relu_mask": ("const double dz1 = z1[i] > 0 ? dh1[i] : 0.0;", "const double dz1 = dh1[i];",
+                      ["test_mlp_oracle_gradient_vs_central_differences"]),
+    # Snell's law with the relative index inverted (entering and leaving swapped)
+    "snell_eta_swap": ("T eta = entering ? T(1.0 / ior) : T(ior);", "T eta = entering ? T(ior) : T(1.0 / ior);",
+                       ["test_dielectric_fresnel_and_snell"]),
+    # refracted direction with the normal component's sign flipped
+    "refract_sign": ("refr = din * eta + ns * (eta * ci - ct);", "refr = din * eta + ns * (eta * ci + ct);",
+                     ["test_dielectric_fresnel_and_snell"]),
+    # diffuse bounce that continues the path without the albedo in its throughput
+    "bounce_no_albedo": ("      for (int c = 0; c < 3; ++c) beta[c] = beta[c] * rho[c];\n", "\n",
+                         ["test_primal_reciprocity_with_path_tracer",
+                          "test_detached_albedo_gradient_vs_central_differences"]),
 }
 
 
