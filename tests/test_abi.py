@@ -92,3 +92,24 @@ def test_size_queries_refuse_path_counts_that_would_wrap(liblt):
         assert liblt.lt_naive_workspace_bytes(C.byref(o)) == 0
         assert liblt.lt_lrb2_buffer_bytes(C.byref(o)) == 0
         assert liblt.lt_lrb3_state_bytes(C.byref(o)) == 0
+
+
+def test_lrb3_state_is_constant_in_depth_and_48_bytes_per_path(liblt):
+    """The separate-kernel LRB-3 state (Sec. 4.3; Results, "Memory Scaling"): per path the validity
+    mask, delta_total, a list entry, the first connection and the path order (48 B), plus the
+    counting sort's fixed 4.2 MB; nothing grows with the path depth."""
+    from paper_2609_32920_gb300 import lt
+    liblt.lt_lrb3_state_bytes.restype = C.c_size_t
+    o = lt.lt_render_opts()
+    sizes = {}
+    for n in (1 << 20, 1 << 24):
+        per_depth = set()
+        for D in (1, 8, 64):
+            o.n_paths, o.max_depth = n, D
+            per_depth.add(liblt.lt_lrb3_state_bytes(C.byref(o)))
+        assert len(per_depth) == 1, per_depth
+        sizes[n] = per_depth.pop()
+    assert sizes[1 << 24] - sizes[1 << 20] == 48 * ((1 << 24) - (1 << 20))
+    fixed = sizes[1 << 20] - 48 * (1 << 20)
+    sort_area = 4 * 4096 * 257
+    assert sort_area <= fixed <= sort_area + 8 * 256
