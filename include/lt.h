@@ -87,7 +87,7 @@ typedef struct {
 /* Per-call parameters theta (DEVICE pointers, FP32, caller-owned, read only). */
 typedef struct {
   const float* albedo;   /* [n_albedo] */
-  const float* Le;       /* [3]        */
+  const float* Le;       /* [3]; each component > 0 wherever d_Le is requested (below) */
 } lt_params;
 
 /* Largest n_paths and path_offset any call accepts (LT_ERR_INVALID_ARG beyond): every byte
@@ -188,7 +188,10 @@ typedef struct {
  * Overwritten unless accumulate != 0. */
 typedef struct {
   float* d_albedo;   /* [n_albedo]  */
-  float* d_Le;       /* [3]         */
+  float* d_Le;       /* [3]: a path's value is linear in Le (Eq. 2), so every backward
+                        forms this gradient as the path's contribution divided by Le; a
+                        zero component of Le makes that entry non-finite (the other
+                        outputs stay valid) */
   float* d_heights;  /* [n_heights] */
   int accumulate;
 } lt_grads;
