@@ -1205,6 +1205,9 @@ __device__ __forceinline__ void primal_body(const DevScene& S0, const KParams& k
   }
 }
 
+// Primal light tracing (Sec. 3.1, Eq. 1-2, splats by Eq. 20) for one estimator: EST 0 plain
+// (with the LRB-3 state: validity masks, path list, first connections), 1 ResLRB reservoir
+// records (Sec. 4.2, Eq. 8-9), 2 naive per-vertex tape (Sec. 3.2), 3 buffered splat records.
 template <int EST>
 __global__ void __launch_bounds__(128) k_primal(DevScene S, KParams kp, float* __restrict__ image, void* aux) {
   primal_body<EST, false>(S, kp, image, aux, BatchArgs{});
@@ -1223,6 +1226,7 @@ __global__ void __launch_bounds__(128, 4) k_primal_learned(DevScene S, KParams k
   primal_body<1, false, true>(S, kp, image, aux, BatchArgs{});
 }
 
+// Batched primal: lanes take (item, path) chunks from the batch queue.
 template <int EST>
 __global__ void __launch_bounds__(256) k_primal_batch(BatchArgs ba) {
   primal_body<EST, true>(ba.jobs[0].S, ba.jobs[0].kp, nullptr, nullptr, ba);
@@ -1765,6 +1769,8 @@ __device__ __forceinline__ void reslrb_body(const DevScene& S0, const KParams& k
   block_add3(g0.d_Le, gLe);
 }
 
+// ResLRB backward (Sec. 4.2.1-4.2.2, Eq. 11-13): replay each path to its reservoir vertex R
+// and weight every factor of L_R with Lbar_R (.) S from the primal's record.
 template <bool ATT, bool CH>
 __global__ void __launch_bounds__(128) k_reslrb(DevScene S, KParams kp, const float* __restrict__ dI,
                                                 const float4* __restrict__ rec, GradPtrs g0) {
@@ -2458,6 +2464,9 @@ __device__ __forceinline__ float2 lit_row(const DevScene& S, float3 x, const Pri
   return make_float2(dot(g, P.e1), dot(g, P.e2));
 }
 
+// Paper-literal attached LRB-3 (Eq. 4-7, Eq. 18-19, Sec. 5), one path per thread: pass 2
+// accumulates the 4x4 Jacobians forward and sums A_pos; pass 3 projects the remainder back
+// through the guarded inverse of the accumulated Jacobian at each specular vertex.
 __global__ void __launch_bounds__(128) k_lrb3_literal(DevScene S, KParams kp, const float* __restrict__ dI,
                                                       GradPtrs g0) {
   extern __shared__ float sgrad[];
