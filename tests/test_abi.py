@@ -113,3 +113,29 @@ def test_lrb3_state_is_constant_in_depth_and_48_bytes_per_path(liblt):
     fixed = sizes[1 << 20] - 48 * (1 << 20)
     sort_area = 4 * 4096 * 257
     assert sort_area <= fixed <= sort_area + 8 * 256
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The binding's ctypes structures and include/lt.h describe the same bytes: every field
+    the binding names exists in the C struct at the same offset, and the sizes agree (so
+    the C struct has no field the binding lacks).  Compiled with the host C compiler."""
+    import subprocess
+    from paper_2609_32920_gb300 import lt
+    structs = [lt.lt_scene_desc, lt.lt_params, lt.lt_render_opts, lt.lt_grads, lt.lt_batch_item,
+               lt.lt_bidir_opts, lt.lt_batch_config]
+    lines = ["#include <stdio.h>", '#include "lt.h"', "int main(void) {"]
+    for S in structs:
+        lines.append(f'  printf("%s size %zu\\n", "{S.__name__}", sizeof({S.__name__}));')
+        for name, _ in S._fields_:
+            lines.append(f'  printf("%s.%s %zu\\n", "{S.__name__}", "{name}", offsetof({S.__name__}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, "-o", str(exe), str(src)])
+    got = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for S in structs:
+        assert int(got[f"{S.__name__} size"]) == C.sizeof(S), S.__name__
+        for name, _ in S._fields_:
+            assert int(got[f"{S.__name__}.{name}"]) == getattr(S, name).offset, (S.__name__, name)
