@@ -206,6 +206,9 @@ lt_status lt_scene_create(const lt_scene_desc* desc, void* stream, lt_scene** ou
  * should see the heights.  Attached derivatives are taken at these heights. */
 lt_status lt_scene_refit(lt_scene* scene, const float* heights, void* stream);
 
+/* Free the scene's device memory (cudaFree, which waits for work in flight on the
+ * device) and the handle.  NULL is accepted and ignored.  The scene must not be in use
+ * by a batch that is still alive; the handle is invalid afterwards. */
 void lt_scene_destroy(lt_scene* scene);
 
 /* Primal light tracing (Sec. 3.1; ResLRB primal Sec. 4.2 and its listing; naive AD
@@ -387,7 +390,11 @@ lt_status lt_batch_create(const lt_batch_item* items, int n, void* stream, lt_ba
  * LT_ERR_INVALID_ARG: unknown pass, or a ResLRB pass with an item without records. */
 lt_status lt_batch_run(lt_batch* batch, int pass, void* stream);
 
+/* Set the launch shape of the batch's persistent kernels.  LT_ERR_INVALID_ARG for a NULL
+ * batch or a cfg outside the ranges of lt_batch_config (the configuration is then left
+ * unchanged).  The captured graphs are dropped and recaptured at the next run. */
 lt_status lt_batch_set_config(lt_batch* batch, const lt_batch_config* cfg);
+/* Copy the current configuration into *cfg (LT_ERR_INVALID_ARG if either is NULL). */
 lt_status lt_batch_get_config(const lt_batch* batch, lt_batch_config* cfg);
 
 /* Autotuner: time the pass (graph replay, CUDA events on `stream`, best of `reps` after
@@ -398,6 +405,9 @@ lt_status lt_batch_get_config(const lt_batch* batch, lt_batch_config* cfg);
  * backward pass with accumulate set accumulates every run). */
 lt_status lt_batch_tune(lt_batch* batch, int pass, int reps, void* stream, lt_batch_config* best, float* best_ms);
 
+/* Free the item table, the captured graphs and the batch's own streams and events; the
+ * items' scenes and buffers stay the caller's.  NULL is accepted and ignored.  No run of
+ * the batch may be in flight. */
 void lt_batch_destroy(lt_batch* batch);
 
 /* ---------------------------------------------------------------------------------
