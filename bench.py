@@ -827,6 +827,17 @@ def learned_target_study(dev):
             "cfg_stated": learned_stated_study(dev)}
 
 
+def connection_histogram(S, n, depth, seed, dev):
+    """Fraction of the paths with 0, 1, 2, ... valid sensor connections (the plain primal's
+    per-path count): the learned target can only pay where paths connect more than once."""
+    import torch
+    dbg = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+    S.primal(S.opts(seed=seed, n_paths=n, max_depth=depth, attached=1, dbg_out=dbg))
+    h = torch.bincount(dbg[:, 0].round().long()).cpu()
+    del dbg
+    return [float(c) / n for c in h]
+
+
 def learned_stated_study(dev, seeds=16, ref_seeds=256, depth=32):
     """The learned reservoir target at its stated size: ResLRB at depth 32 with 2^24 paths
     per gradient on the caustic workload (slab512_hm128, attached heights), the network
@@ -885,6 +896,10 @@ def learned_stated_study(dev, seeds=16, ref_seeds=256, depth=32):
                            f"{seeds} seeds; g_ref = LRB-3 over {ref_seeds} seeds",
                "connections_per_path": cnt / n, "pairs": int(f.shape[0]), "collect_ms": ms_collect,
                "train_ms": ms_train, "train_loss_first_last": [losses[0], losses[-1]]}
+        try:
+            row["connections_histogram"] = connection_histogram(S, n, depth, 9, dev)
+        except Exception as e:  # a diagnostic: its failure leaves the study's numbers standing
+            row["connections_histogram"] = "unavailable: %s" % e
         for name, extra in (("luminance", {}), ("learned", {"target": lt.TARGET_MLP, "mlp": P})):
             G, ms = [], []
             for s_ in range(seeds):
