@@ -40,7 +40,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_cover_the_single_process_run(oracle):
     world, port = 2, _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
         res = dict(out)
