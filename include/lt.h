@@ -41,7 +41,7 @@ typedef enum {
   LT_ERR_CUDA = 3,          /* a CUDA runtime call failed                           */
   LT_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up                   */
   LT_ERR_DEVICE_CHECK = 5,  /* a device-side bounds/consistency check fired         */
-  LT_ERR_UNSUPPORTED = 6    /* valid request this build does not implement          */
+  LT_ERR_UNSUPPORTED = 6    /* valid request the library does not implement         */
 } lt_status;
 
 enum { LT_MAT_DIFFUSE = 0, LT_MAT_DIELECTRIC = 1, LT_MAT_EMITTER = 2 };
