@@ -1,6 +1,6 @@
 """Host-side logic of the benchmark (CPU): the kernel fingerprint that keys the committed
-DRAM-traffic summaries, the reading of those summaries, and the clock-record parsing that
-decides whether a run is kept."""
+DRAM-traffic summaries, the reading of those summaries, the clock-record parsing that
+decides whether a run is kept, and the reference arm's output line."""
 import os
 import shutil
 
@@ -67,3 +67,42 @@ def test_workload_config_names_the_workload():
         cfg = bench.workload_config(1 << bench.WORKLOADS[wl]["paths_log2"], wl)
         assert cfg["workload"] == wl and cfg["paths_per_gpu"] == 1 << bench.WORKLOADS[wl]["paths_log2"]
         assert "model" not in cfg
+
+
+def _ref_args(**kw):
+    import argparse
+    a = dict(gpus=1, steps=2, warmup=3, impl="reference", workload="box256_hm32", paths_log2=0)
+    a.update(kw)
+    return argparse.Namespace(**a)
+
+
+def test_reference_arm_prints_one_contract_line(oracle, monkeypatch, capsys):
+    """`bench.py --impl reference` (the FP64 oracle on the host cores): one JSON line with the
+    contract's keys, the GPU arm's metric and workload, and zero host<->device bytes.  The
+    oracle's sample is forced small here; the arm itself sizes it by time."""
+    import json
+    monkeypatch.setattr(bench, "oracle_sample", lambda sc, dI, s, n_norm, depth: (64, 0.01, 2))
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    assert bench.run_reference(_ref_args()) == 0
+    out = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(out) == 1
+    line = json.loads(out[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
+    assert (line["steps"], line["warmup"], line["n_gpus"]) == (2, 3, 1)
+    assert line["config"] == bench.workload_config(1 << 22, "box256_hm32")
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] == 2 and "64 of the workload's" in line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "paths/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a: (_ for _ in ()).throw(AssertionError("rank 1 ran")))
+    assert bench.run_reference(_ref_args()) == 0
+    assert capsys.readouterr().out == ""
