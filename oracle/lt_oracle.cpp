@@ -973,6 +973,8 @@ int bidir_check(const or_scene* s, const or_run* run) {
 // =============================================================================== C API
 extern "C" {
 
+// One Philox4x32-10 block (Salmon et al., SC'11): the counter-based generator every pass
+// replays from (Sec. 3.2: a path is regenerated from its seed, not stored).
 void or_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, uint32_t* out) {
   U4 c = {{ctr[0], ctr[1], ctr[2], ctr[3]}};
   U4 o = philox(k0, k1, c);
@@ -985,12 +987,16 @@ int or_filter_taps(int filter, int W, int H, double ux, double uy, int* px, int*
   return filter_taps<double>(filter, W, H, ux, uy, px, py, w);
 }
 
+// The four uniforms in [0, 1) of path n at vertex depth d from Philox stream s (the
+// counter layout both sides implement from the generator's definition).
 void or_uniforms(uint64_t seed, uint64_t n, uint32_t d, uint32_t s, double* out4) {
   Rand4 r = rand4(seed, n, d, s);
   for (int i = 0; i < 4; ++i) out4[i] = r.u[i];
 }
 
-// Smooth-dielectric scattering of a unit direction at a surface with geometric normal n.
+// Smooth-dielectric scattering of a unit direction at a surface with geometric normal n:
+// unpolarised Fresnel reflectance, Snell refraction, total internal reflection; the
+// branch is chosen by u against F (the BSDF sampling step of Eq. 2's throughput).
 void or_dielectric(const double* din, const double* n, double ior, double u, double* dout, double* F, int* refl) {
   D3 d = {din[0], din[1], din[2]}, nn = {n[0], n[1], n[2]}, rl, rf;
   bool ent, tir;
@@ -1003,12 +1009,15 @@ void or_dielectric(const double* din, const double* n, double ior, double u, dou
   *refl = r ? 1 : 0;
 }
 
+// Capacity-one weighted reservoir over candidate weights w with uniforms u (Sec. 4.2,
+// Eq. 8-9): the selected index (or -1) and Omega / omega_R.
 int or_reservoir(const double* w, int n, const double* u, double* res_w) {
   std::vector<double> ww(w, w + n), uu(u, u + n);
   return reservoir(ww, uu, *res_w);
 }
 
-// Closest hit from org along dir (skipping primitive `skip`); returns the primitive or -1.
+// Closest hit from org along dir (skipping primitive `skip`) by testing every primitive
+// (no acceleration structure); returns the primitive or -1.
 int or_intersect(const or_scene* s, const or_params* p, const double* org, const double* dir, int skip, double* out3) {
   Scene sc{s, p};
   sc.setup();
@@ -1092,7 +1101,8 @@ int or_render_lt(const or_scene* s, const or_params* p, const or_run* run, const
   return 0;
 }
 
-// Gradient of <dI, I_s(theta)> (see header for methods).  Outputs are overwritten.
+// Gradient of <dI, I_s(theta)> (see header for methods: naive AD, Sec. 3.2; LRB-3-pass,
+// Sec. 4.3, Eq. 14-19; ResLRB, Sec. 4.2, Eq. 9-13).  Outputs are overwritten.
 // path_dbg (optional) [n_paths][4] = (delta_total rgb, number of valid connections).
 int or_gradient(const or_scene* s, const or_params* p, const or_run* run, const double* dI, const uint8_t* mask,
                 or_grads* out, uint32_t* hashes, double* path_dbg) {
@@ -1295,8 +1305,8 @@ double or_frozen_loss(const or_scene* s, const or_params* p0, const or_params* p
   return v;
 }
 
-// Bidirectional estimator (light tracer + camera samples with next-event estimation,
-// balance heuristic; see above): image [H][W][3] overwritten.  N = run->n_norm (or
+// Bidirectional estimator (Discussion, "Toward more complex integrators": light tracer +
+// camera samples with next-event estimation, balance heuristic; see above): image [H][W][3] overwritten.  N = run->n_norm (or
 // n_paths) light paths from run, n_cam camera samples (indices 0..n_cam-1).  Optional
 // per-sample decision hashes of the light paths (hashes [n_paths]) and camera samples
 // (cam_hashes [n_cam]); masks skip paths / samples.  Returns < 0 for unsupported requests
@@ -1426,7 +1436,8 @@ int or_gradient_bidir(const or_scene* s, const or_params* p, const or_run* run, 
   return 0;
 }
 
-// Paper-literal attached LRB-3 gradient of <dI, I_s> (see the section above): naive AD of
+// Paper-literal attached LRB-3 gradient of <dI, I_s> (Eq. 4-7, Eq. 18-19, Sec. 5; see the
+// section above): naive AD of
 // the frozen path function with each connection's film position at its own frozen surface
 // coordinates, plus the film-position transport along specular chains by accumulated
 // two-point Jacobians with the determinant-guarded inverse (threshold det_eps) and, when
@@ -1609,7 +1620,8 @@ int or_gradient_literal(const or_scene* s, const or_params* p, const or_run* run
 }
 
 // Camera-side path tracer with next-event estimation to the area emitter (radiance
-// transport; used only to pin the light tracer by reciprocity).  Pixel p estimates
+// transport; used only to pin the light tracer by reciprocity: Eq. 1 measured from the
+// sensor side, Sec. 3.1).  Pixel p estimates
 // integral of tent_p(u) L(camera ray through u) du with u sampled from the tent itself;
 // camera paths with 1..D surface vertices are counted through NEE at each diffuse vertex
 // (matching light paths x0..xi with i <= D); emitter hits are black.  Diffuse scenes only.
@@ -1725,6 +1737,8 @@ struct MlpRef {
 }  // namespace
 
 extern "C" {
+// The learned reservoir target's network (not in the paper: 16 -> 64 -> 64 -> 1, ReLU),
+// optionally with the BF16 roundings of the GPU path; outputs in standardised units.
 void or_mlp_forward(const double* P, const double* X, int64_t n, int round, double* out) {
   MlpRef M{P, round != 0};
   for (int64_t s = 0; s < n; ++s) {
