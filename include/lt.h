@@ -39,7 +39,8 @@ typedef enum {
   LT_ERR_INVALID_ARG = 1,   /* a host-side argument check failed                    */
   LT_ERR_OOM = 2,           /* allocation failed or caller workspace too small      */
   LT_ERR_CUDA = 3,          /* a CUDA runtime call failed                           */
-  LT_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up                   */
+  LT_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up (reserved: no kernel
+                               of the library waits on another thread or launch)    */
   LT_ERR_DEVICE_CHECK = 5,  /* a device-side bounds/consistency check fired         */
   LT_ERR_UNSUPPORTED = 6    /* valid request the library does not implement         */
 } lt_status;
