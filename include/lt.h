@@ -87,8 +87,8 @@ typedef struct {
 
 /* Per-call parameters theta (DEVICE pointers, FP32, caller-owned, read only). */
 typedef struct {
-  const float* albedo;   /* [n_albedo] */
-  const float* Le;       /* [3]; each component > 0 wherever d_Le is requested (below) */
+  const float* albedo;   /* [n_albedo]; > 0 wherever d_albedo is requested (below)  */
+  const float* Le;       /* [3]; each component > 0 wherever d_Le is requested      */
 } lt_params;
 
 /* Largest n_paths and path_offset any call accepts (LT_ERR_INVALID_ARG beyond): every byte
@@ -188,7 +188,10 @@ typedef struct {
 /* Gradient outputs (DEVICE, FP32, caller-owned).  NULL skips a parameter group.
  * Overwritten unless accumulate != 0. */
 typedef struct {
-  float* d_albedo;   /* [n_albedo]  */
+  float* d_albedo;   /* [n_albedo]: the adjoints apply the log-derivative identity (Eq. 3)
+                        at each diffuse vertex, dividing its weight by the albedo there;
+                        a texel of zero albedo seen by a path makes its entries
+                        non-finite */
   float* d_Le;       /* [3]: a path's value is linear in Le (Eq. 2), so every backward
                         forms this gradient as the path's contribution divided by Le; a
                         zero component of Le makes that entry non-finite (the other
